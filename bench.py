@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the random-circuit state-vector hot path on GB300.
+
+One step = one pass of the whole path over one synthetic circuit instance:
+generate the circuit (grid rules of Sec. "Convergence to Porter-Thomas"),
+reset the state, plan + evolve (fused tile passes), write the 2^n output
+probabilities, Porter-Thomas statistics (moments 1..10, entropy, uniform
+cross entropy, norm), draw m samples, sample cross entropy (Eq. ae).  Each
+step uses a new circuit seed, so nothing is cached between steps.
+
+Metric: cycles/s = circuit depth / step time.  Default workload: the 5x6
+grid, 30 qubits, depth 40, complex64, 1e6 samples.
+
+Prints one JSON line (rank 0).  With --impl reference the oracle (FP64 CPU)
+is timed instead on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "grid5x6_n30_d40": dict(rows=5, cols=6, dead=(), depth=40, m=1_000_000, fp64_probs=True),
+    "grid6x6m2_n34_d40": dict(rows=6, cols=6, dead=((0, 0), (5, 5)), depth=40, m=1_000_000,
+                              fp64_probs=False),
+    "grid4x5_n20_d25": dict(rows=4, cols=5, dead=(), depth=25, m=100_000, fp64_probs=True),
+}
+DEFAULT_WORKLOAD = "grid5x6_n30_d40"
+METRIC = "cycles/s (random circuit, state-vector evolution + statistics + sampling)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--mode", choices=["fused", "tc"], default="fused")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the one-off plain-mode comparison run")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def kernel_launches_per_step(passes):
+    # fused passes + reset (memset, basis kernel) + probabilities (1)
+    # + statistics (2) + sampler (chunk sums, 3 scan kernels, search = 5)
+    # + cross entropy (memset, kernel, final sum = 3)
+    return passes + 2 + 1 + 2 + 5 + 3
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_1608_00263_gb300 as qs
+    from paper_1608_00263_gb300 import build as qs_build
+
+    qs_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOADS[args.workload]
+    dead = None
+    if W["dead"]:
+        dead = np.zeros(W["rows"] * W["cols"], dtype=np.uint8)
+        for r, c in W["dead"]:
+            dead[r * W["cols"] + c] = 1
+    n = W["rows"] * W["cols"] - len(W["dead"])
+    depth, m = W["depth"], W["m"]
+    mode = qs.QS_MODE_FUSED if args.mode == "fused" else qs.QS_MODE_FUSED_TC
+    stream = torch.cuda.current_stream()
+    h = qs.qs_state_create(n, qs.QS_C64, stream)
+    probs = torch.empty(1 << n, dtype=torch.float64 if W["fp64_probs"] else torch.float32,
+                        device="cuda")
+    samples = torch.empty(m, dtype=torch.int64, device="cuda")
+    base_seed = 1_000_003 * rank
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    apply_ms = []
+    timed_gates = []
+    results = {}
+
+    def step(i, timed):
+        seed = base_seed + i
+        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed, dead)   # a1
+        qs.qs_state_reset(h)                                                         # a2
+        qs.qs_prepare_circuit(h, gates, mode=mode)                                   # a3 (host plan)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        qs.qs_apply_circuit(h, gates, mode=mode)                                     # a4-a6
+        e1.record(stream)
+        qs.qs_probabilities(h, probs, fp64=W["fp64_probs"])                          # a7
+        st = qs.qs_pt_moments(h, 10)                                                 # a8
+        qs.qs_sample(h, m, 1000 + seed, out=samples)                                 # a9
+        ce, dh = qs.qs_cross_entropy(h, samples)                                     # a10
+        if timed:
+            apply_ms.append((e0, e1))
+            timed_gates.append(gates)
+        results["last"] = dict(entropy=st["entropy"], norm=st["norm"], delta_h=dh, ce=ce)
+
+    for i in range(args.warmup):
+        step(i, False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start, t_end = ev(), ev()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    apply_total = sum(a.elapsed_time(b) for a, b in apply_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    passes_seen = [qs.qs_plan_circuit(n, qs.QS_C64, g, mode=mode)["passes"] for g in timed_gates]
+    cycles = depth * args.steps * world
+    value = cycles / (total_ms / 1000.0)
+    passes_total = sum(passes_seen)
+    pass_bytes = 16.0 * (1 << n)                 # read + write of 2^n complex64
+    avg_pass_ms = apply_total / passes_total
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    achieved = pass_bytes / (avg_pass_ms / 1000.0) / 1e9
+    traffic = load_traffic(args.mode, n)
+
+    # ---- e2e: same steps through the public API with host buffers ----
+    probs_host = torch.empty(1 << n, dtype=probs.dtype, pin_memory=True)
+    samples_host = np.empty(m, dtype=np.uint64)
+    h2d = d2h = 0
+    e2e_ms = 0.0
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        seed = base_seed + 10_000 + i
+        t0 = time.perf_counter()
+        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed, dead)
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, gates, mode=mode)
+        qs.qs_probabilities(h, probs_host, fp64=W["fp64_probs"])
+        qs.qs_pt_moments(h, 10)
+        qs.qs_sample(h, m, 1000 + seed, out=samples_host)
+        qs.qs_cross_entropy(h, samples_host)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1000.0
+        h2d += gates.nbytes + samples_host.nbytes
+        d2h += probs_host.numel() * probs_host.element_size() + samples_host.nbytes + 8 * 14
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = depth * args.steps * world / (e2e_ms / 1000.0)
+
+    # ---- one-off comparison of the forms (apply only, untimed region) ----
+    compare = {}
+    if not args.no_compare and rank == 0:
+        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, base_seed, dead)
+        for name, md in (("plain", qs.QS_MODE_PLAIN), ("fused", qs.QS_MODE_FUSED)):
+            qs.qs_state_reset(h)
+            qs.qs_prepare_circuit(h, gates, mode=md)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            qs.qs_apply_circuit(h, gates, mode=md)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            pst = qs.qs_plan_circuit(n, qs.QS_C64, gates, mode=md)
+            compare[name] = {"apply_ms": round(ms, 3), "cycles_per_s": round(depth / (ms / 1e3), 2),
+                             "launches": pst["passes"],
+                             "hbm_frac_of_measured": round(pst["bytes"] / (ms / 1e3) / 1e9 / hbm_peak, 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(W, dead, n)
+
+    qs.qs_state_destroy(h)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "cycles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded random circuits of the paper's grid rules)",
+        "config": {"workload": args.workload, "qubits": n, "depth": depth, "samples": m,
+                   "state": "complex64 %.1f GB" % ((8 << n) / 1e9),
+                   "form": args.mode, "l2": "inputs larger than L2 (state %.1f GB)" % ((8 << n) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "apply_cycles_per_s": round(depth * args.steps / (apply_total / 1000.0), 3),
+        "passes_per_circuit": passes_total / args.steps,
+        "roofline": {"kernel": "k_fused_pass" if args.mode == "fused" else "k_tc_pass",
+                     "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                     "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                     "bytes_per_launch": pass_bytes, "avg_launch_ms": round(avg_pass_ms, 4)},
+        "e2e": {"value": round(e2e_value, 3), "unit": "cycles/s",
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": sum(kernel_launches_per_step(p) for p in passes_seen),
+        "clocks": clk,
+        "last_step": {k: round(v, 6) for k, v in results["last"].items()},
+        "forms": compare,
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def load_traffic(mode, n):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1608_00263_gb300", "csrc",
+                       "qs_fused.cu" if mode == "fused" else "qs_tc.cu")
+    try:
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    r = rec.get(mode)
+    if not r or r.get("source_sha1") != digest:
+        return None
+    # scale the captured launch's traffic to this state size
+    return round(r["bytes_per_launch"] * (2.0 ** n) / (2.0 ** r["qubits"]), 1)
+
+
+def cpu_baseline(W, dead, n, cycles=(1, 2)):
+    """Oracle (FP64 CPU) on a bounded sample: the gates of the given cycles of
+    the workload's circuit, applied to an n-qubit state; returns cycles/s."""
+    import numpy as np
+
+    import oracle as O
+    gates = O.generate_circuit(W["rows"], W["cols"], W["depth"], 0, dead)
+    sel = gates[(gates["cycle"] >= cycles[0]) & (gates["cycle"] <= cycles[-1])]
+    psi = O.zero_state(n)
+    t0 = time.perf_counter()
+    O.apply_circuit(psi, sel)
+    dt = time.perf_counter() - t0
+    del psi
+    ncyc = cycles[-1] - cycles[0] + 1
+    return {"value": round(ncyc / dt, 5), "unit": "cycles/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "FP64 oracle applying the %d gates of cycles %d-%d of the %s circuit to a "
+                      "%d-qubit state (OpenMP over all host cores; state allocation excluded)"
+                      % (len(sel), cycles[0], cycles[-1], "x".join(map(str, (W["rows"], W["cols"]))),
+                         n)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+
+    W = WORKLOADS[args.workload]
+    dead = None
+    if W["dead"]:
+        dead = np.zeros(W["rows"] * W["cols"], dtype=np.uint8)
+        for r, c in W["dead"]:
+            dead[r * W["cols"] + c] = 1
+    n = W["rows"] * W["cols"] - len(W["dead"])
+    import oracle as O
+    gates = O.generate_circuit(W["rows"], W["cols"], W["depth"], 0, dead)
+    sel = gates[(gates["cycle"] >= 1) & (gates["cycle"] <= 1)]
+    psi = O.zero_state(n)
+    for _ in range(args.warmup):
+        O.apply_circuit(psi, sel)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply_circuit(psi, sel)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = ("FP64 oracle, one cycle (%d gates, cycle 1) of the %s circuit per step on a "
+              "%d-qubit state, OpenMP over all host cores" % (len(sel), args.workload, n))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "cycles/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt * 1000 / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded random circuits of the paper's grid rules)",
+           "config": {"workload": args.workload, "qubits": n, "depth": W["depth"]},
+           "cpu_baseline": {"value": round(value, 5), "unit": "cycles/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 5), "unit": "cycles/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

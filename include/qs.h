@@ -1,0 +1,245 @@
+/*
+ * qs.h -- C ABI of the GB300 (sm_103a) state-vector library for the random
+ * circuit sampling method of Boixo et al., "Characterizing Quantum Supremacy
+ * in Near-Term Devices" (arXiv:1608.00263).
+ *
+ * The calls follow the paper's statement of the problem (Sec.
+ * "Characterizing quantum supremacy", the four-step estimation procedure):
+ * choose a circuit U, evolve |psi> = U|0...0>, take m samples x_j from
+ * p_U(x) = |<x|psi>|^2, compute log 1/p_U(x_j) and estimate the cross-entropy
+ * difference (Eq. ae); plus the Porter-Thomas statistics of Sec.
+ * "Convergence to Porter-Thomas" (entropy, Eq. eu; uniform cross entropy,
+ * Eq. eue; moments / inverse participation ratios).
+ *
+ * Conventions (all calls)
+ *   - Bit j of a basis-state index is qubit j.  Results are always in this
+ *     canonical order, whatever tiling the library uses internally.
+ *   - Every call returns a qs_status; on failure qs_last_error() gives a
+ *     thread-local message.  Arguments are validated on the host before any
+ *     kernel launch; no call aborts, traps or exits the process.
+ *   - Work is ordered on the state's CUDA stream.  Calls that return host
+ *     scalars (qs_cross_entropy, qs_pt_moments) synchronise that stream.
+ *   - Device memory of a state created by qs_state_create is owned by the
+ *     library; qs_state_attach wraps caller-owned device memory (for example
+ *     a torch tensor), which must outlive the handle.
+ *   - Output buffers are caller-owned.  Pointer arguments documented as
+ *     "host or device" are classified with cudaPointerGetAttributes.
+ *   - Gate arrays are read during the call only.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef QS_PUBLIC_API_H_
+#define QS_PUBLIC_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_state qs_state;
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_INVALID_ARG = 1,   /* bad size, qubit, pointer or option */
+    QS_ERR_OOM = 2,           /* device or host allocation failed */
+    QS_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed */
+    QS_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    QS_ERR_UNSUPPORTED = 5    /* valid request this build does not handle */
+} qs_status;
+
+/* Amplitude storage: complex64 (interleaved float re, im; 8 B) or complex128
+ * (interleaved double re, im; 16 B).  The paper's simulator used double
+ * complex (appendix "Quantum Simulation Details"). */
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Gate kinds.  Fixed gates of Sec. "Convergence to Porter-Thomas":
+ *   H; X^1/2 = exp(-i pi/4 X) and Y^1/2 = exp(-i pi/4 Y) (pi/2 rotations);
+ *   T = diag(1, e^{i pi/4}); CZ = diag(1, 1, 1, -1).
+ * Parameterised forms (theta in radians):
+ *   RX/RY/RZ(theta) = exp(-i theta/2 P);  CPHASE(theta) = diag(1,1,1,e^{i theta}).
+ * Two-qubit kinds (CZ, CPHASE) use q0 and q1 (q0 != q1, either order; both
+ * are diagonal and symmetric); single-qubit kinds use q0 and ignore q1. */
+typedef enum {
+    QS_H = 0, QS_X_HALF = 1, QS_Y_HALF = 2, QS_T = 3, QS_CZ = 4,
+    QS_RX = 5, QS_RY = 6, QS_RZ = 7, QS_CPHASE = 8
+} qs_kind;
+
+/* One gate, 16 bytes.  `cycle` is informational (clock cycle of the gate in
+ * the generated circuit); gates are applied in array order. */
+typedef struct {
+    uint8_t kind, q0, q1, pad;
+    uint32_t cycle;
+    double theta;
+} qs_gate;
+
+/* Execution forms of qs_apply_circuit. */
+typedef enum {
+    QS_MODE_PLAIN = 0,     /* one kernel, one state pass per gate; gate
+                              specialisation as in the appendix: diagonal
+                              gates touch only the amplitudes they change */
+    QS_MODE_FUSED = 1,     /* planner groups gates into tile passes; each
+                              pass stages 2^t-amplitude tiles through shared
+                              memory and applies many gates in registers
+                              (exact FP32 / FP64 CUDA-core arithmetic) */
+    QS_MODE_FUSED_TC = 2   /* as FUSED, but gates are merged into dense
+                              k-qubit blocks applied as complex matrix
+                              products on the tcgen05 tensor cores */
+} qs_mode;
+
+/* Operand precision of QS_MODE_FUSED_TC (ignored by the other modes). */
+typedef enum {
+    QS_PREC_DEFAULT = 0,   /* FP16x3 for TC mode */
+    QS_PREC_FP16X3 = 1,    /* hi/lo FP16 split of both operands, three
+                              products, FP32 accumulation, per-tile
+                              power-of-two scaling: ~22 significant bits */
+    QS_PREC_BF16X3 = 2     /* hi/lo BF16 split, three products: ~16 bits;
+                              reported lossy */
+} qs_precision;
+
+/* Options for qs_apply_circuit; NULL means defaults
+ * {QS_MODE_FUSED, QS_PREC_DEFAULT, k = 0 (library choice), tile_log2 = 0
+ * (library choice), autotune = 0}. */
+typedef struct {
+    int mode;        /* qs_mode */
+    int precision;   /* qs_precision */
+    int k;           /* TC block size in qubits (6 is the only built value) */
+    int tile_log2;   /* fused tile size in amplitudes, log2 (0 = default) */
+    int autotune;    /* reserved, must be 0 */
+} qs_opts;
+
+/* Planner summary (host-only, see qs_plan_circuit). */
+typedef struct {
+    int passes;          /* state passes (kernel launches over the state) */
+    int phases;          /* register / tensor-core phases over all passes */
+    int ops;             /* device ops over all phases */
+    int tile_log2;       /* tile size used, log2 amplitudes */
+    int reg_log2;        /* register (or block) bits per phase */
+    int gates;           /* gates planned */
+    double bytes;        /* algorithmic HBM bytes of the plan (read+write) */
+} qs_plan_stats;
+
+/* Library version string, e.g. "qs 1.0 sm_103a". */
+const char *qs_version(void);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *qs_last_error(void);
+
+/* Creates an n-qubit state (1 <= n <= 34) of type dt in device memory owned
+ * by the library, initialised to |0...0>, with all work ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * Returns QS_ERR_OOM if 2^n amplitudes do not fit.  *out is set only on
+ * success. */
+qs_status qs_state_create(int n, qs_dtype dt, void *cuda_stream, qs_state **out);
+
+/* Wraps caller-owned device memory `device_amps` (2^n amplitudes of type dt,
+ * 16-byte aligned) as a state.  The contents are left untouched.  The
+ * library still allocates its small statistics workspace. */
+qs_status qs_state_attach(int n, qs_dtype dt, void *device_amps,
+                          void *cuda_stream, qs_state **out);
+
+/* Releases the handle (and the amplitudes if the library owns them).
+ * NULL is accepted.  Synchronises the state's stream first. */
+qs_status qs_state_destroy(qs_state *s);
+
+/* Device pointer of the amplitudes (interleaved re, im). */
+qs_status qs_state_amplitudes(const qs_state *s, void **device_amps);
+
+/* Sets the state to |0...0>. */
+qs_status qs_state_reset(qs_state *s);
+
+/* Applies `ngates` gates (host array, read during the call) in order:
+ * |psi> <- G_{ngates-1} ... G_0 |psi>  (Eq. sqgunitaryoperation for each
+ * single-qubit gate; controlled form for CZ / CPHASE).  Every gate is
+ * validated first (kind < 9, qubits < n, q0 != q1 for two-qubit kinds); on
+ * error nothing is launched.  `opts` may be NULL. */
+qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
+                           const qs_opts *opts);
+
+/* Plans `gates` for this state and uploads the plan to the device without
+ * launching anything (synchronous).  A following qs_apply_circuit with the
+ * same gate list and options reuses the plan, so its call only launches
+ * kernels.  Validation as for qs_apply_circuit; QS_MODE_PLAIN needs no plan
+ * and returns QS_OK. */
+qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
+                             const qs_opts *opts);
+
+/* Runs the planner only (no device work): fills *stats for the given gate
+ * list, qubit count, dtype and options. */
+qs_status qs_plan_circuit(int n, qs_dtype dt, const qs_gate *gates,
+                          size_t ngates, const qs_opts *opts,
+                          qs_plan_stats *stats);
+
+/* Writes p_U(x) = |<x|psi>|^2 for all 2^n x in canonical order into `out`
+ * (host or device, caller-owned): doubles if out_is_fp64, else floats.
+ * Asynchronous for device `out`; synchronous for host `out`. */
+qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64);
+
+/* Draws k bitstrings from p_U (inverse-CDF sampling, Sec. "Characterizing
+ * quantum supremacy", step 2 of the procedure).  Sample j uses the uniform
+ * u_j = (SplitMix64 output j of a stream seeded with `seed`) >> 11, times
+ * 2^-53, and returns the smallest x with C_x > u_j * C_{N-1}, where C is the
+ * cumulative sum of p in index order.  The total C_{N-1} normalises away any
+ * norm drift; x with p(x) = 0 is never returned.  `out` (host or device,
+ * caller-owned) receives k uint64 indices in sample order.  Synchronous for
+ * host `out`.  Returns QS_ERR_INVALID_ARG if the state has zero norm. */
+qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out);
+
+/* Cross entropy of a sample against the ideal distribution, Eq. ae:
+ *   *ce = (1/m) sum_j ln(1/p_U(x_j)),  *delta_h = ln N + gamma - *ce
+ * (gamma = Euler's constant; ln N + gamma = H_0 of Eq. au).  `samples`
+ * (host or device) holds m indices < 2^n; an index out of range returns
+ * QS_ERR_INVALID_ARG.  ce or delta_h may be NULL.  Synchronous. */
+qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples,
+                           uint64_t m, double *ce, double *delta_h);
+
+/* Porter-Thomas statistics of p_U in one read of the state, FP64
+ * accumulation (Sec. "Convergence to Porter-Thomas").  They are computed
+ * for the normalised distribution p / S, S = sum p, so that the rounding
+ * drift of the state's norm does not enter them (the paper's quantities are
+ * defined for a normalised distribution):
+ *   moments[k-1] = N^{k-1} sum_x (p_x/S)^k for k = 1..kmax (kmax <= 10), the
+ *                  normalised inverse participation ratios (-> k! for
+ *                  Porter-Thomas);
+ *   *entropy     = -sum (p/S) ln(p/S) (Eq. lps; Porter-Thomas value
+ *                  ln N - 1 + gamma, Eq. eu);
+ *   *uniform_ce  = -(1/N) sum ln(p/S) (Eq. eue; ln N + gamma), +inf if some
+ *                  p is exactly zero;
+ *   *norm        = S = sum p.
+ * For a zero state: norm 0, entropy 0, uniform_ce +inf, moments 0.
+ * Any output pointer may be NULL (kmax = 0 skips moments).  Synchronous. */
+qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments,
+                        double *entropy, double *uniform_ce, double *norm);
+
+/* Copies the amplitudes to / from a host buffer of 2^n amplitudes in
+ * canonical order (testing, checkpoints).  Synchronous. */
+qs_status qs_state_copy_out(const qs_state *s, void *host_amps);
+qs_status qs_state_copy_in(qs_state *s, const void *host_amps);
+
+/* Random circuit of Sec. "Convergence to Porter-Thomas" on a rows x cols
+ * grid (live sites numbered row-major are qubits 0..n-1; dead[r*cols+c] != 0
+ * removes a site; dead may be NULL):
+ *   cycle 0: H on every qubit;
+ *   cycle t = 1..depth: CZ layout (t-1) mod 8, then on each qubit that was in
+ *   a CZ at t-1 and is not in one at t: T if it is the qubit's first
+ *   single-qubit gate after the H layer, else a uniform pick (SplitMix64
+ *   stream seeded with `seed`, one draw per pick, top bit) from
+ *   {X^1/2, Y^1/2, T} without the qubit's previous single-qubit gate.
+ * The eight layouts (the paper's figure of them is not reproduced in the
+ * text) are read as: H_a = horizontal edges (r,c)-(r,c+1) with
+ * (c + 2r) mod 4 = a, V_a = vertical edges (r,c)-(r+1,c) with
+ * (r + 2c) mod 4 = a, in the order H0 H2 V0 V2 H1 H3 V1 V3; edges touching
+ * dead sites are dropped.  Within a cycle: CZs first (row-major edge order,
+ * q0 < q1), then single-qubit gates by ascending qubit.
+ * If out == NULL, *ngates receives the gate count; otherwise `out` must hold
+ * *ngates entries on entry (capacity) and *ngates receives the count.
+ * n = live sites must be 1..64. */
+qs_status qs_circuit_generate(int rows, int cols, const uint8_t *dead,
+                              int depth, uint64_t seed, qs_gate *out,
+                              size_t *ngates);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_PUBLIC_API_H_ */

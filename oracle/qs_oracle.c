@@ -218,6 +218,9 @@ int oracle_apply_1q(double complex *psi, int n, int k, const double complex u[4]
 {
     if (k < 0 || k >= n) return -1;
     uint64_t N = 1ULL << n, bit = 1ULL << k;
+    /* every pair is updated independently: the loop may run on several
+     * threads without changing any result */
+#pragma omp parallel for schedule(static) if (n >= 16)
     for (uint64_t i = 0; i < N; ++i) {
         if (i & bit) continue;
         double complex a0 = psi[i], a1 = psi[i | bit];
@@ -234,6 +237,7 @@ int oracle_apply_controlled(double complex *psi, int n, int c, int t,
 {
     if (c < 0 || c >= n || t < 0 || t >= n || c == t) return -1;
     uint64_t N = 1ULL << n, cb = 1ULL << c, tb = 1ULL << t;
+#pragma omp parallel for schedule(static) if (n >= 16)
     for (uint64_t i = 0; i < N; ++i) {
         if (!(i & cb) || (i & tb)) continue;
         double complex a0 = psi[i], a1 = psi[i | tb];
@@ -274,6 +278,7 @@ int oracle_apply_circuit(double complex *psi, int n, const oracle_gate *g, size_
 void oracle_probabilities(const double complex *psi, int n, double *p)
 {
     uint64_t N = 1ULL << n;
+#pragma omp parallel for schedule(static) if (n >= 16)
     for (uint64_t i = 0; i < N; ++i) {
         double re = creal(psi[i]), im = cimag(psi[i]);
         p[i] = re * re + im * im;

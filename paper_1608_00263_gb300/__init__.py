@@ -1,0 +1,185 @@
+"""GB300 (sm_103a) state-vector library for the random-circuit sampling method of
+Boixo et al., "Characterizing Quantum Supremacy in Near-Term Devices"
+(arXiv:1608.00263).
+
+Thin Python binding of the C ABI in ``include/qs.h``: the functions below
+carry the C names and only marshal arguments (numpy arrays, torch tensors or
+raw pointers) into ``libqs.so``.  Every step of the method runs in the
+library's CUDA kernels; if the library is missing the calls raise.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+from ._native import (GATE_DTYPE, QSError, QS_C64, QS_C128, QS_H, QS_X_HALF, QS_Y_HALF, QS_T,
+                      QS_CZ, QS_RX, QS_RY, QS_RZ, QS_CPHASE, QS_MODE_PLAIN, QS_MODE_FUSED,
+                      QS_MODE_FUSED_TC, QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3)
+
+__all__ = [
+    "GATE_DTYPE", "QSError", "QS_C64", "QS_C128", "QS_H", "QS_X_HALF", "QS_Y_HALF", "QS_T",
+    "QS_CZ", "QS_RX", "QS_RY", "QS_RZ", "QS_CPHASE", "QS_MODE_PLAIN", "QS_MODE_FUSED",
+    "QS_MODE_FUSED_TC", "QS_PREC_DEFAULT", "QS_PREC_FP16X3", "QS_PREC_BF16X3",
+    "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
+    "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
+    "qs_plan_circuit",
+    "qs_probabilities", "qs_sample", "qs_cross_entropy", "qs_pt_moments",
+    "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "library_path",
+]
+
+
+def library_path():
+    return N.LIB_PATH
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError("expected a torch tensor, numpy array or int address, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(mode, precision, k, tile_log2):
+    return N.qs_opts(mode, precision, k, tile_log2, 0)
+
+
+def _gates(gates):
+    g = np.ascontiguousarray(gates)
+    if g.dtype != GATE_DTYPE:
+        g = g.astype(GATE_DTYPE)
+    return g
+
+
+def qs_version():
+    return N.lib().qs_version().decode()
+
+
+def qs_last_error():
+    return N.lib().qs_last_error().decode()
+
+
+def qs_state_create(n, dtype=QS_C64, stream=None):
+    h = ctypes.c_void_p()
+    N.check(N.lib().qs_state_create(n, dtype, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_state_attach(n, dtype, amps, stream=None):
+    h = ctypes.c_void_p()
+    N.check(N.lib().qs_state_attach(n, dtype, _ptr(amps), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_state_destroy(h):
+    N.check(N.lib().qs_state_destroy(h))
+
+
+def qs_state_amplitudes(h):
+    p = ctypes.c_void_p()
+    N.check(N.lib().qs_state_amplitudes(h, ctypes.byref(p)))
+    return p.value
+
+
+def qs_state_reset(h):
+    N.check(N.lib().qs_state_reset(h))
+
+
+def qs_apply_circuit(h, gates, mode=QS_MODE_FUSED, precision=QS_PREC_DEFAULT, k=0, tile_log2=0):
+    g = _gates(gates)
+    o = _opts(mode, precision, k, tile_log2)
+    N.check(N.lib().qs_apply_circuit(h, g.ctypes.data if g.size else None, g.size, ctypes.byref(o)))
+
+
+def qs_prepare_circuit(h, gates, mode=QS_MODE_FUSED, precision=QS_PREC_DEFAULT, k=0, tile_log2=0):
+    g = _gates(gates)
+    o = _opts(mode, precision, k, tile_log2)
+    N.check(N.lib().qs_prepare_circuit(h, g.ctypes.data if g.size else None, g.size, ctypes.byref(o)))
+
+
+def qs_plan_circuit(n, dtype, gates, mode=QS_MODE_FUSED, precision=QS_PREC_DEFAULT, k=0,
+                    tile_log2=0):
+    g = _gates(gates)
+    o = _opts(mode, precision, k, tile_log2)
+    st = N.qs_plan_stats()
+    N.check(N.lib().qs_plan_circuit(n, dtype, g.ctypes.data if g.size else None, g.size,
+                                    ctypes.byref(o), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in N.qs_plan_stats._fields_}
+
+
+def qs_probabilities(h, out, fp64=True):
+    """Writes |<x|psi>|^2 into `out` (torch tensor, numpy array or address)."""
+    N.check(N.lib().qs_probabilities(h, _ptr(out), 1 if fp64 else 0))
+    return out
+
+
+def qs_sample(h, k, seed, out=None):
+    """k samples; returns a uint64 numpy array unless `out` is given."""
+    if out is None:
+        out = np.empty(k, dtype=np.uint64)
+    N.check(N.lib().qs_sample(h, k, seed & (2**64 - 1), _ptr(out)))
+    return out
+
+
+def qs_cross_entropy(h, samples):
+    """Returns (CE, Delta H) of Eq. ae for the sample indices."""
+    if isinstance(samples, np.ndarray):
+        samples = np.ascontiguousarray(samples, dtype=np.uint64)
+        m = samples.size
+    else:
+        m = samples.numel()
+    ce = ctypes.c_double()
+    dh = ctypes.c_double()
+    N.check(N.lib().qs_cross_entropy(h, _ptr(samples), m, ctypes.byref(ce), ctypes.byref(dh)))
+    return ce.value, dh.value
+
+
+def qs_pt_moments(h, kmax=10):
+    m = (ctypes.c_double * max(kmax, 1))()
+    ent, uce, nrm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    N.check(N.lib().qs_pt_moments(h, kmax, m, ctypes.byref(ent), ctypes.byref(uce),
+                                  ctypes.byref(nrm)))
+    return {"moments": np.array(m[:kmax]), "entropy": ent.value, "uniform_ce": uce.value,
+            "norm": nrm.value}
+
+
+def qs_state_copy_out(h, n, dtype=QS_C64):
+    out = np.empty(1 << n, dtype=np.complex64 if dtype == QS_C64 else np.complex128)
+    N.check(N.lib().qs_state_copy_out(h, out.ctypes.data))
+    return out
+
+
+def qs_state_copy_in(h, amps):
+    a = np.ascontiguousarray(amps)
+    N.check(N.lib().qs_state_copy_in(h, a.ctypes.data))
+
+
+def qs_circuit_generate(rows, cols, depth, seed, dead=None):
+    d = None
+    if dead is not None:
+        d = np.ascontiguousarray(dead, dtype=np.uint8)
+    cnt = ctypes.c_size_t(0)
+    dp = d.ctypes.data if d is not None else None
+    N.check(N.lib().qs_circuit_generate(rows, cols, dp, depth, seed & (2**64 - 1), None,
+                                        ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    N.check(N.lib().qs_circuit_generate(rows, cols, dp, depth, seed & (2**64 - 1),
+                                        out.ctypes.data, ctypes.byref(cnt)))
+    return out

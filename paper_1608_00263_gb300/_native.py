@@ -1,0 +1,94 @@
+"""ctypes binding of the C ABI in include/qs.h (argument marshalling only).
+
+Every computation happens in ``libqs.so``; this module converts Python
+arguments to pointers and sizes and raises ``QSError`` on a non-zero status.
+The library must be built (``paper_1608_00263_gb300.build.build()``); there
+is no fallback path: a missing library raises at import of the functions.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqs.so")
+
+QS_OK, QS_ERR_INVALID_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = range(6)
+QS_C64, QS_C128 = 0, 1
+(QS_H, QS_X_HALF, QS_Y_HALF, QS_T, QS_CZ, QS_RX, QS_RY, QS_RZ, QS_CPHASE) = range(9)
+QS_MODE_PLAIN, QS_MODE_FUSED, QS_MODE_FUSED_TC = 0, 1, 2
+QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3 = 0, 1, 2
+
+GATE_DTYPE = np.dtype([("kind", np.uint8), ("q0", np.uint8), ("q1", np.uint8),
+                       ("pad", np.uint8), ("cycle", np.uint32), ("theta", np.float64)])
+
+STATUS_NAMES = {0: "QS_OK", 1: "QS_ERR_INVALID_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA",
+                4: "QS_ERR_TIMEOUT", 5: "QS_ERR_UNSUPPORTED"}
+
+
+class QSError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class qs_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("precision", ctypes.c_int), ("k", ctypes.c_int),
+                ("tile_log2", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class qs_plan_stats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int), ("phases", ctypes.c_int), ("ops", ctypes.c_int),
+                ("tile_log2", ctypes.c_int), ("reg_log2", ctypes.c_int), ("gates", ctypes.c_int),
+                ("bytes", ctypes.c_double)]
+
+
+# Every function the header declares, with its ctypes signature.
+P = ctypes.c_void_p
+D = ctypes.c_double
+U64 = ctypes.c_uint64
+PD = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "qs_version": (ctypes.c_char_p, []),
+    "qs_last_error": (ctypes.c_char_p, []),
+    "qs_state_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]),
+    "qs_state_attach": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, ctypes.POINTER(P)]),
+    "qs_state_destroy": (ctypes.c_int, [P]),
+    "qs_state_amplitudes": (ctypes.c_int, [P, ctypes.POINTER(P)]),
+    "qs_state_reset": (ctypes.c_int, [P]),
+    "qs_apply_circuit": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.POINTER(qs_opts)]),
+    "qs_prepare_circuit": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.POINTER(qs_opts)]),
+    "qs_plan_circuit": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
+                                       ctypes.POINTER(qs_opts), ctypes.POINTER(qs_plan_stats)]),
+    "qs_probabilities": (ctypes.c_int, [P, P, ctypes.c_int]),
+    "qs_sample": (ctypes.c_int, [P, U64, U64, P]),
+    "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),
+    "qs_pt_moments": (ctypes.c_int, [P, ctypes.c_int, PD, PD, PD, PD]),
+    "qs_state_copy_out": (ctypes.c_int, [P, P]),
+    "qs_state_copy_in": (ctypes.c_int, [P, P]),
+    "qs_circuit_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, U64, P,
+                                           ctypes.POINTER(ctypes.c_size_t)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libqs.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError("libqs.so is not built: run paper_1608_00263_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != QS_OK:
+        msg = lib().qs_last_error()
+        raise QSError(status, msg.decode() if msg else "")

@@ -1,0 +1,367 @@
+// qs_api.cu -- the C ABI entry points of include/qs.h (host side): argument
+// validation, memory classification, planning and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qs_device.cuh"
+
+using namespace qs;
+
+namespace {
+
+constexpr size_t kWsDoubles = 1 << 16;
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+qs_status check_state(const qs_state *s)
+{
+    if (!s) return set_error(QS_ERR_INVALID_ARG, "state is NULL");
+    return QS_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ULL)
+{
+    const unsigned char *p = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+qs_status alloc_workspace(qs_state *s)
+{
+    QS_CUDA_TRY(cudaMalloc((void **)&s->ws_f64, kWsDoubles * sizeof(double)));
+    s->ws_f64_count = kWsDoubles;
+    QS_CUDA_TRY(cudaMalloc((void **)&s->ws_u64, 64 * sizeof(uint64_t)));
+    return QS_OK;
+}
+
+qs_status new_state(int n, qs_dtype dt, void *stream, qs_state **out)
+{
+    if (n < 1 || n > kMaxQubits) return set_error(QS_ERR_INVALID_ARG, "n = %d out of range 1..%d", n, kMaxQubits);
+    if (dt != QS_C64 && dt != QS_C128) return set_error(QS_ERR_INVALID_ARG, "bad dtype %d", (int)dt);
+    if (!out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
+    int dev = 0;
+    QS_CUDA_TRY(cudaGetDevice(&dev));
+    qs_state *s = new qs_state();
+    s->n = n;
+    s->dt = dt;
+    s->amps = nullptr;
+    s->owns = false;
+    s->stream = (cudaStream_t)stream;
+    s->device = dev;
+    s->ws_f64 = nullptr;
+    s->ws_u64 = nullptr;
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (s->num_sms <= 0) s->num_sms = 1;
+    *out = s;
+    return QS_OK;
+}
+
+void free_state(qs_state *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    if (s->owns && s->amps) cudaFree(s->amps);
+    if (s->ws_f64) cudaFree(s->ws_f64);
+    if (s->ws_u64) cudaFree(s->ws_u64);
+    if (s->plan_cache.dev) cudaFree(s->plan_cache.dev);
+    delete s;
+}
+
+}  // namespace
+
+extern "C" const char *qs_version(void) { return "qs 1.0 sm_103a"; }
+
+extern "C" qs_status qs_state_create(int n, qs_dtype dt, void *cuda_stream, qs_state **out)
+{
+    clear_error();
+    qs_state *s = nullptr;
+    qs_status st = new_state(n, dt, cuda_stream, &s);
+    if (st) return st;
+    const size_t bytes = (size_t(1) << n) * dtype_bytes(dt);
+    cudaError_t e = cudaMalloc(&s->amps, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_state(s);
+        return set_error(QS_ERR_OOM, "cannot allocate %zu bytes for %d qubits: %s", bytes, n,
+                         cudaGetErrorString(e));
+    }
+    s->owns = true;
+    if ((st = alloc_workspace(s)) || (st = launch_init_zero(s))) {
+        free_state(s);
+        return st;
+    }
+    *out = s;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_attach(int n, qs_dtype dt, void *device_amps, void *cuda_stream,
+                                     qs_state **out)
+{
+    clear_error();
+    if (!device_amps) return set_error(QS_ERR_INVALID_ARG, "device_amps is NULL");
+    if (((uintptr_t)device_amps & 15) != 0) return set_error(QS_ERR_INVALID_ARG, "device_amps not 16-byte aligned");
+    if (!is_device_ptr(device_amps)) return set_error(QS_ERR_INVALID_ARG, "device_amps is not device memory");
+    qs_state *s = nullptr;
+    qs_status st = new_state(n, dt, cuda_stream, &s);
+    if (st) return st;
+    s->amps = device_amps;
+    s->owns = false;
+    if ((st = alloc_workspace(s))) {
+        free_state(s);
+        return st;
+    }
+    *out = s;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_destroy(qs_state *s)
+{
+    clear_error();
+    free_state(s);
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_amplitudes(const qs_state *s, void **device_amps)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (!device_amps) return set_error(QS_ERR_INVALID_ARG, "device_amps is NULL");
+    *device_amps = s->amps;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_reset(qs_state *s)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    DeviceGuard g(s->device);
+    return launch_init_zero(s);
+}
+
+static qs_status get_plan(qs_state *s, const qs_gate *gates, size_t ng, const qs_opts *o,
+                          const Plan **plan, const void **dev)
+{
+    PlanParams pp = default_plan_params(s->n, s->dt, o);
+    uint64_t key = fnv1a(gates, ng * sizeof(qs_gate));
+    key = fnv1a(&pp, sizeof pp, key);
+    DevicePlanCache &c = s->plan_cache;
+    if (!(c.dev && c.key == key && c.ngates == ng)) {
+        Plan p;
+        if (qs_status st = build_plan(pp, gates, ng, &p)) return st;
+        const size_t b_pass = p.passes.size() * sizeof(DevPass);
+        const size_t b_phase = p.phases.size() * sizeof(DevPhase);
+        const size_t b_ops = p.ops.size() * sizeof(DevOp);
+        const size_t b_blk = p.tc_blocks.size() * sizeof(double);
+        const size_t total = b_pass + b_phase + b_ops + b_blk + 16;
+        std::vector<unsigned char> host(total, 0);
+        std::memcpy(host.data(), p.passes.data(), b_pass);
+        std::memcpy(host.data() + b_pass, p.phases.data(), b_phase);
+        std::memcpy(host.data() + b_pass + b_phase, p.ops.data(), b_ops);
+        if (b_blk) std::memcpy(host.data() + b_pass + b_phase + b_ops, p.tc_blocks.data(), b_blk);
+        if (c.dev && c.dev_bytes < total) {
+            QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+            cudaFree(c.dev);
+            c.dev = nullptr;
+        }
+        if (!c.dev) {
+            cudaError_t e = cudaMalloc(&c.dev, total);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                c.dev = nullptr;
+                return set_error(QS_ERR_OOM, "plan upload: %s", cudaGetErrorString(e));
+            }
+            c.dev_bytes = total;
+        }
+        // synchronous copy: the previous plan may still be in use on the stream
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        QS_CUDA_TRY(cudaMemcpy(c.dev, host.data(), total, cudaMemcpyHostToDevice));
+        c.key = key;
+        c.ngates = ng;
+        c.plan = std::move(p);
+    }
+    *plan = &c.plan;
+    *dev = c.dev;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
+                                      const qs_opts *opts)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
+    if (opts && opts->autotune != 0) return set_error(QS_ERR_UNSUPPORTED, "autotune is not built");
+    const int mode = opts ? opts->mode : QS_MODE_FUSED;
+    if (ngates == 0) return QS_OK;
+    DeviceGuard g(s->device);
+    const int rb = s->dt == QS_C128 ? 4 : 5;
+    if (mode == QS_MODE_PLAIN || (mode == QS_MODE_FUSED && s->n < rb)) {
+        for (size_t i = 0; i < ngates; ++i)
+            if (qs_status st = launch_plain_gate(s, gates[i])) return st;
+        return QS_OK;
+    }
+    if (mode == QS_MODE_FUSED) {
+        if (opts && opts->tile_log2 && (opts->tile_log2 < rb || opts->tile_log2 > rb + 8))
+            return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside %d..%d", opts->tile_log2, rb, rb + 8);
+        const Plan *plan;
+        const void *dev;
+        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev)) return st;
+        return run_fused_plan(s, *plan, dev);
+    }
+    if (mode == QS_MODE_FUSED_TC) {
+        return set_error(QS_ERR_UNSUPPORTED, "tensor-core mode is not built yet");
+    }
+    return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+}
+
+extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
+                                        const qs_opts *opts)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
+    const int mode = opts ? opts->mode : QS_MODE_FUSED;
+    const int rb = s->dt == QS_C128 ? 4 : 5;
+    if (ngates == 0 || mode == QS_MODE_PLAIN || s->n < rb) return QS_OK;
+    if (mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
+        return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    DeviceGuard g(s->device);
+    const Plan *plan;
+    const void *dev;
+    return get_plan(s, gates, ngates, opts, &plan, &dev);
+}
+
+extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (!out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(s->device);
+    const uint64_t N = 1ULL << s->n;
+    const size_t esz = out_is_fp64 ? 8 : 4;
+    if (is_device_ptr(out)) return launch_probabilities(s, out, out_is_fp64, 0, N);
+    // host output: convert in device chunks and copy back
+    const uint64_t chunk = N < (1ULL << 24) ? N : (1ULL << 24);
+    void *buf = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&buf, chunk * esz, s->stream));
+    qs_status st = QS_OK;
+    for (uint64_t f = 0; f < N && !st; f += chunk) {
+        st = launch_probabilities(s, buf, out_is_fp64, f, chunk);
+        if (st) break;
+        cudaError_t e = cudaMemcpyAsync((char *)out + f * esz, buf, chunk * esz, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = set_error(QS_ERR_CUDA, "probabilities copy: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(buf, s->stream);
+    cudaStreamSynchronize(s->stream);
+    return st;
+}
+
+extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (k && !out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(s->device);
+    if (k == 0) return sampler_run(s, 0, seed, nullptr);
+    if (is_device_ptr(out)) return sampler_run(s, k, seed, out);
+    uint64_t *buf = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync((void **)&buf, k * sizeof(uint64_t), s->stream));
+    qs_status st = sampler_run(s, k, seed, buf);
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(out, buf, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = set_error(QS_ERR_CUDA, "sample copy: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(buf, s->stream);
+    cudaStreamSynchronize(s->stream);
+    return st;
+}
+
+extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples, uint64_t m,
+                                      double *ce, double *delta_h)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (m == 0) return set_error(QS_ERR_INVALID_ARG, "empty sample");
+    if (!samples) return set_error(QS_ERR_INVALID_ARG, "samples is NULL");
+    DeviceGuard g(s->device);
+    double c = 0;
+    qs_status st;
+    if (is_device_ptr(samples)) {
+        st = cross_entropy_run(s, samples, m, &c);
+    } else {
+        uint64_t *buf = nullptr;
+        QS_CUDA_TRY(cudaMallocAsync((void **)&buf, m * sizeof(uint64_t), s->stream));
+        cudaError_t e = cudaMemcpyAsync(buf, samples, m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+        st = e == cudaSuccess ? cross_entropy_run(s, buf, m, &c)
+                              : set_error(QS_ERR_CUDA, "sample upload: %s", cudaGetErrorString(e));
+        cudaFreeAsync(buf, s->stream);
+        cudaStreamSynchronize(s->stream);
+    }
+    if (st) return st;
+    const double euler_gamma = 0.57721566490153286061;
+    if (ce) *ce = c;
+    if (delta_h) *delta_h = s->n * std::log(2.0) + euler_gamma - c;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments, double *entropy,
+                                   double *uniform_ce, double *norm)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (kmax < 0 || kmax > kMaxMoments) return set_error(QS_ERR_INVALID_ARG, "kmax %d outside 0..%d", kmax, kMaxMoments);
+    if (kmax > 0 && !moments) return set_error(QS_ERR_INVALID_ARG, "moments is NULL");
+    DeviceGuard g(s->device);
+    return stats_moments(s, kmax, moments, entropy, uniform_ce, norm);
+}
+
+extern "C" qs_status qs_state_copy_out(const qs_state *s, void *host_amps)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (!host_amps) return set_error(QS_ERR_INVALID_ARG, "host_amps is NULL");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
+    QS_CUDA_TRY(cudaMemcpyAsync(host_amps, s->amps, bytes, cudaMemcpyDefault, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_copy_in(qs_state *s, const void *host_amps)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (!host_amps) return set_error(QS_ERR_INVALID_ARG, "host_amps is NULL");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
+    QS_CUDA_TRY(cudaMemcpyAsync(s->amps, host_amps, bytes, cudaMemcpyDefault, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}

@@ -1,0 +1,55 @@
+// qs_device.cuh -- device-side helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+template <typename R> struct V2T;
+template <> struct V2T<float> { using T = float2; };
+template <> struct V2T<double> { using T = double2; };
+
+template <typename V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    V r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Inserts a zero bit at position q of j.
+__device__ __forceinline__ uint64_t insert_zero(uint64_t j, int q)
+{
+    uint64_t lo = j & ((1ULL << q) - 1);
+    return ((j >> q) << (q + 1)) | lo;
+}
+
+#define QS_CUDA_TRY(expr)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess)                                                   \
+            return set_error(QS_ERR_CUDA, "%s failed: %s (%s:%d)", #expr,       \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);        \
+    } while (0)
+
+#define QS_LAUNCH_CHECK()                                                        \
+    do {                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                     \
+        if (e_ != cudaSuccess)                                                   \
+            return set_error(QS_ERR_CUDA, "kernel launch failed: %s (%s:%d)",   \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);        \
+    } while (0)
+
+inline int grid_for(uint64_t work, int threads, int num_sms, int per_sm = 8)
+{
+    uint64_t b = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms * per_sm;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace qs

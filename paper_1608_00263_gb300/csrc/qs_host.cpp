@@ -1,0 +1,496 @@
+// qs_host.cpp -- host-side parts of the library: error strings, gate
+// definitions and validation, the random-circuit generator, and the fused
+// pass planner.  No CUDA calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+qs_status set_error(qs_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+size_t dtype_bytes(qs_dtype dt) { return dt == QS_C128 ? 16 : 8; }
+
+// ---------------------------------------------------------------------------
+// gates (Sec. "Convergence to Porter-Thomas": H, X^1/2 and Y^1/2 as pi/2
+// rotations, T = diag(1, e^{i pi/4}), CZ = diag(1,1,1,-1); parameterised
+// R_P(theta) = exp(-i theta/2 P) and CPHASE(phi) = diag(1,1,1,e^{i phi}))
+// ---------------------------------------------------------------------------
+bool gate_is_two_qubit(int kind) { return kind == QS_CZ || kind == QS_CPHASE; }
+
+bool gate_is_diagonal(int kind)
+{
+    return kind == QS_T || kind == QS_CZ || kind == QS_RZ || kind == QS_CPHASE;
+}
+
+void gate_matrix(int kind, double theta, Cplx u[4])
+{
+    const double h = std::sqrt(0.5);
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    for (int i = 0; i < 4; ++i) u[i] = {0, 0};
+    switch (kind) {
+    case QS_H: u[0] = {h, 0}; u[1] = {h, 0}; u[2] = {h, 0}; u[3] = {-h, 0}; break;
+    case QS_X_HALF: u[0] = {h, 0}; u[1] = {0, -h}; u[2] = {0, -h}; u[3] = {h, 0}; break;
+    case QS_Y_HALF: u[0] = {h, 0}; u[1] = {-h, 0}; u[2] = {h, 0}; u[3] = {h, 0}; break;
+    case QS_T: u[0] = {1, 0}; u[3] = {h, h}; break;
+    case QS_CZ: u[0] = {1, 0}; u[3] = {-1, 0}; break;
+    case QS_RX: u[0] = {c, 0}; u[1] = {0, -s}; u[2] = {0, -s}; u[3] = {c, 0}; break;
+    case QS_RY: u[0] = {c, 0}; u[1] = {-s, 0}; u[2] = {s, 0}; u[3] = {c, 0}; break;
+    case QS_RZ: u[0] = {c, -s}; u[3] = {c, s}; break;
+    case QS_CPHASE: u[0] = {1, 0}; u[3] = {std::cos(theta), std::sin(theta)}; break;
+    default: break;
+    }
+}
+
+qs_status validate_gates(int n, const qs_gate *g, size_t ng)
+{
+    if (ng && !g) return set_error(QS_ERR_INVALID_ARG, "gates is NULL but ngates = %zu", ng);
+    for (size_t i = 0; i < ng; ++i) {
+        if (g[i].kind > QS_CPHASE)
+            return set_error(QS_ERR_INVALID_ARG, "gate %zu: unknown kind %u", i, g[i].kind);
+        if (g[i].q0 >= n)
+            return set_error(QS_ERR_INVALID_ARG, "gate %zu: qubit %u >= n = %d", i, g[i].q0, n);
+        if (gate_is_two_qubit(g[i].kind)) {
+            if (g[i].q1 >= n)
+                return set_error(QS_ERR_INVALID_ARG, "gate %zu: qubit %u >= n = %d", i, g[i].q1, n);
+            if (g[i].q0 == g[i].q1)
+                return set_error(QS_ERR_INVALID_ARG, "gate %zu: two-qubit gate on equal qubits %u",
+                                 i, g[i].q0);
+        }
+        if (!std::isfinite(g[i].theta))
+            return set_error(QS_ERR_INVALID_ARG, "gate %zu: non-finite angle", i);
+    }
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// random circuits (Sec. "Convergence to Porter-Thomas")
+// ---------------------------------------------------------------------------
+namespace {
+
+// SplitMix64 (Steele, Lea & Flood 2014): Weyl step by the golden gamma,
+// then the 64-bit finaliser.
+struct SplitMix64 {
+    uint64_t x;
+    explicit SplitMix64(uint64_t seed) : x(seed) {}
+    uint64_t next()
+    {
+        x += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = x;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+};
+
+struct Grid {
+    int rows, cols;
+    std::vector<int> qubit;   // site -> qubit or -1
+    int n = 0;
+    Grid(int r, int c, const uint8_t *dead) : rows(r), cols(c), qubit(r * c, -1)
+    {
+        for (int s = 0; s < r * c; ++s)
+            if (!(dead && dead[s])) qubit[s] = n++;
+    }
+    // CZ pairs of one of the eight layouts.  Layout order H0 H2 V0 V2 H1 H3
+    // V1 V3; H_a: edges (r,c)-(r,c+1) with (c + 2r) % 4 == a; V_a: edges
+    // (r,c)-(r+1,c) with (r + 2c) % 4 == a.
+    std::vector<std::pair<int, int>> layout(int which) const
+    {
+        static const bool vertical[8] = {false, false, true, true, false, false, true, true};
+        static const int offset[8] = {0, 2, 0, 2, 1, 3, 1, 3};
+        std::vector<std::pair<int, int>> out;
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c) {
+                int r2 = r, c2 = c;
+                if (vertical[which]) {
+                    if ((r + 2 * c) % 4 != offset[which]) continue;
+                    r2 = r + 1;
+                } else {
+                    if ((c + 2 * r) % 4 != offset[which]) continue;
+                    c2 = c + 1;
+                }
+                if (r2 >= rows || c2 >= cols) continue;
+                int a = qubit[r * cols + c], b = qubit[r2 * cols + c2];
+                if (a < 0 || b < 0) continue;
+                out.emplace_back(std::min(a, b), std::max(a, b));
+            }
+        return out;
+    }
+};
+
+}  // namespace
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" const char *qs_last_error(void) { return last_error_cstr(); }
+
+extern "C" qs_status qs_circuit_generate(int rows, int cols, const uint8_t *dead,
+                                         int depth, uint64_t seed, qs_gate *out,
+                                         size_t *ngates)
+{
+    clear_error();
+    if (rows < 1 || cols < 1 || rows * (int64_t)cols > 4096)
+        return set_error(QS_ERR_INVALID_ARG, "bad grid %d x %d", rows, cols);
+    if (depth < 0) return set_error(QS_ERR_INVALID_ARG, "negative depth");
+    if (!ngates) return set_error(QS_ERR_INVALID_ARG, "ngates is NULL");
+    Grid grid(rows, cols, dead);
+    if (grid.n < 1 || grid.n > 64)
+        return set_error(QS_ERR_INVALID_ARG, "grid has %d live sites (1..64 allowed)", grid.n);
+    const size_t cap = out ? *ngates : 0;
+    size_t count = 0;
+    auto emit = [&](int kind, int a, int b, int cycle) {
+        if (out && count < cap) {
+            qs_gate &g = out[count];
+            g.kind = (uint8_t)kind; g.q0 = (uint8_t)a; g.q1 = (uint8_t)b; g.pad = 0;
+            g.cycle = (uint32_t)cycle; g.theta = 0.0;
+        }
+        ++count;
+    };
+    SplitMix64 rng(seed);
+    const int n = grid.n;
+    std::vector<char> busy_prev(n, 0), busy(n, 0);
+    std::vector<int> previous(n, -1);   // last single-qubit gate since H
+    for (int q = 0; q < n; ++q) emit(QS_H, q, 0, 0);
+    for (int t = 1; t <= depth; ++t) {
+        std::fill(busy.begin(), busy.end(), 0);
+        for (auto &e : grid.layout((t - 1) % 8)) {
+            emit(QS_CZ, e.first, e.second, t);
+            busy[e.first] = busy[e.second] = 1;
+        }
+        for (int q = 0; q < n; ++q) {
+            if (!busy_prev[q] || busy[q]) continue;
+            int kind;
+            if (previous[q] < 0) {
+                kind = QS_T;
+            } else {
+                int choices[2], m = 0;
+                for (int k : {QS_X_HALF, QS_Y_HALF, QS_T})
+                    if (k != previous[q]) choices[m++] = k;
+                kind = choices[rng.next() >> 63];
+            }
+            emit(kind, q, 0, t);
+            previous[q] = kind;
+        }
+        busy_prev.swap(busy);
+    }
+    if (out && count > cap) {
+        *ngates = count;
+        return set_error(QS_ERR_INVALID_ARG, "output holds %zu gates, circuit has %zu", cap, count);
+    }
+    *ngates = count;
+    return QS_OK;
+}
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// planner
+//
+// A pass keeps t qubits ("tile qubits", always including the c lowest for
+// coalesced runs) local: every CTA owns the 2^t amplitudes that share the
+// values of the other n - t qubits.  Non-diagonal gates need their qubit in
+// the tile; diagonal gates (T, CZ, RZ, CPHASE) never do, because the bits of
+// out-of-tile qubits are constant per tile (the appendix's observation that
+// diagonal gates need no communication).  A pass applies, in circuit order,
+// every pending gate whose qubits are not blocked; a gate that cannot be
+// applied blocks its qubits for the rest of the pass, so the applied set is
+// closed under dependencies.  Inside a pass the same rule with r "register"
+// qubits splits the gates into phases; each phase is one shared-memory round
+// trip of the tile.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct PGate {
+    int kind;
+    int q0, q1;
+    bool two, diag;
+    double theta;
+};
+
+// Returns the indices (in order) of gates applicable with the local set
+// `local` (bitmask over qubits), among gates not yet done.
+static void collect(const std::vector<PGate> &g, const std::vector<int> &cand,
+                    const std::vector<char> &done, uint64_t local,
+                    std::vector<int> *out, int *count)
+{
+    uint64_t blocked = 0;
+    int cnt = 0;
+    if (out) out->clear();
+    for (int i : cand) {
+        if (done[i]) continue;
+        const PGate &x = g[i];
+        uint64_t qm = (1ULL << x.q0) | (x.two ? (1ULL << x.q1) : 0);
+        bool ok = !(qm & blocked) && (x.diag || (qm & ~local) == 0);
+        if (ok) {
+            ++cnt;
+            if (out) out->push_back(i);
+        } else {
+            blocked |= qm;
+        }
+    }
+    *count = cnt;
+}
+
+// First pending non-diagonal gate index per qubit (large if none).
+static void first_pending(const std::vector<PGate> &g, const std::vector<int> &cand,
+                          const std::vector<char> &done, int n, std::vector<int> *first)
+{
+    first->assign(n, 1 << 30);
+    for (int i : cand) {
+        if (done[i] || g[i].diag) continue;
+        int q = g[i].q0;
+        if ((*first)[q] > i) (*first)[q] = i;
+    }
+}
+
+// Greedy choice of `want` qubits added to `base` from `pool`, maximising the
+// number of applicable gates; ties go to the qubit whose next non-diagonal
+// gate is earliest.
+static uint64_t choose_local(const std::vector<PGate> &g, const std::vector<int> &cand,
+                             const std::vector<char> &done, int n, uint64_t base,
+                             uint64_t pool, int want)
+{
+    std::vector<int> first;
+    first_pending(g, cand, done, n, &first);
+    uint64_t local = base;
+    for (int step = 0; step < want; ++step) {
+        int best_q = -1, best_cnt = -1, best_first = 1 << 30;
+        for (int q = 0; q < n; ++q) {
+            if (!((pool >> q) & 1) || ((local >> q) & 1)) continue;
+            int cnt;
+            collect(g, cand, done, local | (1ULL << q), nullptr, &cnt);
+            if (cnt > best_cnt || (cnt == best_cnt && first[q] < best_first)) {
+                best_q = q; best_cnt = cnt; best_first = first[q];
+            }
+        }
+        if (best_q < 0) break;
+        local |= 1ULL << best_q;
+    }
+    return local;
+}
+
+static int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
+{
+    PlanParams pp;
+    pp.n = n;
+    pp.mode = o ? o->mode : QS_MODE_FUSED;
+    pp.r = dt == QS_C128 ? 4 : 5;
+    int tile = dt == QS_C128 ? 12 : 13;
+    if (o && o->tile_log2 > 0) tile = o->tile_log2;
+    pp.t = std::min(tile, n);
+    pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t);
+    pp.k = (o && o->k > 0) ? o->k : 6;
+    if (pp.mode == QS_MODE_FUSED_TC) pp.r = pp.k;
+    pp.r = std::min(pp.r, pp.t);
+    return pp;
+}
+
+double plan_bytes(const Plan &p, qs_dtype dt)
+{
+    return (double)p.passes.size() * 2.0 * std::ldexp(1.0, p.n) * (double)dtype_bytes(dt);
+}
+
+qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *out)
+{
+    const int n = pp.n;
+    if (pp.t < 1 || pp.t > kMaxTileBits || pp.t > n || pp.r < 1 || pp.r > kMaxRegBits ||
+        pp.r > pp.t || pp.c < 0 || pp.c > pp.t)
+        return set_error(QS_ERR_INVALID_ARG, "bad plan parameters t=%d r=%d c=%d n=%d",
+                         pp.t, pp.r, pp.c, n);
+    std::vector<PGate> g(ng);
+    for (size_t i = 0; i < ng; ++i) {
+        g[i].kind = gin[i].kind;
+        g[i].q0 = gin[i].q0;
+        g[i].q1 = gin[i].q1;
+        g[i].two = gate_is_two_qubit(gin[i].kind);
+        g[i].diag = gate_is_diagonal(gin[i].kind);
+        g[i].theta = gin[i].theta;
+    }
+    Plan &P = *out;
+    P = Plan();
+    P.n = n; P.t = pp.t; P.r = pp.r; P.c = pp.c; P.mode = pp.mode;
+    P.gates = (int)ng;
+
+    std::vector<char> done(ng, 0);
+    std::vector<int> all(ng);
+    for (size_t i = 0; i < ng; ++i) all[i] = (int)i;
+    size_t remaining = ng;
+    const uint64_t allq = (n == 64) ? ~0ULL : ((1ULL << n) - 1);
+    const uint64_t low = (pp.c >= 64) ? ~0ULL : ((1ULL << pp.c) - 1);
+    std::vector<int> pass_gates, phase_gates;
+    while (remaining) {
+        uint64_t local = choose_local(g, all, done, n, low & allq, allq & ~low, pp.t - pp.c);
+        int cnt;
+        collect(g, all, done, local, &pass_gates, &cnt);
+        if (cnt == 0) return set_error(QS_ERR_INVALID_ARG, "planner made no progress");
+        DevPass dp;
+        std::memset(&dp, 0, sizeof dp);
+        dp.t = popcount64(local);
+        dp.n = n;
+        dp.r = std::min(pp.r, dp.t);
+        dp.phase_begin = (int)P.phases.size();
+        dp.ngates = cnt;
+        int tb = 0, gb = 0;
+        int tile_bit_of[64];
+        for (int q = 0; q < n; ++q) {
+            if ((local >> q) & 1) { tile_bit_of[q] = tb; dp.L[tb++] = (uint8_t)q; }
+            else { tile_bit_of[q] = -1; dp.G[gb++] = (uint8_t)q; }
+        }
+        double gre = 1.0, gim = 0.0;
+        int deferred = 0;
+        // phases inside the pass
+        std::vector<char> pdone(ng, 1);
+        for (int i : pass_gates) pdone[i] = 0;
+        size_t prem = pass_gates.size();
+        while (prem) {
+            uint64_t reg = choose_local(g, pass_gates, pdone, n, 0, local, dp.r);
+            collect(g, pass_gates, pdone, reg, &phase_gates, &cnt);
+            if (cnt == 0) return set_error(QS_ERR_INVALID_ARG, "planner made no phase progress");
+            DevPhase ph;
+            std::memset(&ph, 0, sizeof ph);
+            int reg_bit_of[64];
+            int j = 0;
+            for (int q = 0; q < n; ++q) reg_bit_of[q] = -1;
+            for (int q = 0; q < n; ++q)
+                if ((reg >> q) & 1) { reg_bit_of[q] = j; ph.R[j++] = (uint8_t)tile_bit_of[q]; }
+            // pad with unused tile bits so the phase always has dp.r register bits
+            for (int b = 0; j < dp.r && b < dp.t; ++b) {
+                bool used = false;
+                for (int i2 = 0; i2 < j; ++i2) used |= ph.R[i2] == b;
+                if (!used) ph.R[j++] = (uint8_t)b;
+            }
+            std::sort(ph.R, ph.R + dp.r);
+            for (int q = 0; q < n; ++q) reg_bit_of[q] = -1;
+            for (int i2 = 0; i2 < dp.r; ++i2) reg_bit_of[dp.L[ph.R[i2]]] = i2;
+            ph.op_begin = (int)P.ops.size();
+            for (int gi : phase_gates) {
+                const PGate &x = g[gi];
+                DevOp op;
+                std::memset(&op, 0, sizeof op);
+                if (!x.diag) {
+                    op.a = (uint8_t)reg_bit_of[x.q0];
+                    switch (x.kind) {
+                    case QS_H: op.type = OP_H; ++deferred; break;
+                    case QS_X_HALF: op.type = OP_XH; ++deferred; break;
+                    case QS_Y_HALF: op.type = OP_YH; ++deferred; break;
+                    default: {
+                        op.type = OP_DENSE;
+                        Cplx u[4];
+                        gate_matrix(x.kind, x.theta, u);
+                        for (int e = 0; e < 4; ++e) { op.m[2 * e] = u[e].re; op.m[2 * e + 1] = u[e].im; }
+                    }
+                    }
+                } else {
+                    int qs2[2] = {x.q0, x.q1};
+                    for (int e = 0; e < (x.two ? 2 : 1); ++e) {
+                        int q = qs2[e];
+                        if (reg_bit_of[q] >= 0) op.rmask |= (uint8_t)(1u << reg_bit_of[q]);
+                        else op.qmask |= 1ULL << q;
+                    }
+                    if (x.kind == QS_CZ) {
+                        op.type = OP_NEG;
+                    } else {
+                        op.type = OP_PHASE;
+                        double ang;
+                        if (x.kind == QS_T) {
+                            ang = M_PI / 4;
+                        } else if (x.kind == QS_RZ) {
+                            // diag(e^{-i th/2}, e^{i th/2}) = e^{-i th/2} diag(1, e^{i th})
+                            ang = x.theta;
+                            double c = std::cos(-x.theta / 2), s = std::sin(-x.theta / 2);
+                            double nr = gre * c - gim * s, ni = gre * s + gim * c;
+                            gre = nr; gim = ni;
+                        } else {
+                            ang = x.theta;   // CPHASE
+                        }
+                        op.m[0] = std::cos(ang);
+                        op.m[1] = std::sin(ang);
+                        if (x.kind == QS_T) { op.m[0] = std::sqrt(0.5); op.m[1] = std::sqrt(0.5); }
+                    }
+                }
+                P.ops.push_back(op);
+                pdone[gi] = 1;
+                --prem;
+            }
+            ph.op_end = (int)P.ops.size();
+            P.phases.push_back(ph);
+            ++dp.nphases;
+        }
+        for (int i : pass_gates) { done[i] = 1; --remaining; }
+        double sc = std::ldexp(1.0, -(deferred / 2));
+        if (deferred & 1) sc *= std::sqrt(0.5);
+        dp.deferred = deferred;
+        dp.gscale_re = gre * sc;
+        dp.gscale_im = gim * sc;
+        P.passes.push_back(dp);
+    }
+    return QS_OK;
+}
+
+}  // namespace qs
+
+extern "C" qs_status qs_plan_circuit(int n, qs_dtype dt, const qs_gate *gates,
+                                     size_t ngates, const qs_opts *opts,
+                                     qs_plan_stats *stats)
+{
+    clear_error();
+    if (n < 1 || n > kMaxQubits) return set_error(QS_ERR_INVALID_ARG, "n = %d out of range 1..%d", n, kMaxQubits);
+    if (dt != QS_C64 && dt != QS_C128) return set_error(QS_ERR_INVALID_ARG, "bad dtype");
+    if (!stats) return set_error(QS_ERR_INVALID_ARG, "stats is NULL");
+    qs_status st = validate_gates(n, gates, ngates);
+    if (st) return st;
+    int mode = opts ? opts->mode : QS_MODE_FUSED;
+    std::memset(stats, 0, sizeof *stats);
+    stats->gates = (int)ngates;
+    if (mode == QS_MODE_PLAIN) {
+        stats->passes = (int)ngates;
+        double N = std::ldexp(1.0, n) * (double)dtype_bytes(dt);
+        for (size_t i = 0; i < ngates; ++i) {
+            int k = gates[i].kind;
+            stats->bytes += k == QS_T ? N : (k == QS_CZ || k == QS_CPHASE) ? 0.5 * N : 2.0 * N;
+        }
+        return QS_OK;
+    }
+    if (mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
+        return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    PlanParams pp = default_plan_params(n, dt, opts);
+    Plan plan;
+    st = build_plan(pp, gates, ngates, &plan);
+    if (st) return st;
+    stats->passes = (int)plan.passes.size();
+    stats->phases = (int)plan.phases.size();
+    stats->ops = (int)plan.ops.size();
+    stats->tile_log2 = pp.t;
+    stats->reg_log2 = pp.r;
+    stats->bytes = plan_bytes(plan, dt);
+    return QS_OK;
+}

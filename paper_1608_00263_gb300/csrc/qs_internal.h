@@ -1,0 +1,166 @@
+// qs_internal.h -- private declarations shared by the library's translation
+// units: the state handle, the planner's device plan format, and the kernel
+// launchers.  Not part of the public ABI (include/qs.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qs.h"
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+struct CUstream_st;
+typedef CUstream_st *cudaStream_t;
+#endif
+
+namespace qs {
+
+constexpr int kMaxQubits = 34;
+constexpr int kMaxMoments = 10;
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message, returned status)
+// ---------------------------------------------------------------------------
+qs_status set_error(qs_status st, const char *fmt, ...);
+void clear_error();
+const char *last_error_cstr();
+
+// ---------------------------------------------------------------------------
+// Gate helpers (host)
+// ---------------------------------------------------------------------------
+struct Cplx {
+    double re, im;
+};
+
+bool gate_is_two_qubit(int kind);
+bool gate_is_diagonal(int kind);
+// 2x2 matrix (row-major u00 u01 u10 u11) of a gate; for two-qubit kinds the
+// matrix applied to the target when the control bit is set.
+void gate_matrix(int kind, double theta, Cplx u[4]);
+qs_status validate_gates(int n, const qs_gate *g, size_t ng);
+
+// ---------------------------------------------------------------------------
+// Fused-pass plan (built on the host, executed by the fused kernels)
+// ---------------------------------------------------------------------------
+enum OpType : uint8_t {
+    OP_DENSE = 0,   // general 2x2 complex matrix on register bit `a`
+    OP_H = 1,       // [[1, 1], [1, -1]]      (1/sqrt2 deferred to pass end)
+    OP_XH = 2,      // [[1, -i], [-i, 1]]     (1/sqrt2 deferred)
+    OP_YH = 3,      // [[1, -1], [1, 1]]      (1/sqrt2 deferred)
+    OP_PHASE = 4,   // multiply by m[0] + i m[1] where all bits of the op's
+                    // qubit set are 1 (register part rmask, rest qmask)
+    OP_NEG = 5,     // multiply by -1, same selection as OP_PHASE
+    OP_MATRIX = 6,  // tensor-core dense block (TC mode only): index of the
+                    // block matrix in `a`
+};
+
+struct DevOp {          // 80 bytes
+    uint8_t type;
+    uint8_t a;          // register bit (dense ops) / block index (OP_MATRIX)
+    uint8_t rmask;      // register-slot bits of the selection (phase ops)
+    uint8_t pad0;
+    uint32_t pad1;
+    uint64_t qmask;     // qubit-index bits of the selection outside the
+                        // register set (phase ops)
+    double m[8];        // matrix u00 u01 u10 u11 as (re, im) pairs, or phase
+};
+
+constexpr int kMaxTileBits = 16;
+constexpr int kMaxRegBits = 8;
+
+struct DevPhase {       // 16 bytes
+    uint8_t R[kMaxRegBits];  // tile bit of each register bit
+    int32_t op_begin, op_end;
+};
+
+struct DevPass {
+    int32_t t;              // tile bits
+    int32_t r;              // register bits per phase (or block bits, TC)
+    int32_t nphases;
+    int32_t phase_begin;    // index into the plan's phase array
+    int32_t ngates;         // gates this pass applies
+    int32_t deferred;       // number of deferred 1/sqrt2 factors
+    int32_t n;              // qubits of the state
+    int32_t pad;
+    double gscale_re, gscale_im;  // pass-wide factor applied at the end
+    uint8_t L[kMaxTileBits];      // qubit of each tile bit (ascending)
+    uint8_t G[64];                // qubits outside the tile (ascending)
+};
+
+struct Plan {
+    int n = 0;
+    int t = 0, r = 0, c = 0;
+    int mode = 0;
+    std::vector<DevPass> passes;
+    std::vector<DevPhase> phases;
+    std::vector<DevOp> ops;
+    std::vector<double> tc_blocks;   // TC mode: realified block matrices
+    int gates = 0;
+};
+
+struct PlanParams {
+    int n;
+    int t;           // tile bits (<= n)
+    int r;           // register bits per phase
+    int c;           // low qubits always inside the tile (coalescing)
+    int mode;        // QS_MODE_FUSED or QS_MODE_FUSED_TC
+    int k;           // TC block bits
+};
+
+qs_status build_plan(const PlanParams &pp, const qs_gate *g, size_t ng, Plan *out);
+PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o);
+double plan_bytes(const Plan &p, qs_dtype dt);
+
+// ---------------------------------------------------------------------------
+// State handle
+// ---------------------------------------------------------------------------
+struct DevicePlanCache {
+    uint64_t key = 0;          // hash of (gates, options)
+    size_t ngates = 0;
+    void *dev = nullptr;       // passes | phases | ops | blocks on device
+    size_t dev_bytes = 0;
+    Plan plan;
+};
+
+}  // namespace qs
+
+struct qs_state {
+    int n;
+    qs_dtype dt;
+    void *amps;              // device, 2^n amplitudes
+    bool owns;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    // statistics / sampler workspace (device)
+    double *ws_f64;          // reduction partials
+    size_t ws_f64_count;
+    uint64_t *ws_u64;        // small integer scratch (flags, counters)
+    qs::DevicePlanCache plan_cache;
+};
+
+namespace qs {
+
+// Launchers (defined in the .cu files).  All are asynchronous on `st` and
+// return QS_ERR_CUDA (with message) on a launch failure.
+qs_status launch_init_zero(qs_state *s);
+qs_status launch_plain_gate(qs_state *s, const qs_gate &g);
+qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan);
+qs_status run_tc_plan(qs_state *s, const Plan &plan, const void *dev_plan,
+                      int precision);
+qs_status launch_probabilities(const qs_state *s, void *out, int fp64,
+                               uint64_t first, uint64_t count);
+qs_status stats_moments(const qs_state *s, int kmax, double *moments,
+                        double *entropy, double *uniform_ce, double *norm);
+qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed,
+                      uint64_t *dev_out);
+qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples,
+                            uint64_t m, double *ce);
+
+size_t dtype_bytes(qs_dtype dt);
+
+}  // namespace qs

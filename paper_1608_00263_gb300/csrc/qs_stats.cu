@@ -1,0 +1,506 @@
+// qs_stats.cu -- output probabilities, Porter-Thomas statistics, inverse-CDF
+// sampler and sample cross entropy.
+//
+//   probabilities  p_U(x) = |<x|psi>|^2                     (Sec. cqs)
+//   statistics     S = sum p, and for p/S: -sum p ln p (Eq. lps, eu),
+//                  -(1/N) sum ln p (Eq. eue), N^{k-1} sum p^k (normalised
+//                  IPR, Sec. "Convergence to Porter-Thomas")
+//   sampler        x_j = min{x : C_x > u_j C_{N-1}}, C = cumulative p
+//   cross entropy  (1/m) sum_j ln(1/p(x_j)) and Delta H (Eq. ae)
+//
+// Reductions read the state once.  Per element the complex64 path works in
+// FP32 on y = N p (O(1) for Porter-Thomas states), accumulates FP32 partial
+// sums over 128 elements and adds those into FP64 accumulators; the
+// complex128 path is FP64 throughout.  Block partials are combined in a
+// fixed order, so results are deterministic.
+//
+// The sampler never materialises a 2^n array: it keeps one FP64 sum per
+// 256-amplitude chunk (N/32 bytes), scans those, and for each sample
+// rescans one chunk with exactly the arithmetic that produced the chunk's
+// sum.
+#include <cmath>
+
+#include "qs_device.cuh"
+
+namespace qs {
+
+constexpr int kStatThreads = 256;
+constexpr int kStatAcc = 12;   // sum y, sum y ln y, sum ln y, sum y^k (k=2..10)
+constexpr int kChunk = 256;    // sampler chunk (amplitudes)
+
+// ---------------------------------------------------------------------------
+// probabilities
+// ---------------------------------------------------------------------------
+template <typename R, typename O>
+__global__ void k_probs(const typename V2T<R>::T *__restrict__ a, O *__restrict__ out,
+                        uint64_t first, uint64_t count)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        auto v = a[first + i];
+        if (sizeof(O) == 8) {
+            double re = (double)v.x, im = (double)v.y;
+            out[i] = (O)(re * re + im * im);
+        } else {
+            out[i] = (O)(v.x * v.x + v.y * v.y);
+        }
+    }
+}
+
+qs_status launch_probabilities(const qs_state *s, void *out, int fp64, uint64_t first,
+                               uint64_t count)
+{
+    const int th = 256;
+    const int grid = grid_for(count, th, s->num_sms, 16);
+    if (s->dt == QS_C64) {
+        if (fp64) k_probs<float, double><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (double *)out, first, count);
+        else k_probs<float, float><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (float *)out, first, count);
+    } else {
+        if (fp64) k_probs<double, double><<<grid, th, 0, s->stream>>>((const double2 *)s->amps, (double *)out, first, count);
+        else k_probs<double, float><<<grid, th, 0, s->stream>>>((const double2 *)s->amps, (float *)out, first, count);
+    }
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// block reduction helpers (fixed order)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&acc)[K], double *dst)
+{
+    __shared__ double red[kStatThreads / 32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = warp_sum(acc[k]);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0;
+        for (int w = 0; w < kStatThreads / 32; ++w) s += red[w][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+}
+
+// Accumulates one element's contributions.  y = N p.
+template <typename T>
+__device__ __forceinline__ void stat_terms(T y, T (&c)[kStatAcc])
+{
+    T ly = (sizeof(T) == 4) ? (T)__logf((float)y) : (T)log((double)y);
+    c[0] += y;
+    c[1] += (y > (T)0) ? y * ly : (T)0;
+    c[2] += ly;
+    T yk = y;
+#pragma unroll
+    for (int k = 2; k <= 10; ++k) {
+        yk *= y;
+        c[k + 1] += yk;
+    }
+}
+
+// complex64: FP32 per element and per 128-element partial, FP64 across.
+__global__ void __launch_bounds__(kStatThreads)
+k_stats_c64(const float4 *__restrict__ a4, uint64_t nquads, float scaleN, double *__restrict__ part)
+{
+    double acc[kStatAcc];
+#pragma unroll
+    for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    while (w < nquads) {
+        float c[kStatAcc];
+#pragma unroll
+        for (int k = 0; k < kStatAcc; ++k) c[k] = 0.f;
+        double big[kStatAcc];
+        bool any_big = false;
+        for (int it = 0; it < 64 && w < nquads; ++it, w += stride) {
+            float4 v = a4[w];
+            float y0 = (v.x * v.x + v.y * v.y) * scaleN;
+            float y1 = (v.z * v.z + v.w * v.w) * scaleN;
+            // y^10 overflows FP32 above ~2^12.8: such (rare) elements go to FP64
+            if (y0 > 4096.f || y1 > 4096.f) {
+                if (!any_big) {
+#pragma unroll
+                    for (int k = 0; k < kStatAcc; ++k) big[k] = 0;
+                    any_big = true;
+                }
+                double d0 = ((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN;
+                double d1 = ((double)v.z * v.z + (double)v.w * v.w) * (double)scaleN;
+                stat_terms<double>(d0, big);
+                stat_terms<double>(d1, big);
+            } else {
+                stat_terms<float>(y0, c);
+                stat_terms<float>(y1, c);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)c[k];
+        if (any_big) {
+#pragma unroll
+            for (int k = 0; k < kStatAcc; ++k) acc[k] += big[k];
+        }
+    }
+    block_sum_store<kStatAcc>(acc, part + (size_t)blockIdx.x * kStatAcc);
+}
+
+__global__ void __launch_bounds__(kStatThreads)
+k_stats_c128(const double2 *__restrict__ a, uint64_t N, double scaleN, double *__restrict__ part)
+{
+    double acc[kStatAcc];
+#pragma unroll
+    for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        double2 v = a[i];
+        stat_terms<double>((v.x * v.x + v.y * v.y) * scaleN, acc);
+    }
+    block_sum_store<kStatAcc>(acc, part + (size_t)blockIdx.x * kStatAcc);
+}
+
+// Final fixed-order sum of block partials.
+__global__ void k_sum_partials(const double *__restrict__ part, int nblocks, int K, double *__restrict__ out)
+{
+    if (threadIdx.x < K) {
+        double s = 0;
+        for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * K + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *entropy,
+                        double *uniform_ce, double *norm)
+{
+    const uint64_t N = 1ULL << s->n;
+    int grid;
+    double *part = s->ws_f64;
+    if (s->dt == QS_C64 && N >= 2) {
+        grid = grid_for(N / 2, kStatThreads, s->num_sms, 4);
+        k_stats_c64<<<grid, kStatThreads, 0, s->stream>>>((const float4 *)s->amps, N / 2,
+                                                           (float)std::ldexp(1.0, s->n), part);
+    } else if (s->dt == QS_C64) {
+        // a single complex64 amplitude: view it as a one-element FP64 problem
+        return set_error(QS_ERR_UNSUPPORTED, "statistics need n >= 1");
+    } else {
+        grid = grid_for(N, kStatThreads, s->num_sms, 4);
+        k_stats_c128<<<grid, kStatThreads, 0, s->stream>>>((const double2 *)s->amps, N,
+                                                            std::ldexp(1.0, s->n), part);
+    }
+    QS_LAUNCH_CHECK();
+    double *fin = part + (size_t)grid * kStatAcc;
+    k_sum_partials<<<1, 32, 0, s->stream>>>(part, grid, kStatAcc, fin);
+    QS_LAUNCH_CHECK();
+    double h[kStatAcc];
+    QS_CUDA_TRY(cudaMemcpyAsync(h, fin, sizeof h, cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    // Statistics of the normalised distribution p / S, S = sum p: the
+    // arithmetic of the evolution leaves |S - 1| at the rounding level
+    // (systematic for FP32: rounded phase constants have modulus below 1),
+    // and dividing it out keeps that drift out of the entropy, moments and
+    // uniform cross entropy.  With y = N p and Y = sum y = N S:
+    //   H      = -sum (p/S) ln(p/S) = ln S + ln N - (sum y ln y) / Y
+    //   CE_u   = -(1/N) sum ln(p/S) = ln S + ln N - (sum ln y) / N
+    //   M_k    = N^{k-1} sum (p/S)^k = (sum y^k) / (N S^k)
+    const double Nd = (double)N, lnN = s->n * std::log(2.0);
+    const double S = h[0] / Nd;
+    if (norm) *norm = S;
+    const double lnS = S > 0 ? std::log(S) : -INFINITY;
+    if (entropy) *entropy = S > 0 ? lnS + lnN - h[1] / h[0] : 0.0;
+    if (uniform_ce) *uniform_ce = S > 0 ? lnS + lnN - h[2] / Nd : INFINITY;
+    for (int k = 1; k <= kmax; ++k)
+        moments[k - 1] = S > 0 ? (k == 1 ? 1.0 : h[k + 1] / (Nd * std::pow(S, k))) : 0.0;
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sampler
+// ---------------------------------------------------------------------------
+// Lane l of a warp covers elements [8l, 8l+8) of a 256-amplitude chunk.  The
+// lane total is accumulated in the element type's precision (FP32 for
+// complex64, FP64 for complex128) and widened to FP64; the chunk sum is the
+// FP64 inclusive warp scan of the lane totals.  The search kernel repeats
+// exactly this arithmetic, so chunk sums and in-chunk prefixes agree.
+template <typename R>
+__device__ __forceinline__ void lane_probs(const typename V2T<R>::T *a, uint64_t chunk, int lane,
+                                           uint64_t N, R (&p)[8])
+{
+    const uint64_t base = chunk * kChunk + (uint64_t)lane * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint64_t idx = base + i;
+        if (idx < N) {
+            auto v = a[idx];
+            p[i] = v.x * v.x + v.y * v.y;
+        } else {
+            p[i] = (R)0;
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R lane_total(const R (&p)[8])
+{
+    R s = (R)0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += p[i];
+    return s;
+}
+
+__device__ __forceinline__ double warp_incl_scan(double v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// One warp per chunk.
+template <typename R>
+__global__ void k_chunk_sums(const typename V2T<R>::T *__restrict__ a, uint64_t N, uint64_t nchunks,
+                             double *__restrict__ csum)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+        R p[8];
+        lane_probs<R>(a, c, lane, N, p);
+        double incl = warp_incl_scan((double)lane_total<R>(p));
+        if (lane == 31) csum[c] = incl;
+    }
+}
+
+// In-place inclusive FP64 scan of x[0..n): three kernels with a fixed
+// association order.  Segment of one block: kScanSeg elements, kScanPer per
+// thread, sequential inside a thread, warp shuffle scan across threads,
+// shared-memory scan across warps.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 16;
+constexpr int kScanSeg = kScanThreads * kScanPer;
+
+__device__ __forceinline__ double block_excl_scan(double v, double *total)
+{
+    __shared__ double wsum[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double incl = warp_incl_scan(v);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < kScanThreads / 32 ? wsum[lane] : 0.0;
+        double wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) wsum[lane] = wi - w;   // exclusive
+        if (lane == kScanThreads / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    double r = wsum[warp] + (incl - v);
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_block_totals(const double *__restrict__ x, uint64_t n, double *__restrict__ btot)
+{
+    __shared__ double tot;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanSeg + (uint64_t)threadIdx.x * kScanPer;
+    double s = 0;
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) s += x[base + i];
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) btot[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block totals (sequential per thread).
+__global__ void k_scan_totals(double *__restrict__ btot, int nb)
+{
+    __shared__ double tot;
+    const int per = (nb + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per;
+    double s = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < nb) s += btot[b0 + i];
+    double off = block_excl_scan(s, &tot);
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < nb) {
+            double v = btot[b0 + i];
+            btot[b0 + i] = off;
+            off += v;
+        }
+}
+
+__global__ void k_scan_apply(double *__restrict__ x, uint64_t n, const double *__restrict__ boff)
+{
+    __shared__ double tot;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanSeg + (uint64_t)threadIdx.x * kScanPer;
+    double s = 0;
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) s += x[base + i];
+    double off = block_excl_scan(s, &tot) + boff[blockIdx.x];
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) {
+            off += x[base + i];
+            x[base + i] = off;
+        }
+}
+
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t j)
+{
+    uint64_t z = seed + (j + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// One warp handles 32 samples: each lane binary-searches the chunk of its
+// own sample, then the warp rescans each of the 32 chunks in turn.
+template <typename R>
+__global__ void k_sample_search(const typename V2T<R>::T *__restrict__ a, uint64_t N, uint64_t nchunks,
+                                const double *__restrict__ cincl, uint64_t k, uint64_t seed,
+                                uint64_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const double total = cincl[nchunks - 1];
+    for (uint64_t j0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; j0 < k;
+         j0 += warps * 32) {
+        const uint64_t j = j0 + lane;
+        double tloc = 0;
+        uint64_t chunk = 0;
+        if (j < k) {
+            const double u = (double)(splitmix_out(seed, j) >> 11) * (1.0 / 9007199254740992.0);
+            const double target = u * total;
+            uint64_t lo = 0, hi = nchunks - 1;   // cincl[hi] = total > target
+            while (lo < hi) {
+                uint64_t mid = lo + (hi - lo) / 2;
+                if (cincl[mid] > target) hi = mid; else lo = mid + 1;
+            }
+            chunk = lo;
+            tloc = target - (lo ? cincl[lo - 1] : 0.0);
+        }
+        const int cnt = (int)((k - j0) < 32 ? (k - j0) : 32);
+        for (int q = 0; q < cnt; ++q) {
+            const uint64_t c = __shfl_sync(0xffffffffu, chunk, q);
+            const double tq = __shfl_sync(0xffffffffu, tloc, q);
+            R p[8];
+            lane_probs<R>(a, c, lane, N, p);
+            const R lt = lane_total<R>(p);
+            const double incl = warp_incl_scan((double)lt);
+            const double excl = incl - (double)lt;
+            unsigned hit = __ballot_sync(0xffffffffu, incl > tq);
+            unsigned nz = __ballot_sync(0xffffffffu, lt > (R)0);
+            int L = hit ? __ffs(hit) - 1 : 31 - __clz(nz);   // rounding edge: last non-empty lane
+            uint64_t res = 0;
+            if (lane == L) {
+                R acc = (R)0;
+                int pick = -1, last_nz = -1;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    acc += p[i];
+                    if (p[i] > (R)0) last_nz = i;
+                    if (pick < 0 && p[i] > (R)0 && excl + (double)acc > tq) pick = i;
+                }
+                if (pick < 0) pick = last_nz;
+                res = c * kChunk + (uint64_t)L * 8 + (uint64_t)pick;
+            }
+            res = __shfl_sync(0xffffffffu, res, L);
+            if (lane == q) out[j0 + q] = res;
+        }
+    }
+}
+
+qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *dev_out)
+{
+    const uint64_t N = 1ULL << s->n;
+    const uint64_t nchunks = (N + kChunk - 1) / kChunk;
+    const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
+    const size_t bytes = (nchunks + nblk + 1) * sizeof(double);
+    double *csum = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync((void **)&csum, bytes, s->stream));
+    double *btot = csum + nchunks;
+    qs_status st = QS_OK;
+    const int th = 256;
+    const int g1 = grid_for(nchunks * 32, th, s->num_sms, 16);
+    if (s->dt == QS_C64)
+        k_chunk_sums<float><<<g1, th, 0, s->stream>>>((const float2 *)s->amps, N, nchunks, csum);
+    else
+        k_chunk_sums<double><<<g1, th, 0, s->stream>>>((const double2 *)s->amps, N, nchunks, csum);
+    k_scan_block_totals<<<(unsigned)nblk, kScanThreads, 0, s->stream>>>(csum, nchunks, btot);
+    k_scan_totals<<<1, kScanThreads, 0, s->stream>>>(btot, (int)nblk);
+    k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, s->stream>>>(csum, nchunks, btot);
+    double total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, csum + nchunks - 1, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        st = set_error(QS_ERR_CUDA, "sampler scan failed: %s", cudaGetErrorString(e));
+    } else if (!(total > 0) || !std::isfinite(total)) {
+        st = set_error(QS_ERR_INVALID_ARG, "state has zero or non-finite norm (%g)", total);
+    } else if (k > 0) {
+        const int g2 = grid_for((k + 31) / 32 * 32, th, s->num_sms, 16);
+        if (s->dt == QS_C64)
+            k_sample_search<float><<<g2, th, 0, s->stream>>>((const float2 *)s->amps, N, nchunks, csum, k, seed, dev_out);
+        else
+            k_sample_search<double><<<g2, th, 0, s->stream>>>((const double2 *)s->amps, N, nchunks, csum, k, seed, dev_out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) st = set_error(QS_ERR_CUDA, "sampler launch failed: %s", cudaGetErrorString(e));
+    }
+    cudaFreeAsync(csum, s->stream);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// sample cross entropy (Eq. ae)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kStatThreads)
+k_cross_entropy(const typename V2T<R>::T *__restrict__ a, uint64_t N, const uint64_t *__restrict__ x,
+                uint64_t m, double *__restrict__ part, unsigned long long *__restrict__ bad)
+{
+    double acc[1] = {0.0};
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        uint64_t i = x[j];
+        if (i >= N) {
+            atomicAdd(bad, 1ULL);
+            continue;
+        }
+        auto v = a[i];
+        double re = (double)v.x, im = (double)v.y;
+        acc[0] -= log(re * re + im * im);
+    }
+    block_sum_store<1>(acc, part + blockIdx.x);
+}
+
+qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples, uint64_t m, double *ce)
+{
+    const uint64_t N = 1ULL << s->n;
+    const int grid = grid_for(m, kStatThreads, s->num_sms, 4);
+    double *part = s->ws_f64;
+    unsigned long long *bad = (unsigned long long *)s->ws_u64;
+    QS_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s->stream));
+    if (s->dt == QS_C64)
+        k_cross_entropy<float><<<grid, kStatThreads, 0, s->stream>>>((const float2 *)s->amps, N, dev_samples, m, part, bad);
+    else
+        k_cross_entropy<double><<<grid, kStatThreads, 0, s->stream>>>((const double2 *)s->amps, N, dev_samples, m, part, bad);
+    QS_LAUNCH_CHECK();
+    k_sum_partials<<<1, 32, 0, s->stream>>>(part, grid, 1, part + grid);
+    QS_LAUNCH_CHECK();
+    double sum = 0;
+    unsigned long long nbad = 0;
+    QS_CUDA_TRY(cudaMemcpyAsync(&sum, part + grid, sizeof sum, cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA_TRY(cudaMemcpyAsync(&nbad, bad, sizeof nbad, cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (nbad) return set_error(QS_ERR_INVALID_ARG, "%llu sample indices >= 2^n", nbad);
+    *ce = sum / (double)m;
+    return QS_OK;
+}
+
+}  // namespace qs

@@ -1,0 +1,72 @@
+// CPU emulator of the library's fused-pass plan format (test support only).
+//
+// Builds a plan with the library's own host planner and executes it on a
+// double-precision state with the semantics the fused kernels give each
+// op: tiles gathered through the pass's qubit map, phases over register
+// bits, diagonal ops selected by register and qubit masks, deferred 1/sqrt2
+// factors applied at the end of each pass.  Comparing its result with the
+// oracle checks the planner (dependency order, register mapping, masks,
+// scales) without a GPU.
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "../paper_1608_00263_gb300/csrc/qs_internal.h"
+
+using cd = std::complex<double>;
+using namespace qs;
+
+extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, int c,
+                            double *psi_interleaved, int *passes_out)
+{
+    PlanParams pp{n, t, r, c, QS_MODE_FUSED, 6};
+    Plan plan;
+    if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
+    cd *psi = reinterpret_cast<cd *>(psi_interleaved);
+    for (const DevPass &P : plan.passes) {
+        const int T = P.t, ngl = P.n - T;
+        std::vector<cd> tile(size_t(1) << T);
+        for (uint64_t tau = 0; tau < (1ULL << ngl); ++tau) {
+            uint64_t base = 0;
+            for (int i = 0; i < ngl; ++i) base |= ((tau >> i) & 1ULL) << P.G[i];
+            auto addr = [&](uint64_t e) {
+                uint64_t a = base;
+                for (int b = 0; b < T; ++b) a |= ((e >> b) & 1ULL) << P.L[b];
+                return a;
+            };
+            for (uint64_t e = 0; e < tile.size(); ++e) tile[e] = psi[addr(e)];
+            for (int ph = 0; ph < P.nphases; ++ph) {
+                const DevPhase &H = plan.phases[P.phase_begin + ph];
+                for (int o = H.op_begin; o < H.op_end; ++o) {
+                    const DevOp &op = plan.ops[o];
+                    if (op.type == OP_PHASE || op.type == OP_NEG) {
+                        cd f = op.type == OP_NEG ? cd(-1, 0) : cd(op.m[0], op.m[1]);
+                        for (uint64_t e = 0; e < tile.size(); ++e) {
+                            bool sel = (addr(e) & op.qmask) == op.qmask;
+                            for (int j = 0; j < P.r; ++j)
+                                if ((op.rmask >> j) & 1) sel = sel && ((e >> H.R[j]) & 1);
+                            if (sel) tile[e] *= f;
+                        }
+                    } else {
+                        const uint64_t bit = 1ULL << H.R[op.a];
+                        cd u[4];
+                        if (op.type == OP_H) { u[0] = 1; u[1] = 1; u[2] = 1; u[3] = -1; }
+                        else if (op.type == OP_XH) { u[0] = 1; u[1] = cd(0, -1); u[2] = cd(0, -1); u[3] = 1; }
+                        else if (op.type == OP_YH) { u[0] = 1; u[1] = -1; u[2] = 1; u[3] = 1; }
+                        else for (int k = 0; k < 4; ++k) u[k] = cd(op.m[2 * k], op.m[2 * k + 1]);
+                        for (uint64_t e = 0; e < tile.size(); ++e) {
+                            if (e & bit) continue;
+                            cd x = tile[e], y = tile[e | bit];
+                            tile[e] = u[0] * x + u[1] * y;
+                            tile[e | bit] = u[2] * x + u[3] * y;
+                        }
+                    }
+                }
+            }
+            const cd gs(P.gscale_re, P.gscale_im);
+            for (uint64_t e = 0; e < tile.size(); ++e) psi[addr(e)] = tile[e] * gs;
+        }
+    }
+    if (passes_out) *passes_out = (int)plan.passes.size();
+    return 0;
+}

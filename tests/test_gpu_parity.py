@@ -1,0 +1,348 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: state L2 error relative to the oracle <= 1e-5 for complex64
+paths and <= 1e-12 for complex128; entropy and cross entropy within 1e-6
+relative; samples identical to the oracle's for complex128 (up to 1e-5 m
+boundary cases), and for complex64 every sample must satisfy the oracle's
+CDF-inversion condition within the CDF error bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1608_00263_gb300 as qs
+from paper_1608_00263_gb300 import _native
+from paper_1608_00263_gb300 import build as qs_build
+
+pytestmark = pytest.mark.gpu
+
+TOL = {qs.QS_C64: 1e-5, qs.QS_C128: 1e-12}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    qs_build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return _native.lib()
+
+
+def gpu_run(n, gates, dtype, mode=qs.QS_MODE_FUSED, tile=0):
+    h = qs.qs_state_create(n, dtype)
+    try:
+        qs.qs_apply_circuit(h, gates, mode=mode, tile_log2=tile)
+        return qs.qs_state_copy_out(h, n, dtype)
+    finally:
+        qs.qs_state_destroy(h)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a.astype(np.complex128) - b) / np.linalg.norm(b))
+
+
+def random_gates(rng, n, count):
+    g = np.zeros(count, dtype=qs.GATE_DTYPE)
+    for i in range(count):
+        k = int(rng.integers(0, 9)) if n > 1 else int(rng.choice([0, 1, 2, 3, 5, 6, 7]))
+        g[i]["kind"] = k
+        if k in (qs.QS_CZ, qs.QS_CPHASE):
+            a, b = rng.choice(n, size=2, replace=False)
+            g[i]["q0"], g[i]["q1"] = a, b
+        else:
+            g[i]["q0"] = rng.integers(0, n)
+        g[i]["theta"] = rng.uniform(-3, 3)
+    return g
+
+
+# --------------------------------------------------------------------------
+# state evolution
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n", [1, 3, 12, 20])
+def test_create_is_basis_zero(dtype, n):
+    h = qs.qs_state_create(n, dtype)
+    try:
+        psi = qs.qs_state_copy_out(h, n, dtype)
+    finally:
+        qs.qs_state_destroy(h)
+    ref = np.zeros(1 << n)
+    ref[0] = 1
+    assert np.array_equal(psi, ref)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 12, 15])
+def test_plain_random_gates(dtype, n):
+    rng = np.random.default_rng(7 * n + dtype)
+    g = random_gates(rng, n, 150)
+    ref = O.simulate(n, g)
+    psi = gpu_run(n, g, dtype, mode=qs.QS_MODE_PLAIN)
+    assert rel_l2(psi, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n,tile", [(4, 0), (5, 0), (6, 0), (9, 0), (13, 0), (14, 0),
+                                    (16, 9), (17, 12), (18, 0)])
+def test_fused_random_gates(dtype, n, tile):
+    rb = 5 if dtype == qs.QS_C64 else 4
+    if tile and not (rb <= tile <= rb + 8):
+        pytest.skip("tile outside the kernel's range")
+    rng = np.random.default_rng(11 * n + dtype)
+    g = random_gates(rng, n, 250)
+    ref = O.simulate(n, g)
+    psi = gpu_run(n, g, dtype, tile=tile)
+    assert rel_l2(psi, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("mode", [qs.QS_MODE_PLAIN, qs.QS_MODE_FUSED])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_grid_4x5_depth25(dtype, mode, seed):
+    g = qs.qs_circuit_generate(4, 5, 25, seed)
+    ref = O.simulate(20, g)
+    psi = gpu_run(20, g, dtype, mode=mode)
+    assert rel_l2(psi, ref) < TOL[dtype]
+
+
+def test_grid_4x6_depth30_c64():
+    g = qs.qs_circuit_generate(4, 6, 30, 5)
+    ref = O.simulate(24, g)
+    for mode in (qs.QS_MODE_PLAIN, qs.QS_MODE_FUSED):
+        assert rel_l2(gpu_run(24, g, qs.QS_C64, mode=mode), ref) < 1e-5
+
+
+def test_invalid_gate_launches_nothing():
+    n = 10
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        good = qs.qs_circuit_generate(2, 5, 6, 1)
+        bad = good.copy()
+        bad[-1]["q0"] = 10
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_apply_circuit(h, bad)
+        assert e.value.status == _native.QS_ERR_INVALID_ARG
+        psi = qs.qs_state_copy_out(h, n)
+        assert psi[0] == 1 and np.count_nonzero(psi) == 1
+        qs.qs_apply_circuit(h, good[:0])          # empty gate list is a no-op
+        assert qs.qs_state_copy_out(h, n)[0] == 1
+    finally:
+        qs.qs_state_destroy(h)
+
+
+def test_attach_torch_tensor():
+    import torch
+    n = 14
+    amps = torch.zeros(2 << n, dtype=torch.float32, device="cuda")
+    amps[0] = 1
+    g = qs.qs_circuit_generate(2, 7, 12, 4)
+    h = qs.qs_state_attach(n, qs.QS_C64, amps)
+    try:
+        qs.qs_apply_circuit(h, g)
+        torch.cuda.synchronize()
+    finally:
+        qs.qs_state_destroy(h)
+    psi = amps.cpu().numpy().view(np.complex64)
+    assert rel_l2(psi, O.simulate(n, g)) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# statistics, probabilities, sampler, cross entropy
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module", params=[qs.QS_C64, qs.QS_C128])
+def state20(request):
+    dtype = request.param
+    g = qs.qs_circuit_generate(4, 5, 25, 0)
+    ref = O.simulate(20, g)
+    h = qs.qs_state_create(20, dtype)
+    qs.qs_apply_circuit(h, g)
+    yield dtype, h, ref, O.probabilities(ref)
+    qs.qs_state_destroy(h)
+
+
+def test_probabilities(state20):
+    import torch
+    dtype, h, ref, p = state20
+    tol = 1e-5 if dtype == qs.QS_C64 else 1e-12
+    out = torch.empty(1 << 20, dtype=torch.float64, device="cuda")
+    qs.qs_probabilities(h, out, fp64=True)
+    torch.cuda.synchronize()
+    pd = out.cpu().numpy()
+    assert np.sum(np.abs(pd - p)) < 2 * tol
+    host = np.empty(1 << 20, dtype=np.float64)
+    qs.qs_probabilities(h, host, fp64=True)
+    assert np.array_equal(host, pd)
+    host32 = np.empty(1 << 20, dtype=np.float32)
+    qs.qs_probabilities(h, host32, fp64=False)
+    assert np.sum(np.abs(host32 - p)) < 1e-5
+
+
+def test_pt_moments(state20):
+    dtype, h, ref, p = state20
+    r = qs.qs_pt_moments(h, 10)
+    tol = 1e-6 if dtype == qs.QS_C64 else 1e-11
+    # the state tolerance (L2 <= TOL) bounds the norm: |S - 1| <= 2 TOL + TOL^2
+    assert r["norm"] == pytest.approx(O.norm(p), abs=2.001 * TOL[dtype])
+    assert r["entropy"] == pytest.approx(O.entropy(p), rel=tol)
+    assert r["uniform_ce"] == pytest.approx(O.uniform_ce(p), rel=tol)
+    mo = O.moments(p, 10)
+    mtol = 1e-5 if dtype == qs.QS_C64 else 1e-10
+    for k in range(10):
+        assert r["moments"][k] == pytest.approx(mo[k], rel=mtol), k
+
+
+def _check_samples_justified(p_oracle, x, seed, bound):
+    C = np.cumsum(p_oracle)          # numpy's pairwise sum; bound covers the order
+    total = C[-1]
+    idx = np.arange(x.size)
+    u = np.array([O.sample_uniform(seed, int(j)) for j in idx])
+    target = u * total
+    lo = np.where(x > 0, C[np.maximum(x.astype(np.int64) - 1, 0)], 0.0)
+    hi = C[x.astype(np.int64)]
+    ok = (lo - bound <= target) & (target < hi + bound)
+    assert ok.all(), np.nonzero(~ok)[0][:10]
+    assert (p_oracle[x.astype(np.int64)] > 0).all()
+
+
+def test_sampler(state20):
+    dtype, h, ref, p = state20
+    m = 100000
+    seed = 1000
+    x = qs.qs_sample(h, m, seed)
+    xo = O.sample(p, m, seed)
+    mismatch = int(np.sum(x != xo))
+    if dtype == qs.QS_C128:
+        assert mismatch <= max(1, int(1e-5 * m))
+        _check_samples_justified(p, x, seed, 1e-12)
+    else:
+        psi = qs.qs_state_copy_out(h, 20, dtype)
+        pg = np.abs(psi.astype(np.complex128)) ** 2
+        bound = np.sum(np.abs(pg - p)) + 1e-12
+        assert mismatch <= 1e-2 * m
+        _check_samples_justified(p, x, seed, bound)
+    # into a device buffer too
+    import torch
+    xd = torch.empty(m, dtype=torch.int64, device="cuda")
+    qs.qs_sample(h, m, seed, out=xd)
+    torch.cuda.synchronize()
+    assert np.array_equal(xd.cpu().numpy().view(np.uint64), x)
+
+
+def test_cross_entropy(state20):
+    dtype, h, ref, p = state20
+    xo = O.sample(p, 100000, 1000)
+    ce, dh = qs.qs_cross_entropy(h, xo)
+    ce_o, dh_o = O.cross_entropy(p, xo)
+    assert ce == pytest.approx(ce_o, rel=1e-6 if dtype == qs.QS_C64 else 1e-12)
+    assert dh == pytest.approx(dh_o, abs=2e-5 if dtype == qs.QS_C64 else 1e-10)
+    assert abs(dh - 1) < 0.03                      # Eq. ae on ideal samples
+
+
+def test_cross_entropy_rejects_out_of_range(state20):
+    dtype, h, ref, p = state20
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_cross_entropy(h, np.array([0, 1 << 20], dtype=np.uint64))
+    assert e.value.status == _native.QS_ERR_INVALID_ARG
+
+
+def test_sampler_edge_cases():
+    n = 7
+    h = qs.qs_state_create(n, qs.QS_C128)
+    try:
+        # basis state: every sample is index 0
+        assert np.array_equal(qs.qs_sample(h, 50, 3), np.zeros(50, dtype=np.uint64))
+        # a state with zero entries: never sampled
+        v = np.zeros(1 << n, dtype=np.complex128)
+        v[[5, 77, 127]] = [0.6, 0.0 + 0.8j, 0.0]
+        qs.qs_state_copy_in(h, v)
+        x = qs.qs_sample(h, 2000, 9)
+        assert set(np.unique(x)) <= {5, 77}
+        assert np.array_equal(x, O.sample(np.abs(v) ** 2, 2000, 9))
+        # zero state: refused
+        qs.qs_state_copy_in(h, np.zeros(1 << n, dtype=np.complex128))
+        with pytest.raises(qs.QSError):
+            qs.qs_sample(h, 10, 1)
+        r = qs.qs_pt_moments(h, 2)
+        assert r["norm"] == 0 and math.isinf(r["uniform_ce"])
+    finally:
+        qs.qs_state_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# full sizes: properties that hold at any size
+# --------------------------------------------------------------------------
+def inverse_circuit(g):
+    inv = g[::-1].copy()
+    for x in inv:
+        k = int(x["kind"])
+        if k == qs.QS_X_HALF:
+            x["kind"], x["theta"] = qs.QS_RX, -np.pi / 2
+        elif k == qs.QS_Y_HALF:
+            x["kind"], x["theta"] = qs.QS_RY, -np.pi / 2
+        elif k == qs.QS_T:
+            x["kind"], x["theta"] = qs.QS_RZ, -np.pi / 4      # T^dagger up to phase
+        elif k in (qs.QS_RX, qs.QS_RY, qs.QS_RZ, qs.QS_CPHASE):
+            x["theta"] = -x["theta"]
+    return inv
+
+
+def test_full_size_30_qubits():
+    import torch
+    n = 30
+    g = qs.qs_circuit_generate(5, 6, 40, 0)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    h2 = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED)
+        qs.qs_apply_circuit(h2, g, mode=qs.QS_MODE_PLAIN)
+        pa = qs.qs_state_amplitudes(h)
+        pb = qs.qs_state_amplitudes(h2)
+        # fused vs plain (two independent CUDA paths), on the device
+        diff = _device_rel_l2(pa, pb, n)
+        assert diff < 1e-5
+        r = qs.qs_pt_moments(h, 10)
+        assert abs(r["norm"] - 1) < 1e-5
+        N = 2.0 ** n
+        sigma = 0.75 * 2.0 ** (-n / 2)
+        assert abs(r["entropy"] - (n * math.log(2) - 1 + O.EULER_GAMMA)) < 4 * sigma
+        assert abs(r["uniform_ce"] - (n * math.log(2) + O.EULER_GAMMA)) < 5 * math.sqrt(1.645 / N)
+        assert abs(r["moments"][1] - 2) < 0.01
+        x = qs.qs_sample(h, 1000000, 1000)
+        ce, dh = qs.qs_cross_entropy(h, x)
+        assert abs(dh - 1) < 4 * 0.8 / 1000 + 0.002
+        # time reversal: U^dagger U |0> = |0> up to a global phase
+        qs.qs_apply_circuit(h, inverse_circuit(g))
+        probs = torch.empty(1 << n, dtype=torch.float32, device="cuda")
+        qs.qs_probabilities(h, probs, fp64=False)
+        torch.cuda.synchronize()
+        assert float(probs[0]) > 1 - 2e-5
+        del probs
+    finally:
+        qs.qs_state_destroy(h)
+        qs.qs_state_destroy(h2)
+
+
+def _device_rel_l2(pa, pb, n):
+    """||a - b|| / ||b|| of two complex64 device states, computed with torch
+    views of the raw buffers (test-side arithmetic only)."""
+    import torch
+    N = 1 << n
+    ta = _view(pa, 2 * N)
+    tb = _view(pb, 2 * N)
+    num = den = 0.0
+    step = 1 << 26
+    for i in range(0, 2 * N, step):
+        a, b = ta[i:i + step].double(), tb[i:i + step].double()
+        num += float(torch.sum((a - b) ** 2))
+        den += float(torch.sum(b ** 2))
+    return math.sqrt(num / den)
+
+
+def _view(ptr, count):
+    import torch
+    # wrap a raw device pointer as a float32 tensor (no copy)
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
+                                    "version": 3}
+    return torch.as_tensor(_Arr(), device="cuda")

@@ -1,0 +1,181 @@
+"""CPU tests of the C ABI library: it loads, exports every symbol the headers
+declare, validates arguments on the host, and its host-side parts (circuit
+generator, planner) agree with the oracle -- no GPU needed."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1608_00263_gb300 as qs
+from paper_1608_00263_gb300 import _native
+from paper_1608_00263_gb300 import build as qs_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    qs_build.build()
+    return _native.lib()
+
+
+def header_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(qs_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    names = header_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert not [n for n in names if n not in _native.SIGNATURES]
+
+
+def test_version_string():
+    assert "sm_103a" in qs.qs_version()
+
+
+GRIDS = [(4, 5, None), (5, 6, None), (2, 2, None), (1, 9, None), (3, 4, [(2, 3)]),
+         (6, 6, [(0, 0), (5, 5)]), (4, 6, [(3, 4), (3, 5)])]
+
+
+@pytest.mark.parametrize("rows,cols,dead_sites", GRIDS)
+def test_generator_matches_oracle_bit_exact(rows, cols, dead_sites):
+    dead = O.grid_dead_mask(rows, cols, dead_sites or ())
+    for seed in (0, 1, 2**63 + 5, 12345678901):
+        for depth in (0, 1, 9, 40):
+            a = qs.qs_circuit_generate(rows, cols, depth, seed, dead)
+            b = O.generate_circuit(rows, cols, depth, seed, dead)
+            assert a.tobytes() == b.tobytes()
+
+
+def test_generator_rejects_bad_arguments():
+    with pytest.raises(qs.QSError):
+        qs.qs_circuit_generate(0, 5, 3, 0)
+    with pytest.raises(qs.QSError):
+        qs.qs_circuit_generate(2, 2, -1, 0)
+    with pytest.raises(qs.QSError):
+        qs.qs_circuit_generate(2, 2, 3, 0, np.ones(4, dtype=np.uint8))   # no live site
+    # too small an output buffer
+    cnt = ctypes.c_size_t(3)
+    out = np.zeros(3, dtype=qs.GATE_DTYPE)
+    st = _native.lib().qs_circuit_generate(2, 2, None, 4, 0, out.ctypes.data, ctypes.byref(cnt))
+    assert st == _native.QS_ERR_INVALID_ARG
+    assert cnt.value > 3
+
+
+def _gate(kind, q0, q1=0, theta=0.0):
+    g = np.zeros(1, dtype=qs.GATE_DTYPE)
+    g[0] = (kind, q0, q1, 0, 0, theta)
+    return g
+
+
+@pytest.mark.parametrize("bad", [
+    _gate(9, 0), _gate(qs.QS_H, 12), _gate(qs.QS_CZ, 3, 3), _gate(qs.QS_CZ, 1, 12),
+    _gate(qs.QS_RX, 1, 0, float("nan"))])
+def test_planner_validates_gates(bad):
+    with pytest.raises(qs.QSError) as e:
+        qs.qs_plan_circuit(12, qs.QS_C64, bad)
+    assert e.value.status == _native.QS_ERR_INVALID_ARG
+
+
+def test_planner_rejects_bad_sizes():
+    g = qs.qs_circuit_generate(3, 4, 5, 0)
+    for n in (0, 35):
+        with pytest.raises(qs.QSError):
+            qs.qs_plan_circuit(n, qs.QS_C64, g)
+    with pytest.raises(qs.QSError):
+        qs.qs_plan_circuit(12, 7, g)
+
+
+def test_planner_stats():
+    g = qs.qs_circuit_generate(5, 6, 40, 0)
+    st = qs.qs_plan_circuit(30, qs.QS_C64, g)
+    assert st["gates"] == len(g)
+    assert 5 <= st["passes"] <= 25
+    assert st["phases"] >= st["passes"]
+    assert st["ops"] == len(g)
+    assert st["bytes"] == st["passes"] * 2 * 8 * 2**30
+    plain = qs.qs_plan_circuit(30, qs.QS_C64, g, mode=qs.QS_MODE_PLAIN)
+    assert plain["passes"] == len(g)
+    # appendix specialisation: T moves half the bytes, CZ a quarter
+    kinds = g["kind"]
+    N8 = 8 * 2**30
+    expect = (np.sum(kinds == qs.QS_T) * N8 + np.sum(kinds == qs.QS_CZ) * N8 / 2
+              + np.sum((kinds != qs.QS_T) & (kinds != qs.QS_CZ)) * 2 * N8)
+    assert plain["bytes"] == expect
+
+
+@pytest.fixture(scope="module")
+def emulator():
+    src = os.path.join(ROOT, "tests", "plan_emulator.cpp")
+    host = os.path.join(ROOT, "paper_1608_00263_gb300", "csrc", "qs_host.cpp")
+    d = tempfile.mkdtemp(prefix="qs_emul_")
+    so = os.path.join(d, "libemul.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include"),
+                    src, host, "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    lib.emulate_plan.restype = ctypes.c_int
+    lib.emulate_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_int)]
+    return lib
+
+
+def _emulate(lib, n, gates, t, r, c):
+    psi = O.zero_state(n)
+    passes = ctypes.c_int(0)
+    g = np.ascontiguousarray(gates, dtype=qs.GATE_DTYPE)
+    assert lib.emulate_plan(n, g.ctypes.data, g.size, t, r, c, psi.ctypes.data,
+                            ctypes.byref(passes)) == 0
+    return psi, passes.value
+
+
+def random_gates(rng, n, count):
+    g = np.zeros(count, dtype=qs.GATE_DTYPE)
+    for i in range(count):
+        k = int(rng.integers(0, 9))
+        g[i]["kind"] = k
+        if k in (qs.QS_CZ, qs.QS_CPHASE):
+            a, b = rng.choice(n, size=2, replace=False)
+            g[i]["q0"], g[i]["q1"] = a, b
+        else:
+            g[i]["q0"] = rng.integers(0, n)
+        g[i]["theta"] = rng.uniform(-3, 3)
+    return g
+
+
+@pytest.mark.parametrize("n,t,r,c", [(10, 7, 5, 5), (12, 8, 3, 2), (11, 11, 5, 5),
+                                     (13, 9, 4, 4), (9, 6, 5, 0), (14, 10, 5, 5)])
+def test_plan_semantics_random_gates(emulator, n, t, r, c):
+    rng = np.random.default_rng(n * 100 + t)
+    g = random_gates(rng, n, 300)
+    psi, passes = _emulate(emulator, n, g, t, r, c)
+    ref = O.simulate(n, g)
+    assert np.max(np.abs(psi - ref)) < 1e-12
+    assert passes >= 1
+
+
+@pytest.mark.parametrize("rows,cols,depth,t", [(4, 5, 25, 13), (4, 4, 30, 9), (3, 5, 40, 10)])
+def test_plan_semantics_random_circuits(emulator, rows, cols, depth, t):
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, 3)
+    psi, passes = _emulate(emulator, n, g, t, 5, 5)
+    ref = O.simulate(n, g)
+    assert np.max(np.abs(psi - ref)) < 1e-12
