@@ -32,6 +32,8 @@ WORKLOADS = {
     "grid6x6m2_n34_d40": dict(rows=6, cols=6, dead=((0, 0), (5, 5)), depth=40, m=1_000_000,
                               fp64_probs=False),
     "grid4x5_n20_d25": dict(rows=4, cols=5, dead=(), depth=25, m=100_000, fp64_probs=True),
+    # small case for profiler captures (2.1 GB state)
+    "grid4x7_n28_d40": dict(rows=4, cols=7, dead=(), depth=40, m=1_000_000, fp64_probs=True),
 }
 DEFAULT_WORKLOAD = "grid5x6_n30_d40"
 METRIC = "cycles/s (random circuit, state-vector evolution + statistics + sampling)"

@@ -31,6 +31,20 @@ namespace {
 
 constexpr int kThreadsMax = 256;
 
+// Compact op record staged in shared memory once per CTA; one flat code per
+// op so the interpreter takes a single indirect branch per op.
+enum : uint32_t {
+    K_H = 0, K_XH = 8, K_YH = 16, K_SHX = 24,     // + register bit
+    K_SHY = 160,                                   // + register bit
+    K_T = 32,                                      // + register mask (1..31): T phase
+    K_NEG = 64,                                    // + register mask: sign flip
+    K_PH = 96,                                     // + register mask: general phase
+    K_UT = 128, K_UNEG = 129, K_UPH = 130,         // thread-uniform selection
+    K_COND = 256                                   // flag: selection has qubits
+                                                   // outside the register set
+};
+
+
 // Swizzled shared-memory index of tile element e: elements are grouped in
 // 16-byte units u = e / CE; bits 0..2 of u are XORed with a fold of its
 // higher bits.  Linear over GF(2): swz(a ^ b) = swz(a) ^ swz(b).
@@ -43,41 +57,104 @@ __host__ __device__ __forceinline__ uint32_t swz(uint32_t e)
 }
 
 // ---- register-bit operations (J = register bit, compile time) -------------
+// Every update is written in place (each output overwrites one input and no
+// temporary is live across it), so the op interpreter keeps the slots in
+// fixed registers.  For the deferred-scale butterflies the second output is
+// formed from the first: H: x' = x + y, y' = x' - 2y (= x - y); Y^1/2:
+// x' = x - y, y' = x' + 2y (= x + y); X^1/2: x' = x - i y, y' = y - i x with
+// the same trick per component.  complex64 uses the packed FP32x2
+// instructions of sm_100+ where both components see the same operation.
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+
+__device__ __forceinline__ void bf_h(float2 &x, float2 &y)
+{
+    x = __fadd2_rn(x, y);
+    y = __ffma2_rn(y, make_float2(-2.f, -2.f), x);
+}
+__device__ __forceinline__ void bf_h(double2 &x, double2 &y)
+{
+    x.x += y.x; x.y += y.y;
+    y.x = fma(y.x, -2.0, x.x); y.y = fma(y.y, -2.0, x.y);
+}
+__device__ __forceinline__ void bf_yh(float2 &x, float2 &y)
+{
+    x = __ffma2_rn(y, make_float2(-1.f, -1.f), x);
+    y = __ffma2_rn(y, make_float2(2.f, 2.f), x);
+}
+__device__ __forceinline__ void bf_yh(double2 &x, double2 &y)
+{
+    x.x -= y.x; x.y -= y.y;
+    y.x = fma(y.x, 2.0, x.x); y.y = fma(y.y, 2.0, x.y);
+}
+template <typename V>
+__device__ __forceinline__ void bf_xh(V &x, V &y)
+{
+    x.x = x.x + y.y;               // x'r = xr + yi
+    y.y = fmaR(y.y, (decltype(y.y))2, -x.x);   // y'i = yi - xr
+    x.y = x.y - y.x;               // x'i = xi - yr
+    y.x = fmaR(y.x, (decltype(y.x))2, x.y);    // y'r = yr + xi
+}
+// multiply by c (1 + i), c = 1/sqrt2 (the T phase), in place
+template <typename V, typename R>
+__device__ __forceinline__ void ph_t(V &v, R c)
+{
+    v.x = v.x * c;
+    v.x = fmaR(v.y, -c, v.x);      // c re - c im
+    v.y = fmaR(v.y, 2 * c, v.x);   // c re + c im
+}
+template <typename V, typename R>
+__device__ __forceinline__ void ph_gen(V &v, R pr, R pi)
+{
+    const R x = v.x;
+    v.x = fmaR(v.x, pr, -v.y * pi);
+    v.y = fmaR(x, pi, v.y * pr);
+}
+__device__ __forceinline__ void neg(float2 &v) { v = __fmul2_rn(v, make_float2(-1.f, -1.f)); }
+__device__ __forceinline__ void neg(double2 &v) { v.x = -v.x; v.y = -v.y; }
+
 template <int NS, int J, typename V>
 __device__ __forceinline__ void reg_h(V *a)
 {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-        if (!(s & (1 << J))) {
-            V x = a[s], y = a[s | (1 << J)];
-            a[s].x = x.x + y.x; a[s].y = x.y + y.y;
-            a[s | (1 << J)].x = x.x - y.x; a[s | (1 << J)].y = x.y - y.y;
-        }
+        if (!(s & (1 << J))) bf_h(a[s], a[s | (1 << J)]);
 }
 
-// [[1, -i], [-i, 1]]
 template <int NS, int J, typename V>
 __device__ __forceinline__ void reg_xh(V *a)
 {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-        if (!(s & (1 << J))) {
-            V x = a[s], y = a[s | (1 << J)];
-            a[s].x = x.x + y.y; a[s].y = x.y - y.x;
-            a[s | (1 << J)].x = y.x + x.y; a[s | (1 << J)].y = y.y - x.x;
-        }
+        if (!(s & (1 << J))) bf_xh(a[s], a[s | (1 << J)]);
 }
 
-// [[1, -1], [1, 1]]
 template <int NS, int J, typename V>
 __device__ __forceinline__ void reg_yh(V *a)
 {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
+        if (!(s & (1 << J))) bf_yh(a[s], a[s | (1 << J)]);
+}
+
+__device__ __forceinline__ void axpy(float2 &x, const float2 &y, float k)
+{
+    x = __ffma2_rn(y, make_float2(k, k), x);
+}
+__device__ __forceinline__ void axpy(double2 &x, const double2 &y, double k)
+{
+    x.x = fma(y.x, k, x.x); x.y = fma(y.y, k, x.y);
+}
+// Shear on register bit J: x += k y (WHICH = 0) or y += k x (WHICH = 1),
+// x the slot with the bit clear, y its partner.
+template <int NS, int J, int WHICH, typename V, typename R>
+__device__ __forceinline__ void reg_shear(V *a, R k)
+{
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
         if (!(s & (1 << J))) {
-            V x = a[s], y = a[s | (1 << J)];
-            a[s].x = x.x - y.x; a[s].y = x.y - y.y;
-            a[s | (1 << J)].x = x.x + y.x; a[s | (1 << J)].y = x.y + y.y;
+            if (WHICH == 0) axpy(a[s], a[s | (1 << J)], k);
+            else axpy(a[s | (1 << J)], a[s], k);
         }
 }
 
@@ -98,17 +175,31 @@ __device__ __forceinline__ void reg_dense(V *a, const R *m)
         }
 }
 
-// Phase / sign on the slots whose register bits include all of M.
+// Phase on the slots whose register bits include all of M.  `tgate` selects
+// the in-place T form (pr = pi = 1/sqrt2).
 template <int NS, int M, typename V, typename R>
-__device__ __forceinline__ void reg_phase(V *a, R pr, R pi)
+__device__ __forceinline__ void reg_phase(V *a, R pr, R pi, bool tgate)
+{
+    if (tgate) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if ((s & M) == M) ph_t(a[s], pr);
+    } else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            if ((s & M) == M) ph_gen(a[s], pr, pi);
+    }
+}
+
+__device__ __forceinline__ void mul_sign(float2 &v, float sg) { v = __fmul2_rn(v, make_float2(sg, sg)); }
+__device__ __forceinline__ void mul_sign(double2 &v, double sg) { v.x *= sg; v.y *= sg; }
+
+template <int NS, int M, typename V, typename R>
+__device__ __forceinline__ void reg_sign(V *a, R sg)
 {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-        if ((s & M) == M) {
-            R x = a[s].x * pr - a[s].y * pi;
-            a[s].y = a[s].x * pi + a[s].y * pr;
-            a[s].x = x;
-        }
+        if ((s & M) == M) mul_sign(a[s], sg);
 }
 
 template <int NS, int M, typename V>
@@ -116,11 +207,13 @@ __device__ __forceinline__ void reg_neg(V *a)
 {
 #pragma unroll
     for (int s = 0; s < NS; ++s)
-        if ((s & M) == M) { a[s].x = -a[s].x; a[s].y = -a[s].y; }
+        if ((s & M) == M) neg(a[s]);
 }
 
 #define QS_CASE_BIT(J, CALL) case J: CALL(J); break;
+#define QS_CASE_BIT2(C, J, CALL) case C: CALL(J); break;
 
+// type: 0 = H, 1 = X^1/2, 2 = Y^1/2 (deferred-scale forms), 3 = dense 2x2.
 template <int RB, typename V, typename R>
 __device__ __forceinline__ void dispatch_bit_op(int type, int j, V *a, const R *m)
 {
@@ -129,15 +222,15 @@ __device__ __forceinline__ void dispatch_bit_op(int type, int j, V *a, const R *
 #define QS_X_(J) reg_xh<NS, (J < RB ? J : 0)>(a)
 #define QS_Y_(J) reg_yh<NS, (J < RB ? J : 0)>(a)
 #define QS_D_(J) reg_dense<NS, (J < RB ? J : 0)>(a, m)
-    switch (type) {
-    case OP_H: switch (j) { QS_CASE_BIT(0, QS_H_) QS_CASE_BIT(1, QS_H_) QS_CASE_BIT(2, QS_H_)
-                            QS_CASE_BIT(3, QS_H_) QS_CASE_BIT(4, QS_H_) QS_CASE_BIT(5, QS_H_) } break;
-    case OP_XH: switch (j) { QS_CASE_BIT(0, QS_X_) QS_CASE_BIT(1, QS_X_) QS_CASE_BIT(2, QS_X_)
-                             QS_CASE_BIT(3, QS_X_) QS_CASE_BIT(4, QS_X_) QS_CASE_BIT(5, QS_X_) } break;
-    case OP_YH: switch (j) { QS_CASE_BIT(0, QS_Y_) QS_CASE_BIT(1, QS_Y_) QS_CASE_BIT(2, QS_Y_)
-                             QS_CASE_BIT(3, QS_Y_) QS_CASE_BIT(4, QS_Y_) QS_CASE_BIT(5, QS_Y_) } break;
-    case OP_DENSE: switch (j) { QS_CASE_BIT(0, QS_D_) QS_CASE_BIT(1, QS_D_) QS_CASE_BIT(2, QS_D_)
-                                QS_CASE_BIT(3, QS_D_) QS_CASE_BIT(4, QS_D_) QS_CASE_BIT(5, QS_D_) } break;
+    switch (type * 8 + j) {
+    QS_CASE_BIT(0, QS_H_) QS_CASE_BIT(1, QS_H_) QS_CASE_BIT(2, QS_H_) QS_CASE_BIT(3, QS_H_)
+    QS_CASE_BIT(4, QS_H_) QS_CASE_BIT(5, QS_H_)
+    QS_CASE_BIT2(8, 0, QS_X_) QS_CASE_BIT2(9, 1, QS_X_) QS_CASE_BIT2(10, 2, QS_X_)
+    QS_CASE_BIT2(11, 3, QS_X_) QS_CASE_BIT2(12, 4, QS_X_) QS_CASE_BIT2(13, 5, QS_X_)
+    QS_CASE_BIT2(16, 0, QS_Y_) QS_CASE_BIT2(17, 1, QS_Y_) QS_CASE_BIT2(18, 2, QS_Y_)
+    QS_CASE_BIT2(19, 3, QS_Y_) QS_CASE_BIT2(20, 4, QS_Y_) QS_CASE_BIT2(21, 5, QS_Y_)
+    QS_CASE_BIT2(24, 0, QS_D_) QS_CASE_BIT2(25, 1, QS_D_) QS_CASE_BIT2(26, 2, QS_D_)
+    QS_CASE_BIT2(27, 3, QS_D_) QS_CASE_BIT2(28, 4, QS_D_) QS_CASE_BIT2(29, 5, QS_D_)
     default: break;
     }
 #undef QS_H_
@@ -151,10 +244,10 @@ __device__ __forceinline__ void dispatch_bit_op(int type, int j, V *a, const R *
 #define QS_M32(F) QS_M16(0, F) QS_M16(16, F)
 
 template <int RB, typename V, typename R>
-__device__ __forceinline__ void dispatch_mask_phase(int mask, V *a, R pr, R pi)
+__device__ __forceinline__ void dispatch_mask_phase(int mask, V *a, R pr, R pi, bool tgate)
 {
     constexpr int NS = 1 << RB;
-#define QS_PC(M) case M: reg_phase<NS, (M) & (NS - 1)>(a, pr, pi); break;
+#define QS_PC(M) case M: reg_phase<NS, (M) & (NS - 1)>(a, pr, pi, tgate); break;
     switch (mask) { QS_M32(QS_PC) default: break; }
 #undef QS_PC
 }
@@ -168,6 +261,112 @@ __device__ __forceinline__ void dispatch_mask_neg(int mask, V *a)
 #undef QS_NC
 }
 
+// Trailing zeros of a positive integer known at compile time (the callers
+// use it on unrolled loop indices, so it folds to a constant).
+template <int X> struct CtzT { static constexpr int value = (X & 1) ? 0 : 1 + CtzT<(X >> 1)>::value; };
+template <> struct CtzT<0> { static constexpr int value = 0; };
+
+// Loads / stores the register slots of a phase from / to the shared tile,
+// visiting slots in Gray-code order so that each address differs from the
+// previous one by one register bit (one XOR with that bit's offset).
+// COUNT slots (or slot pairs when SHIFT = 1: register bit 0 is tile bit 0,
+// so slots s and s+1 are one 16-byte unit).
+template <int COUNT, int SHIFT>
+struct SlotIO {
+    template <int I, typename V>
+    struct Step {
+        static __device__ __forceinline__ void ld(V *a, const V *tile, uint32_t off, const uint32_t *pb)
+        {
+            if (I) off ^= pb[SHIFT + CtzT<I>::value];
+            constexpr int s = (I ^ (I >> 1)) << SHIFT;
+            if (SHIFT) {
+                const float4 v = *reinterpret_cast<const float4 *>(tile + off);
+                a[s].x = v.x; a[s].y = v.y; a[s + 1].x = v.z; a[s + 1].y = v.w;
+            } else {
+                a[s] = tile[off];
+            }
+            Step<I + 1, V>::ld(a, tile, off, pb);
+        }
+        static __device__ __forceinline__ void st(const V *a, V *tile, uint32_t off, const uint32_t *pb)
+        {
+            if (I) off ^= pb[SHIFT + CtzT<I>::value];
+            constexpr int s = (I ^ (I >> 1)) << SHIFT;
+            if (SHIFT)
+                *reinterpret_cast<float4 *>(tile + off) = make_float4(a[s].x, a[s].y, a[s + 1].x, a[s + 1].y);
+            else
+                tile[off] = a[s];
+            Step<I + 1, V>::st(a, tile, off, pb);
+        }
+    };
+    template <typename V>
+    struct Step<COUNT, V> {
+        static __device__ __forceinline__ void ld(V *, const V *, uint32_t, const uint32_t *) {}
+        static __device__ __forceinline__ void st(const V *, V *, uint32_t, const uint32_t *) {}
+    };
+    template <typename V>
+    static __device__ __forceinline__ void load(V *a, const V *tile, uint32_t off, const uint32_t *pb)
+    { Step<0, V>::ld(a, tile, off, pb); }
+    template <typename V>
+    static __device__ __forceinline__ void store(const V *a, V *tile, uint32_t off, const uint32_t *pb)
+    { Step<0, V>::st(a, tile, off, pb); }
+    template <typename V>
+    static __device__ __forceinline__ void load_pairs(V *a, const V *tile, uint32_t off, const uint32_t *pb)
+    { Step<0, V>::ld(a, tile, off, pb); }
+    template <typename V>
+    static __device__ __forceinline__ void store_pairs(const V *a, V *tile, uint32_t off, const uint32_t *pb)
+    { Step<0, V>::st(a, tile, off, pb); }
+};
+
+// Executes one staged op on the register slots.  `sel` is the part of a
+// diagonal op's selection outside the register set (true when the op has
+// none); diagonal ops apply branch-free with sign / identity when unmet.
+template <int RB, typename V, typename R>
+__device__ __forceinline__ void exec_op(uint32_t code, V *a, bool sel, R &fr, R &fi,
+                                        const R *phase, const DevOp *ops_g, uint32_t aux)
+{
+    constexpr int NS = 1 << RB;
+    const R c = (R)0.70710678118654752440;
+#define QS_SGN (sel ? (R)-1 : (R)1)
+#define QS_PR (sel ? phase[0] : (R)1)
+#define QS_PI (sel ? phase[1] : (R)0)
+    switch (code & ~K_COND) {
+#define QS_B(J)                                                          \
+    case K_H + J: reg_h<NS, (J < RB ? J : 0)>(a); break;                 \
+    case K_XH + J: reg_xh<NS, (J < RB ? J : 0)>(a); break;               \
+    case K_YH + J: reg_yh<NS, (J < RB ? J : 0)>(a); break;               \
+    case K_SHX + J: reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;   \
+    case K_SHY + J: reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
+    QS_B(0) QS_B(1) QS_B(2) QS_B(3) QS_B(4) QS_B(5)
+#undef QS_B
+#define QS_M(M)                                                                    \
+    case K_T + M: reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break;           \
+    case K_NEG + M: reg_sign<NS, ((M) & (NS - 1))>(a, QS_SGN); break;              \
+    case K_PH + M: reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
+    QS_M32(QS_M)
+#undef QS_M
+    case K_UT: {
+        // T on a selection outside the register set: f *= e^{i pi/4} if sel
+        const R tr = sel ? c : (R)1, ti = sel ? c : (R)0;
+        const R x = fr * tr - fi * ti;
+        fi = fr * ti + fi * tr;
+        fr = x;
+        break;
+    }
+    case K_UNEG: fr *= QS_SGN; fi *= QS_SGN; break;
+    case K_UPH: {
+        const R pr = QS_PR, pi = QS_PI;
+        const R x = fr * pr - fi * pi;
+        fi = fr * pi + fi * pr;
+        fr = x;
+        break;
+    }
+    default: break;
+    }
+#undef QS_SGN
+#undef QS_PR
+#undef QS_PI
+}
+
 // Deposits the low bits of x into the positions listed in pos[0..cnt).
 __device__ __forceinline__ uint64_t deposit(uint64_t x, const uint8_t *pos, int cnt)
 {
@@ -177,6 +376,36 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, const uint8_t *pos, int 
 }
 
 }  // namespace
+
+template <typename R>
+struct SOp {
+    uint32_t code;
+    uint32_t aux;       // index into the staged phase / shear-factor table
+    uint64_t qmask;     // qubit selection outside the register set
+};
+
+struct SPhase {
+    uint32_t pb[kMaxRegBits];   // swizzled tile offset of each register bit
+    int32_t op_begin, op_end;
+    int32_t paired;             // register bit 0 is tile bit 0 (16-byte slots)
+    int32_t uniform_ops;        // phase has thread-uniform diagonal ops
+};
+
+struct SThread {
+    uint32_t phys;              // swizzled tile offset of the thread's slot 0
+    uint32_t pad;
+    uint64_t qoff;              // qubit-index bits of the thread's tile bits
+};
+
+template <typename R, int RB>
+struct FusedSmem {
+    DevPass P;
+    SPhase ph[kMaxPhasesPerPass];
+    SOp<R> ops[kMaxOpsPerPass];
+    R phase[kMaxOpsPerPass][2];
+    SThread th[kMaxPhasesPerPass][kThreadsMax];
+    uint64_t it_off[(1 << RB)];
+};
 
 // One launch = one pass over the state.  blockDim.x = 2^(t - RB).
 template <typename R, int RB>
@@ -191,32 +420,91 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     constexpr int CPT = NS / CE;                // 16-byte units per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
-    __shared__ DevPass P;
-    __shared__ uint64_t it_off[CPT];
+    __shared__ FusedSmem<R, RB> S;
 
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     for (int i = tid; i < (int)(sizeof(DevPass) / 4); i += nthr)
-        reinterpret_cast<uint32_t *>(&P)[i] = reinterpret_cast<const uint32_t *>(pass_g)[i];
+        reinterpret_cast<uint32_t *>(&S.P)[i] = reinterpret_cast<const uint32_t *>(pass_g)[i];
     __syncthreads();
-    const int t = P.t;
-    const int ng = P.n - t;                     // out-of-tile qubits
-    // qubit offset of the 16-byte units handled by this thread
-    for (int i = tid; i < CPT; i += nthr) it_off[i] = deposit((uint64_t)(CE * nthr) * i, P.L, t);
-    const uint64_t tid_off = deposit((uint64_t)CE * tid, P.L, t);
+    const int t = S.P.t;
+    const int ng = S.P.n - t;                   // out-of-tile qubits
+    const int nph = S.P.nphases;
+    // ---- stage phases, ops and per-thread phase tables (once per CTA) ----
+    for (int ph = 0; ph < nph; ++ph) {
+        const DevPhase &D = phases_g[S.P.phase_begin + ph];
+        uint32_t regmask = 0;
+        for (int j = 0; j < RB; ++j) regmask |= 1u << D.R[j];
+        if (tid == 0) {
+            for (int j = 0; j < RB; ++j) S.ph[ph].pb[j] = swz<CE>(1u << D.R[j]);
+            S.ph[ph].op_begin = D.op_begin - phases_g[S.P.phase_begin].op_begin;
+            S.ph[ph].op_end = D.op_end - phases_g[S.P.phase_begin].op_begin;
+            S.ph[ph].paired = (CE == 2 && D.R[0] == 0) ? 1 : 0;
+            int u = 0;
+            for (int o = D.op_begin; o < D.op_end; ++o)
+                u |= (ops_g[o].type == OP_PHASE || ops_g[o].type == OP_NEG) && ops_g[o].rmask == 0;
+            S.ph[ph].uniform_ops = u;
+        }
+        uint32_t e = 0;
+        uint64_t q = 0;
+        for (int b = 0, k = 0; b < t; ++b) {
+            if ((regmask >> b) & 1u) continue;
+            const uint32_t bit = (tid >> k) & 1u;
+            e |= bit << b;
+            q |= (uint64_t)bit << S.P.L[b];
+            ++k;
+        }
+        S.th[ph][tid].phys = swz<CE>(e);
+        S.th[ph][tid].qoff = q;
+    }
+    {
+        const int o0 = phases_g[S.P.phase_begin].op_begin;
+        const int o1 = phases_g[S.P.phase_begin + nph - 1].op_end;
+        for (int o = o0 + tid; o < o1; o += nthr) {
+            const DevOp &d = ops_g[o];
+            SOp<R> so;
+            const bool tphase = d.type == OP_PHASE && d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
+            switch (d.type) {
+            case OP_H: so.code = K_H + d.a; break;
+            case OP_XH: so.code = K_XH + d.a; break;
+            case OP_YH: so.code = K_YH + d.a; break;
+            case OP_SHX: so.code = K_SHX + d.a; break;
+            case OP_SHY: so.code = K_SHY + d.a; break;
+            case OP_PHASE:
+                so.code = d.rmask ? ((tphase ? K_T : K_PH) + d.rmask) : (tphase ? K_UT : K_UPH);
+                break;
+            default: so.code = d.rmask ? K_NEG + d.rmask : K_UNEG; break;
+            }
+            if (d.type == OP_PHASE || d.type == OP_NEG) {
+                if (d.qmask) so.code |= K_COND;
+            }
+            so.aux = (uint32_t)(o - o0);
+            so.qmask = d.qmask;
+            S.phase[o - o0][0] = (R)d.m[0];
+            S.phase[o - o0][1] = (R)d.m[1];
+            S.ops[o - o0] = so;
+        }
+    }
+    for (int i = tid; i < CPT; i += nthr) S.it_off[i] = deposit((uint64_t)(CE * nthr) * i, S.P.L, t);
+    const uint64_t tid_off = deposit((uint64_t)CE * tid, S.P.L, t);
+    const R gsr = (R)S.P.gscale_re, gsi = (R)S.P.gscale_im;
+    const bool gscale_one = (S.P.gscale_re == 1.0 && S.P.gscale_im == 0.0);
     __syncthreads();
 
-    const R gsr = (R)P.gscale_re, gsi = (R)P.gscale_im;
-    const bool gscale_one = (P.gscale_re == 1.0 && P.gscale_im == 0.0);
-    const bool gscale_real = (P.gscale_im == 0.0);
-
-    for (uint64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
-        const uint64_t base = deposit(tau, P.G, ng);
+    // contiguous range of tiles per CTA; the tile base (bits of the
+    // out-of-tile qubits) advances by a masked increment
+    const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
+    const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
+    const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
+    uint64_t gmask = 0;
+    for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
+    uint64_t base = deposit(t_begin, S.P.G, ng);
+    for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
 #pragma unroll
         for (int it = 0; it < CPT; ++it) {
             uint32_t e = (uint32_t)(CE * (it * nthr + tid));
-            const V *src = amps + (base | tid_off | it_off[it]);
+            const V *src = amps + (base | tid_off | S.it_off[it]);
             uint32_t saddr = (uint32_t)__cvta_generic_to_shared(tile + swz<CE>(e));
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src)
                          : "memory");
@@ -224,78 +512,53 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
 
-        for (int ph = 0; ph < P.nphases; ++ph) {
-            const DevPhase PH = phases_g[P.phase_begin + ph];
-            // thread bits: tile bits outside the register set, ascending
-            uint32_t e_th = 0;
-            uint64_t q_th = 0;
-            {
-                uint32_t regmask = 0;
-#pragma unroll
-                for (int j = 0; j < RB; ++j) regmask |= 1u << PH.R[j];
-                int k = 0;
-                for (int b = 0; b < t; ++b) {
-                    if ((regmask >> b) & 1u) continue;
-                    uint32_t bitv = (tid >> k) & 1u;
-                    e_th |= bitv << b;
-                    q_th |= (uint64_t)bitv << P.L[b];
-                    ++k;
-                }
-            }
-            const uint64_t idx_th = base | q_th;
-            const uint32_t p_th = swz<CE>(e_th);
+        for (int ph = 0; ph < nph; ++ph) {
+            const SThread T = S.th[ph][tid];
+            const uint64_t idx_th = base | T.qoff;
             uint32_t pb[RB];
 #pragma unroll
-            for (int j = 0; j < RB; ++j) pb[j] = swz<CE>(1u << PH.R[j]);
+            for (int j = 0; j < RB; ++j) pb[j] = S.ph[ph].pb[j];
+            const bool paired = S.ph[ph].paired;
             V a[NS];
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                uint32_t off = 0;
-#pragma unroll
-                for (int j = 0; j < RB; ++j)
-                    if ((s >> j) & 1) off ^= pb[j];
-                a[s] = tile[p_th ^ off];
+            // slots in Gray-code order: one XOR per slot address
+            if (CE == 2 && paired)
+                SlotIO<NS / 2, 1>::template load_pairs<V>(a, tile, T.phys, pb);
+            else
+                SlotIO<NS, 0>::template load<V>(a, tile, T.phys, pb);
+            R fr = (R)1, fi = (R)0;             // thread-uniform pending factor
+            const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end;
+            const bool fpend = S.ph[ph].uniform_ops != 0;
+            for (int o = ob; o < oe; ++o) {
+                const SOp<R> op = S.ops[o];
+                // selection bits outside the register set (thread / tile
+                // constant): +1 or -1 sign, or identity phase when unmet
+                const bool sel = (idx_th & op.qmask) == op.qmask;
+                exec_op<RB>(op.code, a, sel, fr, fi, S.phase[op.aux], ops_g, op.aux);
             }
-            for (int o = PH.op_begin; o < PH.op_end; ++o) {
-                const DevOp *op = ops_g + o;
-                const int type = __ldg(&op->type);
-                if (type == OP_PHASE || type == OP_NEG) {
-                    const uint64_t qm = __ldg(&op->qmask);
-                    if ((idx_th & qm) != qm) continue;
-                    const int rm = __ldg(&op->rmask);
-                    if (type == OP_NEG)
-                        dispatch_mask_neg<RB>(rm, a);
-                    else
-                        dispatch_mask_phase<RB>(rm, a, (R)__ldg(&op->m[0]), (R)__ldg(&op->m[1]));
-                } else {
-                    R m[8];
-                    if (type == OP_DENSE) {
+            if (ph == nph - 1 && !gscale_one) {
+                const R x = fr * gsr - fi * gsi;
+                fi = fr * gsi + fi * gsr;
+                fr = x;
+            }
+            if (fpend || (ph == nph - 1 && !gscale_one)) {
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) m[e] = (R)__ldg(&op->m[e]);
-                    }
-                    dispatch_bit_op<RB>(type, __ldg(&op->a), a, m);
+                for (int s = 0; s < NS; ++s) {
+                    const R x = a[s].x * fr - a[s].y * fi;
+                    a[s].y = a[s].x * fi + a[s].y * fr;
+                    a[s].x = x;
                 }
             }
-            if (ph == P.nphases - 1 && !gscale_one) {
-                if (gscale_real) {
+            {
+                // reload the addressing state from shared memory rather than
+                // keeping it live across the op loop
+                uint32_t pb2[RB];
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) { a[s].x *= gsr; a[s].y *= gsr; }
-                } else {
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) {
-                        R x = a[s].x * gsr - a[s].y * gsi;
-                        a[s].y = a[s].x * gsi + a[s].y * gsr;
-                        a[s].x = x;
-                    }
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                uint32_t off = 0;
-#pragma unroll
-                for (int j = 0; j < RB; ++j)
-                    if ((s >> j) & 1) off ^= pb[j];
-                tile[p_th ^ off] = a[s];
+                for (int j = 0; j < RB; ++j) pb2[j] = S.ph[ph].pb[j];
+                const uint32_t phys = S.th[ph][tid].phys;
+                if (CE == 2 && S.ph[ph].paired)
+                    SlotIO<NS / 2, 1>::template store_pairs<V>(a, tile, phys, pb2);
+                else
+                    SlotIO<NS, 0>::template store<V>(a, tile, phys, pb2);
             }
             __syncthreads();
         }
@@ -304,7 +567,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         for (int it = 0; it < CPT; ++it) {
             uint32_t e = (uint32_t)(CE * (it * nthr + tid));
             const float4 v = *reinterpret_cast<const float4 *>(tile + swz<CE>(e));
-            *reinterpret_cast<float4 *>(amps + (base | tid_off | it_off[it])) = v;
+            *reinterpret_cast<float4 *>(amps + (base | tid_off | S.it_off[it])) = v;
         }
         __syncthreads();
     }

@@ -371,10 +371,29 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
         std::vector<char> pdone(ng, 1);
         for (int i : pass_gates) pdone[i] = 0;
         size_t prem = pass_gates.size();
-        while (prem) {
+        int pass_ops = 0;
+        while (prem && dp.nphases < kMaxPhasesPerPass && pass_ops < kMaxOpsPerPass) {
             uint64_t reg = choose_local(g, pass_gates, pdone, n, 0, local, dp.r);
             collect(g, pass_gates, pdone, reg, &phase_gates, &cnt);
             if (cnt == 0) return set_error(QS_ERR_INVALID_ARG, "planner made no phase progress");
+            // keep the pass within the kernel's op table; a prefix of the
+            // phase's (ordered, dependency-closed) gate list stays closed
+            {
+                // ops of a gate: 5 for RX, 3 for RY, else 1
+                size_t keep = 0;
+                int ops_needed = 0;
+                for (int gi : phase_gates) {
+                    const int k = g[gi].kind == QS_RX ? 5 : g[gi].kind == QS_RY ? 3 : 1;
+                    if (pass_ops + ops_needed + k > kMaxOpsPerPass) break;
+                    ops_needed += k;
+                    ++keep;
+                }
+                if (keep == 0 && dp.nphases == 0 && pass_ops == 0)
+                    return set_error(QS_ERR_INVALID_ARG, "op table too small");
+                phase_gates.resize(keep);
+                pass_ops += ops_needed;
+                if (keep == 0) break;
+            }
             DevPhase ph;
             std::memset(&ph, 0, sizeof ph);
             int reg_bit_of[64];
@@ -403,10 +422,29 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
                     case QS_X_HALF: op.type = OP_XH; ++deferred; break;
                     case QS_Y_HALF: op.type = OP_YH; ++deferred; break;
                     default: {
-                        op.type = OP_DENSE;
-                        Cplx u[4];
-                        gate_matrix(x.kind, x.theta, u);
-                        for (int e = 0; e < 4; ++e) { op.m[2 * e] = u[e].re; op.m[2 * e + 1] = u[e].im; }
+                        // RY(theta) is a rotation by phi = theta/2, written as
+                        // three in-place shears (Paeth): x -= t y, y += s x,
+                        // x -= t y with t = tan(phi/2), s = sin(phi).  phi is
+                        // first reduced to [-pi/2, pi/2]; each pi removed is
+                        // a factor -1 folded into the pass-wide scale.
+                        // RX(theta) = S RY(-theta) S^dagger, S = diag(1, i).
+                        const bool rx = x.kind == QS_RX;
+                        double phi = (rx ? -x.theta : x.theta) / 2;
+                        const double k = std::nearbyint(phi / M_PI);
+                        phi -= k * M_PI;
+                        if (std::fmod(std::fabs(k), 2.0) == 1.0) { gre = -gre; gim = -gim; }
+                        const double t = std::tan(phi / 2), sn = std::sin(phi);
+                        DevOp ph = op;
+                        ph.type = OP_PHASE;
+                        ph.rmask = (uint8_t)(1u << op.a);
+                        ph.qmask = 0;
+                        if (rx) { ph.m[0] = 0; ph.m[1] = -1; P.ops.push_back(ph); }
+                        DevOp sh = op;
+                        sh.type = OP_SHX; sh.m[0] = -t; P.ops.push_back(sh);
+                        sh.type = OP_SHY; sh.m[0] = sn; P.ops.push_back(sh);
+                        sh.type = OP_SHX; sh.m[0] = -t;
+                        if (rx) { P.ops.push_back(sh); ph.m[1] = 1; op = ph; }
+                        else op = sh;
                     }
                     }
                 } else {
@@ -445,7 +483,10 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
             P.phases.push_back(ph);
             ++dp.nphases;
         }
-        for (int i : pass_gates) { done[i] = 1; --remaining; }
+        int placed = 0;
+        for (int i : pass_gates)
+            if (pdone[i]) { done[i] = 1; --remaining; ++placed; }
+        dp.ngates = placed;
         double sc = std::ldexp(1.0, -(deferred / 2));
         if (deferred & 1) sc *= std::sqrt(0.5);
         dp.deferred = deferred;

@@ -56,6 +56,8 @@ enum OpType : uint8_t {
     OP_NEG = 5,     // multiply by -1, same selection as OP_PHASE
     OP_MATRIX = 6,  // tensor-core dense block (TC mode only): index of the
                     // block matrix in `a`
+    OP_SHX = 7,     // shear x += m[0] * y on register bit `a` (x: bit 0, y: bit 1)
+    OP_SHY = 8,     // shear y += m[0] * x on register bit `a`
 };
 
 struct DevOp {          // 80 bytes
@@ -71,6 +73,8 @@ struct DevOp {          // 80 bytes
 
 constexpr int kMaxTileBits = 16;
 constexpr int kMaxRegBits = 8;
+constexpr int kMaxPhasesPerPass = 8;    // per-thread phase tables live in shared memory
+constexpr int kMaxOpsPerPass = 256;     // op descriptors live in shared memory
 
 struct DevPhase {       // 16 bytes
     uint8_t R[kMaxRegBits];  // tile bit of each register bit

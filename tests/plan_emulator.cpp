@@ -47,6 +47,13 @@ extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, in
                                 if ((op.rmask >> j) & 1) sel = sel && ((e >> H.R[j]) & 1);
                             if (sel) tile[e] *= f;
                         }
+                    } else if (op.type == OP_SHX || op.type == OP_SHY) {
+                        const uint64_t bit = 1ULL << H.R[op.a];
+                        for (uint64_t e = 0; e < tile.size(); ++e) {
+                            if (e & bit) continue;
+                            if (op.type == OP_SHX) tile[e] += op.m[0] * tile[e | bit];
+                            else tile[e | bit] += op.m[0] * tile[e];
+                        }
                     } else {
                         const uint64_t bit = 1ULL << H.R[op.a];
                         cd u[4];
