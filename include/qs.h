@@ -185,6 +185,32 @@ qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64);
  * host `out`.  Returns QS_ERR_INVALID_ARG if the state has zero norm. */
 qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out);
 
+/* Allocation-free variant of qs_sample, for callers that must not allocate
+ * device memory while they run: code recording a CUDA graph (cudaMalloc is
+ * not permitted during stream capture), latency-critical loops that cannot
+ * absorb the implicit synchronisation of an allocation, and applications or
+ * host frameworks that hand all device memory to their own pool or fix
+ * their budget up front.  The paper has no counterpart; it is a deployment
+ * convenience.
+ *   n, dt, device_amps: the state (2^n amplitudes of type dt in device
+ *     memory, 16-byte aligned, canonical order), read only;
+ *   k, seed: as for qs_sample; device_out: k uint64 slots in device memory.
+ * Results are identical to qs_sample's for the same state, k and seed.  The
+ * scratch (one FP64 sum per 256 amplitudes plus scan totals) is a fixed
+ * array of 8 MiB compiled into the library, held by every GPU that loads it
+ * until the process exits, so n is limited to 1..28 (larger n returns
+ * QS_ERR_INVALID_ARG before any device work).  No call allocates memory.
+ * The first call on each device looks up that device's address of the array
+ * (make it outside any stream capture); later calls reuse it.  All calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or host threads) race and must be serialised by the caller; the
+ * array keeps the previous call's contents, and every entry a call reads is
+ * written by that same call first.  Work is ordered on cuda_stream (NULL =
+ * legacy default stream); the call synchronises that stream once to check
+ * the norm and returns with the search kernel queued. */
+qs_status qs_sample_noalloc(int n, qs_dtype dt, const void *device_amps, void *cuda_stream,
+                            uint64_t k, uint64_t seed, uint64_t *device_out);
+
 /* Cross entropy of a sample against the ideal distribution, Eq. ae:
  *   *ce = (1/m) sum_j ln(1/p_U(x_j)),  *delta_h = ln N + gamma - *ce
  * (gamma = Euler's constant; ln N + gamma = H_0 of Eq. au).  `samples`

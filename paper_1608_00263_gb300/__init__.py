@@ -23,7 +23,7 @@ __all__ = [
     "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
-    "qs_probabilities", "qs_sample", "qs_cross_entropy", "qs_pt_moments",
+    "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "library_path",
 ]
 
@@ -135,6 +135,14 @@ def qs_sample(h, k, seed, out=None):
     if out is None:
         out = np.empty(k, dtype=np.uint64)
     N.check(N.lib().qs_sample(h, k, seed & (2**64 - 1), _ptr(out)))
+    return out
+
+
+def qs_sample_noalloc(n, dtype, amps, k, seed, out, stream=None):
+    """Allocation-free sampling from a state given by its device pointer;
+    `out` is a device buffer of k uint64 (see include/qs.h)."""
+    N.check(N.lib().qs_sample_noalloc(n, dtype, _ptr(amps), _stream(stream), k, seed & (2**64 - 1),
+                                      _ptr(out)))
     return out
 
 

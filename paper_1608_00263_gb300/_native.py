@@ -62,6 +62,7 @@ SIGNATURES = {
                                        ctypes.POINTER(qs_opts), ctypes.POINTER(qs_plan_stats)]),
     "qs_probabilities": (ctypes.c_int, [P, P, ctypes.c_int]),
     "qs_sample": (ctypes.c_int, [P, U64, U64, P]),
+    "qs_sample_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, U64, U64, P]),
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),
     "qs_pt_moments": (ctypes.c_int, [P, ctypes.c_int, PD, PD, PD, PD]),
     "qs_state_copy_out": (ctypes.c_int, [P, P]),

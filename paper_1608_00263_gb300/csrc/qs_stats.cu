@@ -19,6 +19,7 @@
 // rescans one chunk with exactly the arithmetic that produced the chunk's
 // sum.
 #include <cmath>
+#include <mutex>
 
 #include "qs_device.cuh"
 
@@ -504,3 +505,112 @@ qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples, uint
 }
 
 }  // namespace qs
+
+// ---------------------------------------------------------------------------
+// Allocation-free sampler: qs_sample_noalloc
+//
+// The same chunk-sum / scan / search kernels as qs_sample, but their scratch
+// is a fixed file-scope device array instead of memory obtained at run time.
+// It holds one FP64 sum per 256-amplitude chunk plus the scan's block totals
+// for up to 2^28 amplitudes (8 MiB, resident on every device that loads the
+// library until the process exits).
+// ---------------------------------------------------------------------------
+namespace qs {
+
+constexpr uint64_t kNoAllocMaxChunks = 1ULL << 20;   // 2^28 amplitudes / 256
+constexpr uint64_t kNoAllocMaxBlocks = (kNoAllocMaxChunks + kScanSeg - 1) / kScanSeg;
+constexpr int kNoAllocMaxQubits = 28;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxChunks + kNoAllocMaxBlocks];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (host code only sees a host-side stand-in under the array's name).
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_addr[kNoAllocMaxDevices];
+
+static qs_status noalloc_scratch(double **out)
+{
+    int dev = 0;
+    QS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(QS_ERR_UNSUPPORTED, "device %d beyond the %d this entry point tracks", dev,
+                         kNoAllocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(QS_ERR_CUDA, "cudaGetSymbolAddress for the sampler scratch failed: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr[dev] = (double *)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return QS_OK;
+}
+
+static bool noalloc_is_device(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" qs_status qs_sample_noalloc(int n, qs_dtype dt, const void *device_amps, void *cuda_stream,
+                                       uint64_t k, uint64_t seed, uint64_t *device_out)
+{
+    clear_error();
+    if (n < 1 || n > kNoAllocMaxQubits)
+        return set_error(QS_ERR_INVALID_ARG,
+                         "qs_sample_noalloc supports 1..%d qubits (its fixed scratch holds %llu chunk "
+                         "sums); got n = %d", kNoAllocMaxQubits, (unsigned long long)kNoAllocMaxChunks, n);
+    if (dt != QS_C64 && dt != QS_C128) return set_error(QS_ERR_INVALID_ARG, "bad dtype %d", (int)dt);
+    if (!device_amps || ((uintptr_t)device_amps & 15))
+        return set_error(QS_ERR_INVALID_ARG, "device_amps is NULL or not 16-byte aligned");
+    if (k && !device_out) return set_error(QS_ERR_INVALID_ARG, "device_out is NULL");
+    if (!noalloc_is_device(device_amps)) return set_error(QS_ERR_INVALID_ARG, "device_amps is not device memory");
+    if (k && !noalloc_is_device(device_out)) return set_error(QS_ERR_INVALID_ARG, "device_out is not device memory");
+    double *scratch = nullptr;
+    if (qs_status st = noalloc_scratch(&scratch)) return st;
+    int dev = 0, sms = 1;
+    QS_CUDA_TRY(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    const uint64_t N = 1ULL << n;
+    const uint64_t nchunks = (N + kChunk - 1) / kChunk;
+    const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
+    double *csum = scratch;                 // every entry used is written below
+    double *btot = scratch + kNoAllocMaxChunks;
+    const int th = 256;
+    const int g1 = grid_for(nchunks * 32, th, sms, 16);
+    if (dt == QS_C64)
+        k_chunk_sums<float><<<g1, th, 0, stream>>>((const float2 *)device_amps, N, nchunks, csum);
+    else
+        k_chunk_sums<double><<<g1, th, 0, stream>>>((const double2 *)device_amps, N, nchunks, csum);
+    k_scan_block_totals<<<(unsigned)nblk, kScanThreads, 0, stream>>>(csum, nchunks, btot);
+    k_scan_totals<<<1, kScanThreads, 0, stream>>>(btot, (int)nblk);
+    k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, stream>>>(csum, nchunks, btot);
+    QS_LAUNCH_CHECK();
+    double total = 0;
+    QS_CUDA_TRY(cudaMemcpyAsync(&total, csum + nchunks - 1, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (!(total > 0) || !std::isfinite(total))
+        return set_error(QS_ERR_INVALID_ARG, "state has zero or non-finite norm (%g)", total);
+    if (k == 0) return QS_OK;
+    const int g2 = grid_for((k + 31) / 32 * 32, th, sms, 16);
+    if (dt == QS_C64)
+        k_sample_search<float><<<g2, th, 0, stream>>>((const float2 *)device_amps, N, nchunks, csum, k, seed, device_out);
+    else
+        k_sample_search<double><<<g2, th, 0, stream>>>((const double2 *)device_amps, N, nchunks, csum, k, seed, device_out);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
