@@ -248,7 +248,8 @@ def run_ours(args, rank, world, local):
     compare = {}
     if not args.no_compare and rank == 0:
         gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, base_seed, dead)
-        for name, md in (("plain", qs.QS_MODE_PLAIN), ("fused", qs.QS_MODE_FUSED)):
+        for name, md in (("plain", qs.QS_MODE_PLAIN), ("fused", qs.QS_MODE_FUSED),
+                         ("tc", qs.QS_MODE_FUSED_TC)):
             qs.qs_state_reset(h)
             qs.qs_prepare_circuit(h, gates, mode=md)
             torch.cuda.synchronize()
@@ -287,7 +288,7 @@ def run_ours(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "apply_cycles_per_s": round(depth * args.steps / (apply_total / 1000.0), 3),
         "passes_per_circuit": passes_total / args.steps,
-        "roofline": {"kernel": "k_fused_pass" if args.mode == "fused" else "k_tc_pass",
+        "roofline": {"kernel": "k_fused_pass<float,5,%s>" % ("false" if args.mode == "fused" else "true"),
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic,

@@ -176,13 +176,13 @@ static qs_status get_plan(qs_state *s, const qs_gate *gates, size_t ng, const qs
         const size_t b_pass = p.passes.size() * sizeof(DevPass);
         const size_t b_phase = p.phases.size() * sizeof(DevPhase);
         const size_t b_ops = p.ops.size() * sizeof(DevOp);
-        const size_t b_blk = p.tc_blocks.size() * sizeof(double);
+        const size_t b_blk = p.tc_words.size() * sizeof(uint32_t);
         const size_t total = b_pass + b_phase + b_ops + b_blk + 16;
         std::vector<unsigned char> host(total, 0);
         std::memcpy(host.data(), p.passes.data(), b_pass);
         std::memcpy(host.data() + b_pass, p.phases.data(), b_phase);
         std::memcpy(host.data() + b_pass + b_phase, p.ops.data(), b_ops);
-        if (b_blk) std::memcpy(host.data() + b_pass + b_phase + b_ops, p.tc_blocks.data(), b_blk);
+        if (b_blk) std::memcpy(host.data() + b_pass + b_phase + b_ops, p.tc_words.data(), b_blk);
         if (c.dev && c.dev_bytes < total) {
             QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
             cudaFree(c.dev);
@@ -220,7 +220,7 @@ extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t 
     if (ngates == 0) return QS_OK;
     DeviceGuard g(s->device);
     const int rb = s->dt == QS_C128 ? 4 : 5;
-    if (mode == QS_MODE_PLAIN || (mode == QS_MODE_FUSED && s->n < rb)) {
+    if (mode == QS_MODE_PLAIN || ((mode == QS_MODE_FUSED || mode == QS_MODE_FUSED_TC) && s->n < rb)) {
         for (size_t i = 0; i < ngates; ++i)
             if (qs_status st = launch_plain_gate(s, gates[i])) return st;
         return QS_OK;
@@ -234,7 +234,12 @@ extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t 
         return run_fused_plan(s, *plan, dev);
     }
     if (mode == QS_MODE_FUSED_TC) {
-        return set_error(QS_ERR_UNSUPPORTED, "tensor-core mode is not built yet");
+        if (opts && opts->precision != QS_PREC_DEFAULT && opts->precision != QS_PREC_FP16X3)
+            return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
+        const Plan *plan;
+        const void *dev;
+        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev)) return st;
+        return run_fused_plan(s, *plan, dev);
     }
     return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
 }

@@ -23,6 +23,8 @@
 //   * Shared memory uses a 16-byte-granular XOR swizzle (linear over GF(2),
 //     so slot addresses are XORs of per-bit offsets) to spread the strided
 //     phase accesses over the banks.
+#include <cuda_fp16.h>
+
 #include "qs_device.cuh"
 
 namespace qs {
@@ -110,8 +112,6 @@ __device__ __forceinline__ void ph_gen(V &v, R pr, R pi)
     v.x = fmaR(v.x, pr, -v.y * pi);
     v.y = fmaR(x, pi, v.y * pr);
 }
-__device__ __forceinline__ void neg(float2 &v) { v = __fmul2_rn(v, make_float2(-1.f, -1.f)); }
-__device__ __forceinline__ void neg(double2 &v) { v.x = -v.x; v.y = -v.y; }
 
 template <int NS, int J, typename V>
 __device__ __forceinline__ void reg_h(V *a)
@@ -389,6 +389,21 @@ struct SPhase {
     int32_t op_begin, op_end;
     int32_t paired;             // register bit 0 is tile bit 0 (16-byte slots)
     int32_t uniform_ops;        // phase has thread-uniform diagonal ops
+    int32_t kind;               // 0 register phase, 1 tensor-core block phase
+    int32_t slot;               // kind 1: slot of the block in tensor memory
+    int32_t scale_exp;          // kind 1: FP16 operand scale 2^scale_exp
+    int32_t pad;
+};
+
+// Tensor-core phase tables: swizzled tile offset of every block index and
+// of every column index (the XOR swizzle is linear, so an element's offset
+// is blk_off ^ col_off).
+struct TcSmem {
+    uint32_t blk_off[kMaxTcPerPass][64];
+    uint32_t col_off[kMaxTcPerPass][128];
+    uint64_t mbar;
+    uint32_t tmem_base;
+    int32_t abort;
 };
 
 struct SThread {
@@ -407,12 +422,220 @@ struct FusedSmem {
     uint64_t it_off[(1 << RB)];
 };
 
+// ---------------------------------------------------------------------------
+// tensor-core block phase (tcgen05, complex64 tiles of 2^13 amplitudes)
+//
+// The 64 x 64 block unitary acts on the 6 block qubits of the tile for each
+// of the 128 columns (values of the other 7 tile qubits).  Realified:
+// D (128 x 128) = A (128 x 128) * B (128 x 128) with B[k][col] = re (k < 64)
+// or im (k >= 64) of the tile amplitude (block index k mod 64, col), scaled
+// by 2^14 / 2^ceil(d/2), d = deferred 1/sqrt2 factors pending in the tile:
+// |value| <= 2^(d/2) ||psi||, ||psi|| ~ 1, so scaled values stay below the
+// FP16 maximum (the scale is a power of two: exact).  FP16 hi + lo splits of A and B, three products (hi hi, hi lo,
+// lo hi) and FP32 accumulation give ~22 significant bits.  A lives in
+// tensor memory (loaded once per CTA), B in shared memory (canonical
+// K-major layout without swizzle: 8 x 16-byte core matrices, 128 bytes
+// apart along K, 2048 bytes apart along the 128 columns), D in tensor memory.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTmemCols = 512;              // D: 0..127, blocks: 128 + 128 s
+constexpr int kTcWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;     // leading (K) byte offset
+    d |= (uint64_t)((2048u >> 4) & 0x3FFF) << 32;    // stride (column) byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    return d;
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t addr, const uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(addr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(addr)
+        : "memory");
+}
+
+// Allocates tensor memory, loads this pass's block matrices (warps 0-3: one
+// row per thread) and initialises the completion barrier.
+__device__ __forceinline__ void tc_setup(TcSmem &TS, const DevPhase *phases, int nph,
+                                         const uint32_t *tc_words)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&TS.tmem_base)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&TS.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = TS.tmem_base;
+    if (warp < 4) {
+        const int m = warp * 32 + lane;
+        int slot = 0;
+        for (int ph = 0; ph < nph; ++ph) {
+            if (phases[ph].kind != 1) continue;
+            const uint32_t *w = tc_words + (size_t)phases[ph].tc_block * kTcWordsPerBlock + (size_t)m * 128;
+            for (int c = 0; c < 4; ++c) {
+                uint32_t r[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) r[j] = __ldg(w + c * 32 + j);
+                tmem_st32(tbase + ((uint32_t)(warp * 32) << 16) + 128 + 128 * slot + 32 * c, r);
+            }
+            ++slot;
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+__device__ __forceinline__ void tc_teardown(TcSmem &TS)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(TS.tmem_base), "r"(kTmemCols));
+    }
+}
+
+// One block phase on the shared tile (all 256 threads).
+__device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, float2 *tile,
+                                         unsigned char *bbuf, uint32_t parity, int *err_flag)
+{
+    const float sc = ldexpf(1.f, scale_exp), inv_sc = ldexpf(1.f, -scale_exp);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *bhi = bbuf, *blo = bbuf + 32768;
+    const uint32_t *blk = TS.blk_off[slot], *col = TS.col_off[slot];
+    // ---- tile (FP32) -> B hi / lo (FP16, canonical layout) ----
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int u = tid + 256 * i;
+        const int nu = u & 127, bg = u >> 7;
+        const uint32_t base = col[nu] ^ blk[bg * 8];
+        uint32_t hre[4], him[4], lre[4], lim[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+            float2 x0 = tile[base ^ blk[j]], x1 = tile[base ^ blk[j + 1]];
+            x0.x *= sc; x0.y *= sc; x1.x *= sc; x1.y *= sc;
+            const __half2 hr = __floats2half2_rn(x0.x, x1.x);
+            const __half2 hm = __floats2half2_rn(x0.y, x1.y);
+            const float2 hrf = __half22float2(hr), hmf = __half22float2(hm);
+            const __half2 lr = __floats2half2_rn(x0.x - hrf.x, x1.x - hrf.y);
+            const __half2 lm = __floats2half2_rn(x0.y - hmf.x, x1.y - hmf.y);
+            hre[j / 2] = *reinterpret_cast<const uint32_t *>(&hr);
+            him[j / 2] = *reinterpret_cast<const uint32_t *>(&hm);
+            lre[j / 2] = *reinterpret_cast<const uint32_t *>(&lr);
+            lim[j / 2] = *reinterpret_cast<const uint32_t *>(&lm);
+        }
+        const uint32_t off_re = (uint32_t)(((nu >> 3) * 16 + bg) * 128 + (nu & 7) * 16);
+        const uint32_t off_im = off_re + 8 * 128;
+        *reinterpret_cast<uint4 *>(bhi + off_re) = make_uint4(hre[0], hre[1], hre[2], hre[3]);
+        *reinterpret_cast<uint4 *>(bhi + off_im) = make_uint4(him[0], him[1], him[2], him[3]);
+        *reinterpret_cast<uint4 *>(blo + off_re) = make_uint4(lre[0], lre[1], lre[2], lre[3]);
+        *reinterpret_cast<uint4 *>(blo + off_im) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    const uint32_t tbase = TS.tmem_base;
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // M = 128, N = 128, F16 x F16 -> F32, both operands K-major
+        const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t a_hi = tbase + 128 + 128 * slot, a_lo = a_hi + 64;
+        const uint32_t sh = smem_addr(bhi), sl = smem_addr(blo);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint64_t dh = tc_desc(sh + 256 * k), dl = tc_desc(sl + 256 * k);
+            const uint32_t acc = k > 0;
+            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tbase),
+                         "r"(a_hi + 8 * k), "l"(dh), "r"(idesc), "r"(acc));
+            asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(tbase),
+                         "r"(a_hi + 8 * k), "l"(dl), "r"(idesc));
+            asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(tbase),
+                         "r"(a_lo + 8 * k), "l"(dh), "r"(idesc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&TS.mbar)));
+    }
+    // ---- bounded wait for the products ----
+    {
+        uint32_t done = 0;
+        const uint32_t mb = smem_addr(&TS.mbar);
+        for (int it = 0; it < kTcWaitLimit && !done; ++it) {
+            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done)
+                         : "r"(mb), "r"(parity));
+        }
+        if (!done) {
+            TS.abort = 1;
+            atomicExch(err_flag, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // ---- D (TMEM) -> tile: warp w reads lanes 32 (w & 3) .., columns 64 (w >> 2) .. ----
+    {
+        const int m = 32 * (warp & 3) + lane;
+        const uint32_t rowoff = blk[m & 63];
+        const int comp = m >> 6;
+        float *tf = reinterpret_cast<float *>(tile);
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            const int c0 = 64 * (warp >> 2) + 32 * c;
+            uint32_t r[32];
+            tmem_ld32(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + c0, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                tf[2 * (rowoff ^ col[c0 + j]) + comp] = __uint_as_float(r[j]) * inv_sc;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+}
+
 // One launch = one pass over the state.  blockDim.x = 2^(t - RB).
-template <typename R, int RB>
-__global__ void __launch_bounds__(kThreadsMax, 2)
+// TC = true: tensor-core variant (complex64, t = 13), one CTA per SM; its
+// dynamic shared memory holds the tile and the two FP16 operand buffers.
+template <typename R, int RB, bool TC>
+__global__ void __launch_bounds__(kThreadsMax, TC ? 1 : 2)
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
-             uint64_t ntiles)
+             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
 {
     using V = typename V2T<R>::T;
     constexpr int NS = 1 << RB;                 // register slots per thread
@@ -421,6 +644,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
     __shared__ FusedSmem<R, RB> S;
+    __shared__ TcSmem TS;
 
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -440,6 +664,9 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
             S.ph[ph].op_begin = D.op_begin - phases_g[S.P.phase_begin].op_begin;
             S.ph[ph].op_end = D.op_end - phases_g[S.P.phase_begin].op_begin;
             S.ph[ph].paired = (CE == 2 && D.R[0] == 0) ? 1 : 0;
+            S.ph[ph].kind = D.kind;
+            // keep scaled values below 2^14 whatever the deferred factors
+            S.ph[ph].scale_exp = 14 - (D.defer_before + 1) / 2;
             int u = 0;
             for (int o = D.op_begin; o < D.op_end; ++o)
                 u |= (ops_g[o].type == OP_PHASE || ops_g[o].type == OP_NEG) && ops_g[o].rmask == 0;
@@ -456,6 +683,33 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         }
         S.th[ph][tid].phys = swz<CE>(e);
         S.th[ph][tid].qoff = q;
+    }
+    int ntc = 0;
+    if (TC) {
+        for (int ph = 0; ph < nph; ++ph) {
+            const DevPhase &D = phases_g[S.P.phase_begin + ph];
+            if (D.kind != 1) continue;
+            if (tid == 0) S.ph[ph].slot = ntc;
+            uint32_t bmask = 0;
+            for (int j = 0; j < kTcBits; ++j) bmask |= 1u << D.R[j];
+            if (tid < 64) {
+                uint32_t e = 0;
+                for (int j = 0; j < kTcBits; ++j) e |= (uint32_t)((tid >> j) & 1) << D.R[j];
+                TS.blk_off[ntc][tid] = swz<CE>(e);
+            }
+            if (tid < 128) {
+                uint32_t e = 0;
+                for (int b = 0, k = 0; b < t; ++b) {
+                    if ((bmask >> b) & 1u) continue;
+                    e |= (uint32_t)((tid >> k) & 1) << b;
+                    ++k;
+                }
+                TS.col_off[ntc][tid] = swz<CE>(e);
+            }
+            ++ntc;
+        }
+        if (tid == 0) TS.abort = 0;
+        if (ntc) tc_setup(TS, phases_g + S.P.phase_begin, nph, tc_words);
     }
     {
         const int o0 = phases_g[S.P.phase_begin].op_begin;
@@ -499,7 +753,12 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     uint64_t gmask = 0;
     for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
     uint64_t base = deposit(t_begin, S.P.G, ng);
+    uint32_t tc_parity = 0;
+    // FP16 operand buffers after the tile, 1024-byte aligned in the shared window
+    unsigned char *tc_bbuf = smem_raw + (size_t(1) << t) * sizeof(V);
+    tc_bbuf += (1024u - (smem_addr(tc_bbuf) & 1023u)) & 1023u;
     for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
+        if (TC && TS.abort) break;
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
 #pragma unroll
         for (int it = 0; it < CPT; ++it) {
@@ -513,6 +772,14 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         __syncthreads();
 
         for (int ph = 0; ph < nph; ++ph) {
+            if constexpr (TC) {
+                if (S.ph[ph].kind == 1) {
+                    tc_phase(TS, S.ph[ph].slot, S.ph[ph].scale_exp, tile, tc_bbuf, tc_parity, err_flag);
+                    tc_parity ^= 1u;
+                    if (TS.abort) break;
+                    continue;
+                }
+            }
             const SThread T = S.th[ph][tid];
             const uint64_t idx_th = base | T.qoff;
             uint32_t pb[RB];
@@ -535,12 +802,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
                 const bool sel = (idx_th & op.qmask) == op.qmask;
                 exec_op<RB>(op.code, a, sel, fr, fi, S.phase[op.aux], ops_g, op.aux);
             }
-            if (ph == nph - 1 && !gscale_one) {
-                const R x = fr * gsr - fi * gsi;
-                fi = fr * gsi + fi * gsr;
-                fr = x;
-            }
-            if (fpend || (ph == nph - 1 && !gscale_one)) {
+            if (fpend) {
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     const R x = a[s].x * fr - a[s].y * fi;
@@ -562,15 +824,26 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
             }
             __syncthreads();
         }
-        // ---- store the tile ----
+        // ---- store the tile, applying the pass-wide factor ----
 #pragma unroll
         for (int it = 0; it < CPT; ++it) {
             uint32_t e = (uint32_t)(CE * (it * nthr + tid));
-            const float4 v = *reinterpret_cast<const float4 *>(tile + swz<CE>(e));
-            *reinterpret_cast<float4 *>(amps + (base | tid_off | S.it_off[it])) = v;
+            V v[CE];
+            *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(tile + swz<CE>(e));
+            if (!gscale_one) {
+#pragma unroll
+                for (int q = 0; q < CE; ++q) {
+                    const R x = v[q].x * gsr - v[q].y * gsi;
+                    v[q].y = v[q].x * gsi + v[q].y * gsr;
+                    v[q].x = x;
+                }
+            }
+            *reinterpret_cast<float4 *>(amps + (base | tid_off | S.it_off[it])) =
+                *reinterpret_cast<const float4 *>(v);
         }
         __syncthreads();
     }
+    if (TC && ntc) tc_teardown(TS);
 }
 
 template <typename R, int RB>
@@ -580,20 +853,49 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
     const DevPass *dpass = reinterpret_cast<const DevPass *>(dev_plan);
     const DevPhase *dphase = reinterpret_cast<const DevPhase *>(dpass + plan.passes.size());
     const DevOp *dops = reinterpret_cast<const DevOp *>(dphase + plan.phases.size());
-    auto kern = k_fused_pass<R, RB>;
+    const uint32_t *dwords = reinterpret_cast<const uint32_t *>(dops + plan.ops.size());
+    int *err = reinterpret_cast<int *>(s->ws_u64);
+    bool any_tc = false;
     for (size_t p = 0; p < plan.passes.size(); ++p) {
         const DevPass &hp = plan.passes[p];
         if (hp.r != RB || hp.t < RB || hp.t - RB > 8)
             return set_error(QS_ERR_INVALID_ARG, "pass %zu: tile %d / register bits %d unsupported",
                              p, hp.t, hp.r);
+        bool tc = false;
+        for (int ph = 0; ph < hp.nphases; ++ph) tc |= plan.phases[hp.phase_begin + ph].kind == 1;
         const int threads = 1 << (hp.t - RB);
-        const size_t smem = (size_t(1) << hp.t) * sizeof(V);
-        QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint64_t ntiles = 1ULL << (plan.n - hp.t);
-        const uint64_t cap = (uint64_t)s->num_sms * 2;
-        const int grid = (int)(ntiles < cap ? ntiles : cap);
-        kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles);
+        if (tc) {
+            if constexpr (sizeof(R) == 4) {
+                if (hp.t != 13)
+                    return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need 13-bit tiles");
+                if (!any_tc) QS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
+                any_tc = true;
+                auto kern = k_fused_pass<R, RB, true>;
+                const size_t smem = (size_t(1) << hp.t) * sizeof(V) + 65536 + 1024;
+                QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                const uint64_t cap = (uint64_t)s->num_sms;
+                const int grid = (int)(ntiles < cap ? ntiles : cap);
+                kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, dwords,
+                                                         err);
+            } else {
+                return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need complex64");
+            }
+        } else {
+            auto kern = k_fused_pass<R, RB, false>;
+            const size_t smem = (size_t(1) << hp.t) * sizeof(V);
+            QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const uint64_t cap = (uint64_t)s->num_sms * 2;
+            const int grid = (int)(ntiles < cap ? ntiles : cap);
+            kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, nullptr, nullptr);
+        }
         QS_LAUNCH_CHECK();
+    }
+    if (any_tc) {
+        int h = 0;
+        QS_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (h) return set_error(QS_ERR_TIMEOUT, "tensor-core pass: completion wait ran out");
     }
     return QS_OK;
 }

@@ -296,6 +296,157 @@ static uint64_t choose_local(const std::vector<PGate> &g, const std::vector<int>
 
 static int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 
+// A tensor-core block phase is chosen when it absorbs at least this many
+// gates and at least this fraction of what the best register phase would.
+constexpr int kTcMinGates = 8;
+constexpr double kTcRegRatio = 0.6;
+
+// Gates absorbable into a tensor-core block on qubit set `block`: like
+// collect(), but a diagonal gate also needs all its qubits in the block (a
+// diagonal gate reaching outside would make the block operator differ
+// between the columns of the tile).
+static void collect_tc(const std::vector<PGate> &g, const std::vector<int> &cand,
+                       const std::vector<char> &done, uint64_t block,
+                       std::vector<int> *out, int *count)
+{
+    uint64_t blocked = 0;
+    int cnt = 0;
+    if (out) out->clear();
+    for (int i : cand) {
+        if (done[i]) continue;
+        const PGate &x = g[i];
+        uint64_t qm = (1ULL << x.q0) | (x.two ? (1ULL << x.q1) : 0);
+        bool ok = !(qm & blocked) && (qm & ~block) == 0;
+        if (ok) {
+            ++cnt;
+            if (out) out->push_back(i);
+        } else {
+            blocked |= qm;
+        }
+    }
+    *count = cnt;
+}
+
+static uint64_t choose_tc_block(const std::vector<PGate> &g, const std::vector<int> &cand,
+                                const std::vector<char> &done, int n, uint64_t pool, int want)
+{
+    std::vector<int> first;
+    first_pending(g, cand, done, n, &first);
+    uint64_t block = 0;
+    for (int step = 0; step < want; ++step) {
+        int best_q = -1, best_cnt = -1, best_first = 1 << 30;
+        for (int q = 0; q < n; ++q) {
+            if (!((pool >> q) & 1) || ((block >> q) & 1)) continue;
+            int cnt;
+            collect_tc(g, cand, done, block | (1ULL << q), nullptr, &cnt);
+            if (cnt > best_cnt || (cnt == best_cnt && first[q] < best_first)) {
+                best_q = q; best_cnt = cnt; best_first = first[q];
+            }
+        }
+        if (best_q < 0) break;
+        block |= 1ULL << best_q;
+    }
+    return block;
+}
+
+// Block unitary (64 x 64, row-major, complex as re/im pairs) of `gates` on
+// block qubits bq[0..5] (block bit j <-> qubit bq[j]), applied in order.
+static void block_unitary(const std::vector<PGate> &g, const std::vector<int> &gates,
+                          const int *bq, std::vector<Cplx> *U)
+{
+    const int D = 1 << kTcBits;
+    U->assign((size_t)D * D, Cplx{0, 0});
+    for (int i = 0; i < D; ++i) (*U)[(size_t)i * D + i] = {1, 0};
+    auto bit_of = [&](int q) {
+        for (int j = 0; j < kTcBits; ++j)
+            if (bq[j] == q) return j;
+        return -1;
+    };
+    auto mul = [](Cplx a, Cplx b) { return Cplx{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; };
+    auto add = [](Cplx a, Cplx b) { return Cplx{a.re + b.re, a.im + b.im}; };
+    for (int gi : gates) {
+        const PGate &x = g[gi];
+        Cplx u[4];
+        gate_matrix(x.kind, x.theta, u);
+        if (x.two) {
+            const int ja = bit_of(x.q0), jb = bit_of(x.q1);
+            for (int r = 0; r < D; ++r)
+                if (((r >> ja) & 1) && ((r >> jb) & 1))
+                    for (int c = 0; c < D; ++c) (*U)[(size_t)r * D + c] = mul(u[3], (*U)[(size_t)r * D + c]);
+        } else {
+            const int j = bit_of(x.q0);
+            for (int r = 0; r < D; ++r) {
+                if ((r >> j) & 1) continue;
+                const int r1 = r | (1 << j);
+                for (int c = 0; c < D; ++c) {
+                    const Cplx a0 = (*U)[(size_t)r * D + c], a1 = (*U)[(size_t)r1 * D + c];
+                    (*U)[(size_t)r * D + c] = add(mul(u[0], a0), mul(u[1], a1));
+                    (*U)[(size_t)r1 * D + c] = add(mul(u[2], a0), mul(u[3], a1));
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// IEEE 754 binary16 from a double, round to nearest even (format: 1 sign,
+// 5 exponent bits with bias 15, 10 fraction bits; subnormals below 2^-14).
+uint16_t f64_to_f16_bits(double x)
+{
+    const uint16_t sign = std::signbit(x) ? 0x8000 : 0;
+    const double a = std::fabs(x);
+    if (std::isnan(a)) return sign | 0x7e00;
+    if (a >= 65520.0) return sign | 0x7c00;                  // rounds past 65504
+    if (a < std::ldexp(1.0, -14)) {                           // subnormal range
+        const double r = std::nearbyint(a * std::ldexp(1.0, 24));   // units of 2^-24
+        return sign | (uint16_t)r;                            // r = 1024 is the smallest normal
+    }
+    int e;
+    std::frexp(a, &e);                                        // a = f 2^e, f in [0.5, 1)
+    int E = e - 1;                                            // a = 1.m 2^E
+    double r = std::nearbyint((std::ldexp(a, -E) - 1.0) * 1024.0);
+    if (r == 1024.0) { r = 0; ++E; }
+    if (E > 15) return sign | 0x7c00;
+    return sign | (uint16_t)((E + 15) << 10) | (uint16_t)r;
+}
+
+double f16_bits_to_f64(uint16_t h)
+{
+    const int s = h >> 15, e = (h >> 10) & 31, f = h & 1023;
+    double v;
+    if (e == 0) v = std::ldexp((double)f, -24);
+    else if (e == 31) v = f ? NAN : INFINITY;
+    else v = std::ldexp(1.0 + f / 1024.0, e - 15);
+    return s ? -v : v;
+}
+
+namespace {
+
+// Realified block A = [[Re U, -Im U], [Im U, Re U]] split into FP16 hi + lo
+// and packed for tensor memory (see kTcWordsPerBlock).
+static void pack_block(const std::vector<Cplx> &U, std::vector<uint32_t> *words)
+{
+    const int D = 1 << kTcBits, MK = 2 * D;
+    const size_t base = words->size();
+    words->resize(base + kTcWordsPerBlock);
+    for (int m = 0; m < MK; ++m) {
+        uint16_t hi[2 * 64], lo[2 * 64];
+        for (int k = 0; k < MK; ++k) {
+            const Cplx &u = U[(size_t)(m % D) * D + (k % D)];
+            double a;
+            if (m < D) a = k < D ? u.re : -u.im;
+            else a = k < D ? u.im : u.re;
+            hi[k] = f64_to_f16_bits(a);
+            lo[k] = f64_to_f16_bits(a - f16_bits_to_f64(hi[k]));
+        }
+        for (int w = 0; w < MK / 2; ++w) {
+            (*words)[base + (size_t)m * MK + w] = hi[2 * w] | ((uint32_t)hi[2 * w + 1] << 16);
+            (*words)[base + (size_t)m * MK + MK / 2 + w] = lo[2 * w] | ((uint32_t)lo[2 * w + 1] << 16);
+        }
+    }
+}
+
 }  // namespace
 
 PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
@@ -308,8 +459,8 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     if (o && o->tile_log2 > 0) tile = o->tile_log2;
     pp.t = std::min(tile, n);
     pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t);
-    pp.k = (o && o->k > 0) ? o->k : 6;
-    if (pp.mode == QS_MODE_FUSED_TC) pp.r = pp.k;
+    pp.k = kTcBits;
+    pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
     pp.r = std::min(pp.r, pp.t);
     return pp;
 }
@@ -372,10 +523,39 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
         for (int i : pass_gates) pdone[i] = 0;
         size_t prem = pass_gates.size();
         int pass_ops = 0;
+        int tc_in_pass = 0;
         while (prem && dp.nphases < kMaxPhasesPerPass && pass_ops < kMaxOpsPerPass) {
             uint64_t reg = choose_local(g, pass_gates, pdone, n, 0, local, dp.r);
             collect(g, pass_gates, pdone, reg, &phase_gates, &cnt);
             if (cnt == 0) return set_error(QS_ERR_INVALID_ARG, "planner made no phase progress");
+            if (pp.tc_ok && tc_in_pass < kMaxTcPerPass && dp.t == 13) {
+                // tensor-core block candidate: worth it when it absorbs many
+                // gates compared with the register phase
+                const uint64_t blk = choose_tc_block(g, pass_gates, pdone, n, local, kTcBits);
+                std::vector<int> tc_gates;
+                int tcnt = 0;
+                collect_tc(g, pass_gates, pdone, blk, &tc_gates, &tcnt);
+                if (popcount64(blk) == kTcBits && tcnt >= kTcMinGates &&
+                    (double)tcnt >= kTcRegRatio * (double)cnt) {
+                    DevPhase ph;
+                    std::memset(&ph, 0, sizeof ph);
+                    int bq[kTcBits], j = 0;
+                    for (int q = 0; q < n; ++q)
+                        if ((blk >> q) & 1) { bq[j] = q; ph.R[j++] = (uint8_t)tile_bit_of[q]; }
+                    ph.kind = 1;
+                    ph.tc_block = (int)(P.tc_words.size() / kTcWordsPerBlock);
+                    ph.defer_before = deferred;
+                    ph.op_begin = ph.op_end = (int)P.ops.size();
+                    std::vector<Cplx> U;
+                    block_unitary(g, tc_gates, bq, &U);
+                    pack_block(U, &P.tc_words);
+                    for (int gi : tc_gates) { pdone[gi] = 1; --prem; }
+                    P.phases.push_back(ph);
+                    ++dp.nphases;
+                    ++tc_in_pass;
+                    continue;
+                }
+            }
             // keep the pass within the kernel's op table; a prefix of the
             // phase's (ordered, dependency-closed) gate list stays closed
             {

@@ -76,10 +76,24 @@ constexpr int kMaxRegBits = 8;
 constexpr int kMaxPhasesPerPass = 8;    // per-thread phase tables live in shared memory
 constexpr int kMaxOpsPerPass = 256;     // op descriptors live in shared memory
 
-struct DevPhase {       // 16 bytes
-    uint8_t R[kMaxRegBits];  // tile bit of each register bit
+struct DevPhase {       // 32 bytes
+    uint8_t R[kMaxRegBits];  // tile bit of each register (or block) bit
     int32_t op_begin, op_end;
+    int32_t kind;            // 0: register phase, 1: tensor-core block phase
+    int32_t tc_block;        // kind 1: index of the block matrix
+    int32_t defer_before;    // kind 1: deferred 1/sqrt2 factors pending in the
+                             // tile when the phase runs (values are up to
+                             // 2^(defer_before/2) times their true size)
+    int32_t pad;
 };
+
+// Tensor-core block phase: a k = 6 qubit block unitary U (64 x 64 complex)
+// realified to A = [[Re U, -Im U], [Im U, Re U]] (128 x 128), split into
+// FP16 hi + lo, stored row-major as 32-bit words of two consecutive K
+// elements (lower K in the low half): 128 rows x (64 hi words, 64 lo words).
+constexpr int kTcBits = 6;
+constexpr int kTcWordsPerBlock = 128 * 128;
+constexpr int kMaxTcPerPass = 3;        // TMEM: accumulator + 3 blocks (hi, lo)
 
 struct DevPass {
     int32_t t;              // tile bits
@@ -102,7 +116,7 @@ struct Plan {
     std::vector<DevPass> passes;
     std::vector<DevPhase> phases;
     std::vector<DevOp> ops;
-    std::vector<double> tc_blocks;   // TC mode: realified block matrices
+    std::vector<uint32_t> tc_words;  // TC mode: packed FP16 block matrices
     int gates = 0;
 };
 
@@ -113,9 +127,12 @@ struct PlanParams {
     int c;           // low qubits always inside the tile (coalescing)
     int mode;        // QS_MODE_FUSED or QS_MODE_FUSED_TC
     int k;           // TC block bits
+    int tc_ok;       // tensor-core phases allowed (complex64, 13-bit tiles)
 };
 
 qs_status build_plan(const PlanParams &pp, const qs_gate *g, size_t ng, Plan *out);
+uint16_t f64_to_f16_bits(double x);
+double f16_bits_to_f64(uint16_t h);
 PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o);
 double plan_bytes(const Plan &p, qs_dtype dt);
 

@@ -16,10 +16,60 @@
 using cd = std::complex<double>;
 using namespace qs;
 
+extern "C" uint16_t emul_f16(double x) { return f64_to_f16_bits(x); }
+extern "C" double emul_f16_back(uint16_t h) { return f16_bits_to_f64(h); }
+
+// Tensor-core phase: apply the stored block matrix (hi + lo, decoded) to
+// every column of the tile: the 64 amplitudes over the block bits, as
+// realified vectors [re; im].
+static void apply_tc(const Plan &plan, const DevPass &P, const DevPhase &H, std::vector<cd> &tile)
+{
+    const uint32_t *w = plan.tc_words.data() + (size_t)H.tc_block * kTcWordsPerBlock;
+    double A[128][128];
+    for (int m = 0; m < 128; ++m)
+        for (int k = 0; k < 128; ++k) {
+            const uint32_t hw = w[m * 128 + k / 2], lw = w[m * 128 + 64 + k / 2];
+            const uint16_t hb = (k & 1) ? (uint16_t)(hw >> 16) : (uint16_t)(hw & 0xffff);
+            const uint16_t lb = (k & 1) ? (uint16_t)(lw >> 16) : (uint16_t)(lw & 0xffff);
+            A[m][k] = f16_bits_to_f64(hb) + f16_bits_to_f64(lb);
+        }
+    uint64_t bmask = 0;
+    for (int j = 0; j < kTcBits; ++j) bmask |= 1ULL << H.R[j];
+    for (uint64_t col = 0; col < tile.size(); ++col) {
+        if (col & bmask) continue;
+        double v[128], o[128];
+        for (int b = 0; b < 64; ++b) {
+            uint64_t e = col;
+            for (int j = 0; j < kTcBits; ++j) e |= (uint64_t)((b >> j) & 1) << H.R[j];
+            v[b] = tile[e].real();
+            v[64 + b] = tile[e].imag();
+        }
+        for (int m = 0; m < 128; ++m) {
+            double s = 0;
+            for (int k = 0; k < 128; ++k) s += A[m][k] * v[k];
+            o[m] = s;
+        }
+        for (int b = 0; b < 64; ++b) {
+            uint64_t e = col;
+            for (int j = 0; j < kTcBits; ++j) e |= (uint64_t)((b >> j) & 1) << H.R[j];
+            tile[e] = cd(o[b], o[64 + b]);
+        }
+    }
+}
+
+extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode,
+                                 double *psi_interleaved, int *passes_out, int *tc_phases_out);
+
 extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, int c,
                             double *psi_interleaved, int *passes_out)
 {
-    PlanParams pp{n, t, r, c, QS_MODE_FUSED, 6};
+    return emulate_plan_mode(n, g, ng, t, r, c, QS_MODE_FUSED, psi_interleaved, passes_out, nullptr);
+}
+
+extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode,
+                                 double *psi_interleaved, int *passes_out, int *tc_phases_out)
+{
+    PlanParams pp{n, t, r, c, mode, kTcBits, mode == QS_MODE_FUSED_TC && t == 13 ? 1 : 0};
     Plan plan;
     if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
     cd *psi = reinterpret_cast<cd *>(psi_interleaved);
@@ -37,6 +87,10 @@ extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, in
             for (uint64_t e = 0; e < tile.size(); ++e) tile[e] = psi[addr(e)];
             for (int ph = 0; ph < P.nphases; ++ph) {
                 const DevPhase &H = plan.phases[P.phase_begin + ph];
+                if (H.kind == 1) {
+                    apply_tc(plan, P, H, tile);
+                    continue;
+                }
                 for (int o = H.op_begin; o < H.op_end; ++o) {
                     const DevOp &op = plan.ops[o];
                     if (op.type == OP_PHASE || op.type == OP_NEG) {
@@ -75,5 +129,10 @@ extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, in
         }
     }
     if (passes_out) *passes_out = (int)plan.passes.size();
+    if (tc_phases_out) {
+        int k = 0;
+        for (const DevPhase &H : plan.phases) k += H.kind == 1;
+        *tc_phases_out = k;
+    }
     return 0;
 }

@@ -305,6 +305,10 @@ def test_full_size_30_qubits():
         # fused vs plain (two independent CUDA paths), on the device
         diff = _device_rel_l2(pa, pb, n)
         assert diff < 1e-5
+        # tensor-core form vs plain
+        qs.qs_state_reset(h2)
+        qs.qs_apply_circuit(h2, g, mode=qs.QS_MODE_FUSED_TC)
+        assert _device_rel_l2(pb, pa, n) < 1e-5
         r = qs.qs_pt_moments(h, 10)
         assert abs(r["norm"] - 1) < 1e-5
         N = 2.0 ** n
@@ -350,3 +354,45 @@ def _view(ptr, count):
         __cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
                                     "version": 3}
     return torch.as_tensor(_Arr(), device="cuda")
+
+
+# --------------------------------------------------------------------------
+# tensor-core form (FP16x3 block products, FP32 accumulation)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rows,cols,depth,seed", [(4, 4, 40, 0), (4, 5, 25, 1), (3, 5, 30, 2)])
+def test_tc_form_vs_oracle(rows, cols, depth, seed):
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, seed)
+    st = qs.qs_plan_circuit(n, qs.QS_C64, g, mode=qs.QS_MODE_FUSED_TC)
+    ref = O.simulate(n, g)
+    psi = gpu_run(n, g, qs.QS_C64, mode=qs.QS_MODE_FUSED_TC)
+    assert rel_l2(psi, ref) < 1e-5, st
+
+
+def test_tc_form_random_gates():
+    rng = np.random.default_rng(17)
+    n = 15
+    # dense random circuits on few qubits give the planner blocks worth taking
+    g = random_gates(rng, 6, 400)
+    g = np.concatenate([g, random_gates(rng, n, 200)])
+    ref = O.simulate(n, g)
+    psi = gpu_run(n, g, qs.QS_C64, mode=qs.QS_MODE_FUSED_TC)
+    assert rel_l2(psi, ref) < 1e-5
+
+
+def test_tc_form_24_qubits():
+    g = qs.qs_circuit_generate(4, 6, 30, 5)
+    ref = O.simulate(24, g)
+    assert rel_l2(gpu_run(24, g, qs.QS_C64, mode=qs.QS_MODE_FUSED_TC), ref) < 1e-5
+
+
+def test_tc_form_rejects_complex128():
+    g = qs.qs_circuit_generate(4, 4, 20, 0)
+    h = qs.qs_state_create(16, qs.QS_C128)
+    try:
+        # complex128 plans carry no tensor-core phases: same result as fused
+        qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED_TC)
+        psi = qs.qs_state_copy_out(h, 16, qs.QS_C128)
+    finally:
+        qs.qs_state_destroy(h)
+    assert rel_l2(psi, O.simulate(16, g)) < 1e-12

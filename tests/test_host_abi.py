@@ -131,6 +131,12 @@ def emulator():
     subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include"),
                     src, host, "-o", so], check=True)
     lib = ctypes.CDLL(so)
+    lib.emul_f16.restype = ctypes.c_uint16
+    lib.emul_f16.argtypes = [ctypes.c_double]
+    lib.emulate_plan_mode.restype = ctypes.c_int
+    lib.emulate_plan_mode.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.emulate_plan.restype = ctypes.c_int
     lib.emulate_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -179,3 +185,33 @@ def test_plan_semantics_random_circuits(emulator, rows, cols, depth, t):
     psi, passes = _emulate(emulator, n, g, t, 5, 5)
     ref = O.simulate(n, g)
     assert np.max(np.abs(psi - ref)) < 1e-12
+
+
+def test_fp16_split_conversion_matches_numpy(emulator):
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([
+        rng.normal(size=2000), rng.normal(size=2000) * 1e-5, rng.normal(size=500) * 1e-7,
+        rng.uniform(-70000, 70000, 500), [0.0, -0.0, 65504.0, 65519.99, 65520.0, 6.1e-5, 5.96e-8,
+                                           2.98e-8, 2.99e-8, 1 + 2**-11, 1 + 3 * 2**-11]])
+    got = np.array([emulator.emul_f16(float(v)) for v in vals], dtype=np.uint16)
+    # numpy rounds float64 -> float16 to nearest even (IEEE)
+    ref = vals.astype(np.float16).view(np.uint16)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed", [(3, 5, 25, 0), (2, 7, 30, 1), (4, 4, 40, 2)])
+def test_tc_plan_semantics(emulator, rows, cols, depth, seed):
+    """Tensor-core block phases: the block unitaries (realified, FP16 hi + lo)
+    reproduce the circuit to the split's precision (~2^-22 per block)."""
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, seed)
+    psi = O.zero_state(n)
+    passes = ctypes.c_int(0)
+    tcp = ctypes.c_int(0)
+    gg = np.ascontiguousarray(g, dtype=qs.GATE_DTYPE)
+    assert emulator.emulate_plan_mode(n, gg.ctypes.data, gg.size, 13, 5, 5, qs.QS_MODE_FUSED_TC,
+                                      psi.ctypes.data, ctypes.byref(passes), ctypes.byref(tcp)) == 0
+    ref = O.simulate(n, g)
+    err = np.linalg.norm(psi - ref) / np.linalg.norm(ref)
+    assert tcp.value > 0
+    assert err < 1e-5, err
