@@ -264,6 +264,17 @@ def run_ours(args, rank, world, local):
                              "launches": pst["passes"],
                              "hbm_frac_of_measured": round(pst["bytes"] / (ms / 1e3) / 1e9 / hbm_peak, 4)}
 
+    # ---- 34 qubits (6x6 grid minus two corners, depth 40): the three forms,
+    # apply only, one circuit each (outside the timed region) ----
+    n34 = None
+    if rank == 0 and not args.no_compare and args.workload == DEFAULT_WORKLOAD:
+        qs.qs_state_destroy(h)
+        h = None
+        del probs, samples, probs_host
+        torch.cuda.empty_cache()
+        n34 = forms_34(qs, torch, hbm_peak)
+        h = qs.qs_state_create(n, qs.QS_C64, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(W, dead, n)
@@ -299,6 +310,7 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "last_step": {k: round(v, 6) for k, v in results["last"].items()},
         "forms": compare,
+        "n34": n34,
     }
     if cpu:
         out["cpu_baseline"] = cpu
@@ -307,6 +319,42 @@ def run_ours(args, rank, world, local):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def forms_34(qs, torch, hbm_peak):
+    """Apply-only cycles/s and fraction of measured HBM bandwidth of the plain,
+    fused and tensor-core forms on the 34-qubit depth-40 circuit."""
+    import numpy as np
+    free, _ = torch.cuda.mem_get_info()
+    n = 34
+    if free < (8 << n) + (8 << 30):
+        return {"skipped": "needs %.0f GB free, %.0f GB available" % (((8 << n) + (8 << 30)) / 1e9, free / 1e9)}
+    W = WORKLOADS["grid6x6m2_n34_d40"]
+    dead = np.zeros(36, dtype=np.uint8)
+    dead[0] = dead[35] = 1
+    g = qs.qs_circuit_generate(6, 6, W["depth"], 0, dead)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    out = {"workload": "grid6x6m2_n34_d40", "state_gb": round((8 << n) / 1e9, 1)}
+    try:
+        for name, md in (("fused", qs.QS_MODE_FUSED), ("tc", qs.QS_MODE_FUSED_TC),
+                         ("plain", qs.QS_MODE_PLAIN)):
+            qs.qs_state_reset(h)
+            qs.qs_prepare_circuit(h, g, mode=md)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            qs.qs_apply_circuit(h, g, mode=md)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            st = qs.qs_plan_circuit(n, qs.QS_C64, g, mode=md)
+            nrm = qs.qs_pt_moments(h, 0)["norm"]
+            out[name] = {"apply_ms": round(ms, 1), "cycles_per_s": round(W["depth"] / (ms / 1e3), 2),
+                         "launches": st["passes"], "norm": round(nrm, 7),
+                         "hbm_frac_of_measured": round(st["bytes"] / (ms / 1e3) / 1e9 / hbm_peak, 4)}
+    finally:
+        qs.qs_state_destroy(h)
+    return out
 
 
 def load_traffic(mode, n):

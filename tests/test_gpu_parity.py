@@ -396,3 +396,44 @@ def test_tc_form_rejects_complex128():
     finally:
         qs.qs_state_destroy(h)
     assert rel_l2(psi, O.simulate(16, g)) < 1e-12
+
+
+def test_full_size_34_qubits():
+    """6x6 grid minus two opposite corners, depth 40, complex64 in place
+    (137 GB).  The FP64 oracle would need 275 GB of host memory, so the
+    checks are properties that hold at any size."""
+    import torch
+    torch.cuda.empty_cache()
+    n = 34
+    dead = O.grid_dead_mask(6, 6, [(0, 0), (5, 5)])
+    g = qs.qs_circuit_generate(6, 6, 40, 0, dead)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        # before the first X^1/2 / Y^1/2 the distribution is exactly uniform
+        first = next(i for i, x in enumerate(g) if int(x["kind"]) in (qs.QS_X_HALF, qs.QS_Y_HALF))
+        qs.qs_apply_circuit(h, g[:first])
+        r = qs.qs_pt_moments(h, 4)
+        assert abs(r["norm"] - 1) < 1e-5
+        assert abs(r["entropy"] - n * math.log(2)) < 1e-6 * n
+        assert np.allclose(r["moments"], 1.0, atol=1e-5)
+        # the whole circuit: norm and Porter-Thomas entropy (Sec. pt: spread
+        # 0.75 2^{-n/2}; the FP32 state adds up to ~5e-5 absolute)
+        qs.qs_apply_circuit(h, g[first:])
+        r = qs.qs_pt_moments(h, 10)
+        assert abs(r["norm"] - 1) < 2e-5
+        sigma = 0.75 * 2.0 ** (-n / 2)
+        assert abs(r["entropy"] - (n * math.log(2) - 1 + O.EULER_GAMMA)) < 4 * sigma + 5e-5
+        assert abs(r["moments"][1] - 2) < 0.01
+        x = qs.qs_sample(h, 1000000, 1000)
+        ce, dh = qs.qs_cross_entropy(h, x)
+        assert abs(dh - 1) < 4 * 0.8 / 1000 + 0.002
+        # time reversal through both fused forms: U_tc^dagger ... U |0> = |0>
+        qs.qs_apply_circuit(h, inverse_circuit(g), mode=qs.QS_MODE_FUSED_TC)
+        qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED_TC)
+        qs.qs_apply_circuit(h, inverse_circuit(g), mode=qs.QS_MODE_FUSED)
+        # probability of |0...0>: the first amplitude, read through a view
+        t = _view(qs.qs_state_amplitudes(h), 2)
+        p0 = float(t[0]) ** 2 + float(t[1]) ** 2
+        assert p0 > 1 - 1e-4, p0
+    finally:
+        qs.qs_state_destroy(h)
