@@ -158,23 +158,6 @@ __device__ __forceinline__ void reg_shear(V *a, R k)
         }
 }
 
-template <int NS, int J, typename V, typename R>
-__device__ __forceinline__ void reg_dense(V *a, const R *m)
-{
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-        if (!(s & (1 << J))) {
-            V x = a[s], y = a[s | (1 << J)];
-            V o0, o1;
-            o0.x = m[0] * x.x - m[1] * x.y + m[2] * y.x - m[3] * y.y;
-            o0.y = m[0] * x.y + m[1] * x.x + m[2] * y.y + m[3] * y.x;
-            o1.x = m[4] * x.x - m[5] * x.y + m[6] * y.x - m[7] * y.y;
-            o1.y = m[4] * x.y + m[5] * x.x + m[6] * y.y + m[7] * y.x;
-            a[s] = o0;
-            a[s | (1 << J)] = o1;
-        }
-}
-
 // Phase on the slots whose register bits include all of M.  `tgate` selects
 // the in-place T form (pr = pi = 1/sqrt2).
 template <int NS, int M, typename V, typename R>
@@ -202,64 +185,6 @@ __device__ __forceinline__ void reg_sign(V *a, R sg)
         if ((s & M) == M) mul_sign(a[s], sg);
 }
 
-template <int NS, int M, typename V>
-__device__ __forceinline__ void reg_neg(V *a)
-{
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-        if ((s & M) == M) neg(a[s]);
-}
-
-#define QS_CASE_BIT(J, CALL) case J: CALL(J); break;
-#define QS_CASE_BIT2(C, J, CALL) case C: CALL(J); break;
-
-// type: 0 = H, 1 = X^1/2, 2 = Y^1/2 (deferred-scale forms), 3 = dense 2x2.
-template <int RB, typename V, typename R>
-__device__ __forceinline__ void dispatch_bit_op(int type, int j, V *a, const R *m)
-{
-    constexpr int NS = 1 << RB;
-#define QS_H_(J) reg_h<NS, (J < RB ? J : 0)>(a)
-#define QS_X_(J) reg_xh<NS, (J < RB ? J : 0)>(a)
-#define QS_Y_(J) reg_yh<NS, (J < RB ? J : 0)>(a)
-#define QS_D_(J) reg_dense<NS, (J < RB ? J : 0)>(a, m)
-    switch (type * 8 + j) {
-    QS_CASE_BIT(0, QS_H_) QS_CASE_BIT(1, QS_H_) QS_CASE_BIT(2, QS_H_) QS_CASE_BIT(3, QS_H_)
-    QS_CASE_BIT(4, QS_H_) QS_CASE_BIT(5, QS_H_)
-    QS_CASE_BIT2(8, 0, QS_X_) QS_CASE_BIT2(9, 1, QS_X_) QS_CASE_BIT2(10, 2, QS_X_)
-    QS_CASE_BIT2(11, 3, QS_X_) QS_CASE_BIT2(12, 4, QS_X_) QS_CASE_BIT2(13, 5, QS_X_)
-    QS_CASE_BIT2(16, 0, QS_Y_) QS_CASE_BIT2(17, 1, QS_Y_) QS_CASE_BIT2(18, 2, QS_Y_)
-    QS_CASE_BIT2(19, 3, QS_Y_) QS_CASE_BIT2(20, 4, QS_Y_) QS_CASE_BIT2(21, 5, QS_Y_)
-    QS_CASE_BIT2(24, 0, QS_D_) QS_CASE_BIT2(25, 1, QS_D_) QS_CASE_BIT2(26, 2, QS_D_)
-    QS_CASE_BIT2(27, 3, QS_D_) QS_CASE_BIT2(28, 4, QS_D_) QS_CASE_BIT2(29, 5, QS_D_)
-    default: break;
-    }
-#undef QS_H_
-#undef QS_X_
-#undef QS_Y_
-#undef QS_D_
-}
-
-#define QS_M4(B, F) F(B + 0) F(B + 1) F(B + 2) F(B + 3)
-#define QS_M16(B, F) QS_M4(B, F) QS_M4(B + 4, F) QS_M4(B + 8, F) QS_M4(B + 12, F)
-#define QS_M32(F) QS_M16(0, F) QS_M16(16, F)
-
-template <int RB, typename V, typename R>
-__device__ __forceinline__ void dispatch_mask_phase(int mask, V *a, R pr, R pi, bool tgate)
-{
-    constexpr int NS = 1 << RB;
-#define QS_PC(M) case M: reg_phase<NS, (M) & (NS - 1)>(a, pr, pi, tgate); break;
-    switch (mask) { QS_M32(QS_PC) default: break; }
-#undef QS_PC
-}
-
-template <int RB, typename V>
-__device__ __forceinline__ void dispatch_mask_neg(int mask, V *a)
-{
-    constexpr int NS = 1 << RB;
-#define QS_NC(M) case M: reg_neg<NS, (M) & (NS - 1)>(a); break;
-    switch (mask) { QS_M32(QS_NC) default: break; }
-#undef QS_NC
-}
 
 // Trailing zeros of a positive integer known at compile time (the callers
 // use it on unrolled loop indices, so it folds to a constant).
@@ -273,9 +198,10 @@ template <> struct CtzT<0> { static constexpr int value = 0; };
 // so slots s and s+1 are one 16-byte unit).
 template <int COUNT, int SHIFT>
 struct SlotIO {
+    // offsets are in bytes from the start of the tile
     template <int I, typename V>
     struct Step {
-        static __device__ __forceinline__ void ld(V *a, const V *tile, uint32_t off, const uint32_t *pb)
+        static __device__ __forceinline__ void ld(V *a, const char *tile, uint32_t off, const uint32_t *pb)
         {
             if (I) off ^= pb[SHIFT + CtzT<I>::value];
             constexpr int s = (I ^ (I >> 1)) << SHIFT;
@@ -283,37 +209,31 @@ struct SlotIO {
                 const float4 v = *reinterpret_cast<const float4 *>(tile + off);
                 a[s].x = v.x; a[s].y = v.y; a[s + 1].x = v.z; a[s + 1].y = v.w;
             } else {
-                a[s] = tile[off];
+                a[s] = *reinterpret_cast<const V *>(tile + off);
             }
             Step<I + 1, V>::ld(a, tile, off, pb);
         }
-        static __device__ __forceinline__ void st(const V *a, V *tile, uint32_t off, const uint32_t *pb)
+        static __device__ __forceinline__ void st(const V *a, char *tile, uint32_t off, const uint32_t *pb)
         {
             if (I) off ^= pb[SHIFT + CtzT<I>::value];
             constexpr int s = (I ^ (I >> 1)) << SHIFT;
             if (SHIFT)
                 *reinterpret_cast<float4 *>(tile + off) = make_float4(a[s].x, a[s].y, a[s + 1].x, a[s + 1].y);
             else
-                tile[off] = a[s];
+                *reinterpret_cast<V *>(tile + off) = a[s];
             Step<I + 1, V>::st(a, tile, off, pb);
         }
     };
     template <typename V>
     struct Step<COUNT, V> {
-        static __device__ __forceinline__ void ld(V *, const V *, uint32_t, const uint32_t *) {}
-        static __device__ __forceinline__ void st(const V *, V *, uint32_t, const uint32_t *) {}
+        static __device__ __forceinline__ void ld(V *, const char *, uint32_t, const uint32_t *) {}
+        static __device__ __forceinline__ void st(const V *, char *, uint32_t, const uint32_t *) {}
     };
     template <typename V>
-    static __device__ __forceinline__ void load(V *a, const V *tile, uint32_t off, const uint32_t *pb)
+    static __device__ __forceinline__ void load(V *a, const char *tile, uint32_t off, const uint32_t *pb)
     { Step<0, V>::ld(a, tile, off, pb); }
     template <typename V>
-    static __device__ __forceinline__ void store(const V *a, V *tile, uint32_t off, const uint32_t *pb)
-    { Step<0, V>::st(a, tile, off, pb); }
-    template <typename V>
-    static __device__ __forceinline__ void load_pairs(V *a, const V *tile, uint32_t off, const uint32_t *pb)
-    { Step<0, V>::ld(a, tile, off, pb); }
-    template <typename V>
-    static __device__ __forceinline__ void store_pairs(const V *a, V *tile, uint32_t off, const uint32_t *pb)
+    static __device__ __forceinline__ void store(const V *a, char *tile, uint32_t off, const uint32_t *pb)
     { Step<0, V>::st(a, tile, off, pb); }
 };
 
@@ -321,29 +241,46 @@ struct SlotIO {
 // diagonal op's selection outside the register set (true when the op has
 // none); diagonal ops apply branch-free with sign / identity when unmet.
 template <int RB, typename V, typename R>
-__device__ __forceinline__ void exec_op(uint32_t code, V *a, bool sel, R &fr, R &fi,
-                                        const R *phase, const DevOp *ops_g, uint32_t aux)
+__device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, uint64_t qmask, R &fr,
+                                        R &fi, const R *phase)
 {
     constexpr int NS = 1 << RB;
     const R c = (R)0.70710678118654752440;
+    // selection bits outside the register set (thread / tile constant); only
+    // the diagonal cases read it
+#define sel ((idx_th & qmask) == qmask)
 #define QS_SGN (sel ? (R)-1 : (R)1)
 #define QS_PR (sel ? phase[0] : (R)1)
 #define QS_PI (sel ? phase[1] : (R)0)
     switch (code & ~K_COND) {
-#define QS_B(J)                                                          \
-    case K_H + J: reg_h<NS, (J < RB ? J : 0)>(a); break;                 \
-    case K_XH + J: reg_xh<NS, (J < RB ? J : 0)>(a); break;               \
-    case K_YH + J: reg_yh<NS, (J < RB ? J : 0)>(a); break;               \
-    case K_SHX + J: reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;   \
-    case K_SHY + J: reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
-    QS_B(0) QS_B(1) QS_B(2) QS_B(3) QS_B(4) QS_B(5)
+#define QS_B(J)                                                                  \
+    case K_H + J: reg_h<NS, J>(a); break;                                        \
+    case K_XH + J: reg_xh<NS, J>(a); break;                                      \
+    case K_YH + J: reg_yh<NS, J>(a); break;                                      \
+    case K_SHX + J: reg_shear<NS, J, 0>(a, phase[0]); break;                     \
+    case K_SHY + J: reg_shear<NS, J, 1>(a, phase[0]); break;
+    QS_B(0) QS_B(1) QS_B(2) QS_B(3)
 #undef QS_B
-#define QS_M(M)                                                                    \
-    case K_T + M: reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break;           \
-    case K_NEG + M: reg_sign<NS, ((M) & (NS - 1))>(a, QS_SGN); break;              \
-    case K_PH + M: reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
-    QS_M32(QS_M)
+#define QS_M(M)                                                                  \
+    case K_T + M: reg_phase<NS, M>(a, c, c, true); break;                        \
+    case K_NEG + M: reg_sign<NS, M>(a, QS_SGN); break;                           \
+    case K_PH + M: reg_phase<NS, M>(a, QS_PR, QS_PI, false); break;
+    // one- and two-qubit gates select at most two register bits
+    QS_M(1) QS_M(2) QS_M(4) QS_M(8) QS_M(3) QS_M(5) QS_M(6) QS_M(9) QS_M(10) QS_M(12)
 #undef QS_M
+#define QS_B4(J)                                                                 \
+    case K_H + J: reg_h<NS, (J < RB ? J : 0)>(a); break;                         \
+    case K_XH + J: reg_xh<NS, (J < RB ? J : 0)>(a); break;                       \
+    case K_YH + J: reg_yh<NS, (J < RB ? J : 0)>(a); break;                       \
+    case K_SHX + J: reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;      \
+    case K_SHY + J: reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
+#define QS_M4(M)                                                                 \
+    case K_T + M: reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break;         \
+    case K_NEG + M: reg_sign<NS, ((M) & (NS - 1))>(a, QS_SGN); break;            \
+    case K_PH + M: reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
+    QS_B4(4) QS_M4(16) QS_M4(17) QS_M4(18) QS_M4(20) QS_M4(24)
+#undef QS_B4
+#undef QS_M4
     case K_UT: {
         // T on a selection outside the register set: f *= e^{i pi/4} if sel
         const R tr = sel ? c : (R)1, ti = sel ? c : (R)0;
@@ -365,6 +302,7 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, bool sel, R &fr, R 
 #undef QS_SGN
 #undef QS_PR
 #undef QS_PI
+#undef sel
 }
 
 // Deposits the low bits of x into the positions listed in pos[0..cnt).
@@ -385,7 +323,7 @@ struct SOp {
 };
 
 struct SPhase {
-    uint32_t pb[kMaxRegBits];   // swizzled tile offset of each register bit
+    uint32_t pb[kMaxRegBits];   // swizzled tile byte offset of each register bit
     int32_t op_begin, op_end;
     int32_t paired;             // register bit 0 is tile bit 0 (16-byte slots)
     int32_t uniform_ops;        // phase has thread-uniform diagonal ops
@@ -407,7 +345,7 @@ struct TcSmem {
 };
 
 struct SThread {
-    uint32_t phys;              // swizzled tile offset of the thread's slot 0
+    uint32_t phys;              // swizzled tile byte offset of the thread's slot 0
     uint32_t pad;
     uint64_t qoff;              // qubit-index bits of the thread's tile bits
 };
@@ -660,7 +598,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         uint32_t regmask = 0;
         for (int j = 0; j < RB; ++j) regmask |= 1u << D.R[j];
         if (tid == 0) {
-            for (int j = 0; j < RB; ++j) S.ph[ph].pb[j] = swz<CE>(1u << D.R[j]);
+            for (int j = 0; j < RB; ++j) S.ph[ph].pb[j] = swz<CE>(1u << D.R[j]) * (uint32_t)sizeof(V);
             S.ph[ph].op_begin = D.op_begin - phases_g[S.P.phase_begin].op_begin;
             S.ph[ph].op_end = D.op_end - phases_g[S.P.phase_begin].op_begin;
             S.ph[ph].paired = (CE == 2 && D.R[0] == 0) ? 1 : 0;
@@ -681,7 +619,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
             q |= (uint64_t)bit << S.P.L[b];
             ++k;
         }
-        S.th[ph][tid].phys = swz<CE>(e);
+        S.th[ph][tid].phys = swz<CE>(e) * (uint32_t)sizeof(V);
         S.th[ph][tid].qoff = q;
     }
     int ntc = 0;
@@ -754,6 +692,12 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
     uint64_t base = deposit(t_begin, S.P.G, ng);
     uint32_t tc_parity = 0;
+    // runs of consecutive amplitudes per tile = 2^(t - c); with c = RB for
+    // complex64 (5) and complex128 (4) there is one 256-byte run per thread
+    constexpr int kRunBits = (sizeof(V) == 8) ? 5 : 4;
+    const bool prefetch_runs = (t - kRunBits) >= 0 && (1 << (t - kRunBits)) == nthr &&
+                               S.P.L[kRunBits - 1] == kRunBits - 1;
+    const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
     // FP16 operand buffers after the tile, 1024-byte aligned in the shared window
     unsigned char *tc_bbuf = smem_raw + (size_t(1) << t) * sizeof(V);
     tc_bbuf += (1024u - (smem_addr(tc_bbuf) & 1023u)) & 1023u;
@@ -770,6 +714,13 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncthreads();
+        // warm L2 with the next tile: thread i prefetches run i (2^c
+        // consecutive amplitudes, 256 bytes) while this tile is processed
+        if (prefetch_runs && tau + 1 < t_end) {
+            const uint64_t nb = ((base | ~gmask) + 1) & gmask;
+            const V *p = amps + (nb | run_off);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
+        }
 
         for (int ph = 0; ph < nph; ++ph) {
             if constexpr (TC) {
@@ -789,18 +740,15 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
             V a[NS];
             // slots in Gray-code order: one XOR per slot address
             if (CE == 2 && paired)
-                SlotIO<NS / 2, 1>::template load_pairs<V>(a, tile, T.phys, pb);
+                SlotIO<NS / 2, 1>::template load<V>(a, reinterpret_cast<const char *>(smem_raw), T.phys, pb);
             else
-                SlotIO<NS, 0>::template load<V>(a, tile, T.phys, pb);
+                SlotIO<NS, 0>::template load<V>(a, reinterpret_cast<const char *>(smem_raw), T.phys, pb);
             R fr = (R)1, fi = (R)0;             // thread-uniform pending factor
             const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end;
             const bool fpend = S.ph[ph].uniform_ops != 0;
             for (int o = ob; o < oe; ++o) {
                 const SOp<R> op = S.ops[o];
-                // selection bits outside the register set (thread / tile
-                // constant): +1 or -1 sign, or identity phase when unmet
-                const bool sel = (idx_th & op.qmask) == op.qmask;
-                exec_op<RB>(op.code, a, sel, fr, fi, S.phase[op.aux], ops_g, op.aux);
+                exec_op<RB>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
             }
             if (fpend) {
 #pragma unroll
@@ -818,9 +766,9 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
                 for (int j = 0; j < RB; ++j) pb2[j] = S.ph[ph].pb[j];
                 const uint32_t phys = S.th[ph][tid].phys;
                 if (CE == 2 && S.ph[ph].paired)
-                    SlotIO<NS / 2, 1>::template store_pairs<V>(a, tile, phys, pb2);
+                    SlotIO<NS / 2, 1>::template store<V>(a, reinterpret_cast<char *>(smem_raw), phys, pb2);
                 else
-                    SlotIO<NS, 0>::template store<V>(a, tile, phys, pb2);
+                    SlotIO<NS, 0>::template store<V>(a, reinterpret_cast<char *>(smem_raw), phys, pb2);
             }
             __syncthreads();
         }
