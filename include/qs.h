@@ -219,6 +219,24 @@ qs_status qs_sample_noalloc(int n, qs_dtype dt, const void *device_amps, void *c
 qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples,
                            uint64_t m, double *ce, double *delta_h);
 
+/* Gradient of the sample cross entropy L(theta) = -(1/m) sum_j ln p_theta(x_j)
+ * (the CE of Eq. ae) with respect to the angle of every parameterised gate
+ * (RX, RY, RZ, CPHASE) of `gates`, by the adjoint method: the call resets the
+ * state to |0...0>, evolves it with `gates` (form chosen by `opts`, NULL =
+ * fused), computes *loss = L on the m sample indices `samples` (host or
+ * device), seeds lambda = -sum_j psi(x_j) / (m p(x_j)) |x_j>, and sweeps the
+ * gates in reverse, uncomputing psi and lambda with G^dagger and reading
+ *   dL/dtheta = Im <lambda|P|psi>            for R_P(theta) = exp(-i theta/2 P),
+ *   dL/dphi   = -2 Im <lambda|Pi_11|psi>     for CPHASE(phi).
+ * grad[k] receives the derivative for gate k (0 for fixed gates).  Uses one
+ * extra state vector (lambda), allocated stream-ordered for the call.  On
+ * return the state holds the uncomputed vector (|0...0> up to rounding).
+ * The paper has no gradients; this serves circuit-parameter studies around
+ * the paper's cross-entropy benchmark.  Synchronous. */
+qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
+                              const uint64_t *samples, uint64_t m, const qs_opts *opts,
+                              double *loss, double *grad);
+
 /* Porter-Thomas statistics of p_U in one read of the state, FP64
  * accumulation (Sec. "Convergence to Porter-Thomas").  They are computed
  * for the normalised distribution p / S, S = sum p, so that the rounding

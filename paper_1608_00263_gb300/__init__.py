@@ -24,7 +24,8 @@ __all__ = [
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
     "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
-    "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "library_path",
+    "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
+    "library_path",
 ]
 
 
@@ -157,6 +158,23 @@ def qs_cross_entropy(h, samples):
     dh = ctypes.c_double()
     N.check(N.lib().qs_cross_entropy(h, _ptr(samples), m, ctypes.byref(ce), ctypes.byref(dh)))
     return ce.value, dh.value
+
+
+def qs_adjoint_gradient(h, gates, samples, mode=QS_MODE_FUSED):
+    """Returns (loss, grad): the sample cross entropy and its derivative with
+    respect to each gate's angle (0 for fixed gates), by the adjoint method."""
+    g = _gates(gates)
+    if isinstance(samples, np.ndarray):
+        samples = np.ascontiguousarray(samples, dtype=np.uint64)
+        m = samples.size
+    else:
+        m = samples.numel()
+    grad = np.zeros(g.size, dtype=np.float64)
+    loss = ctypes.c_double()
+    o = _opts(mode, QS_PREC_DEFAULT, 0, 0)
+    N.check(N.lib().qs_adjoint_gradient(h, g.ctypes.data if g.size else None, g.size, _ptr(samples), m,
+                                        ctypes.byref(o), ctypes.byref(loss), grad.ctypes.data))
+    return loss.value, grad
 
 
 def qs_pt_moments(h, kmax=10):

@@ -65,6 +65,7 @@ SIGNATURES = {
     "qs_sample_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, U64, U64, P]),
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),
     "qs_pt_moments": (ctypes.c_int, [P, ctypes.c_int, PD, PD, PD, PD]),
+    "qs_adjoint_gradient": (ctypes.c_int, [P, P, ctypes.c_size_t, P, U64, ctypes.POINTER(qs_opts), PD, P]),
     "qs_state_copy_out": (ctypes.c_int, [P, P]),
     "qs_state_copy_in": (ctypes.c_int, [P, P]),
     "qs_circuit_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, U64, P,

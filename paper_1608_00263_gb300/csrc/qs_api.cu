@@ -370,3 +370,35 @@ extern "C" qs_status qs_state_copy_in(qs_state *s, const void *host_amps)
     QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return QS_OK;
 }
+
+extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
+                                         const uint64_t *samples, uint64_t m, const qs_opts *opts,
+                                         double *loss, double *grad)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
+    if (m == 0 || !samples) return set_error(QS_ERR_INVALID_ARG, "empty sample");
+    if (ngates && !grad) return set_error(QS_ERR_INVALID_ARG, "grad is NULL");
+    DeviceGuard g(s->device);
+    if (qs_status st = launch_init_zero(s)) return st;
+    if (qs_status st = qs_apply_circuit(s, gates, ngates, opts)) return st;
+    uint64_t *buf = nullptr;
+    const uint64_t *dx = samples;
+    if (!is_device_ptr(samples)) {
+        QS_CUDA_TRY(cudaMallocAsync((void **)&buf, m * sizeof(uint64_t), s->stream));
+        cudaError_t e = cudaMemcpyAsync(buf, samples, m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(buf, s->stream);
+            return set_error(QS_ERR_CUDA, "sample upload: %s", cudaGetErrorString(e));
+        }
+        dx = buf;
+    }
+    double ce = 0;
+    qs_status st = cross_entropy_run(s, dx, m, &ce);   // also range-checks the samples
+    if (!st) st = adjoint_run(s, gates, ngates, dx, m, grad);
+    if (buf) cudaFreeAsync(buf, s->stream);
+    cudaStreamSynchronize(s->stream);
+    if (!st && loss) *loss = ce;
+    return st;
+}

@@ -181,6 +181,8 @@ qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed,
                       uint64_t *dev_out);
 qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples,
                             uint64_t m, double *ce);
+qs_status adjoint_run(qs_state *s, const qs_gate *g, size_t ng, const uint64_t *dev_x,
+                      uint64_t m, double *grad);
 
 size_t dtype_bytes(qs_dtype dt);
 
