@@ -275,6 +275,15 @@ def run_ours(args, rank, world, local):
         n34 = forms_34(qs, torch, hbm_peak)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
 
+    ens = None
+    if rank == 0 and not args.no_compare and args.workload == DEFAULT_WORKLOAD:
+        if h is not None:
+            qs.qs_state_destroy(h)
+        h = None
+        torch.cuda.empty_cache()
+        ens = ensemble_4096(qs, torch, hbm_peak)
+        h = qs.qs_state_create(n, qs.QS_C64, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(W, dead, n)
@@ -311,6 +320,7 @@ def run_ours(args, rank, world, local):
         "last_step": {k: round(v, 6) for k, v in results["last"].items()},
         "forms": compare,
         "n34": n34,
+        "ensemble": ens,
     }
     if cpu:
         out["cpu_baseline"] = cpu
@@ -355,6 +365,52 @@ def forms_34(qs, torch, hbm_peak):
     finally:
         qs.qs_state_destroy(h)
     return out
+
+
+def ensemble_instance(s):
+    """Instance s of the 4096-circuit ensemble: n uniform in 12..24, depth
+    uniform in 10..40 (SplitMix64 finaliser of s), 3 or 4 grid rows."""
+    M = (1 << 64) - 1
+
+    def mix64(z):
+        z &= M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+    n = 12 + mix64(s) % 13
+    depth = 10 + mix64(s ^ 0xD1B54A32D192ED03) % 31
+    rows = 3 if n <= 15 else 4
+    cols = -(-n // rows)
+    dead = [0] * (rows * cols)
+    for k in range(rows * cols - n):
+        dead[rows * cols - 1 - k] = 1
+    return n, depth, rows, cols, dead
+
+
+def ensemble_4096(qs, torch, hbm_peak):
+    """Aggregate cycles/s and effective bandwidth of the batched ensemble
+    (graph replay of 4096 circuits, statistics included)."""
+    import numpy as np
+    inst = [ensemble_instance(s) for s in range(4096)]
+    gl = [qs.qs_circuit_generate(r, c, d, s, np.array(dd, dtype=np.uint8))
+          for s, (n, d, r, c, dd) in enumerate(inst)]
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        t0 = time.perf_counter()
+        qs.qs_batch_run(b, gl, kmax=10)            # plan, capture, first run
+        first = time.perf_counter() - t0
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            st = qs.qs_batch_run(b, gl, kmax=10)
+        dt = (time.perf_counter() - t0) / reps
+    finally:
+        qs.qs_batch_destroy(b)
+    cycles = sum(x[1] for x in inst)
+    bytes_state = sum(8 << x[0] for x in inst)
+    return {"instances": 4096, "state_gb": round(bytes_state / 1e9, 1), "first_run_s": round(first, 3),
+            "replay_s": round(dt, 4), "cycles_per_s": round(cycles / dt, 1),
+            "mean_norm": round(float(np.mean(st[:, 0])), 7)}
 
 
 def load_traffic(mode, n):

@@ -255,6 +255,33 @@ qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
 qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments,
                         double *entropy, double *uniform_ce, double *norm);
 
+/* Batched ensemble of independent circuits (the paper's statistics are
+ * ensemble averages over circuit instances, Secs. "Characterizing quantum
+ * supremacy" and "Convergence to Porter-Thomas").  All `count` complex64
+ * states (nqubits[i] in 5..30) stay resident in one device allocation made
+ * by qs_batch_create; work is ordered on cuda_stream (NULL = legacy default
+ * stream). */
+typedef struct qs_batch qs_batch;
+qs_status qs_batch_create(int count, const int *nqubits, void *cuda_stream, qs_batch **out);
+
+/* Resets every state to |0...0>, applies instance i's gates
+ * gates[offsets[i] .. offsets[i+1]) (host arrays, offsets has count+1
+ * entries, offsets[0] = 0), and writes per-instance statistics of the
+ * normalised output distribution (as qs_pt_moments) to stats[i*(3+kmax) ..]:
+ * norm, entropy, uniform cross entropy, moments 1..kmax (kmax <= 10; stats
+ * may be NULL when kmax = 0).  Instances run in lockstep rounds of the fused
+ * tile pass, one launch per round and tile size over all instances; the
+ * device work is captured once into a CUDA graph and replayed while the gate
+ * lists are unchanged (a new gate list replans and recaptures).
+ * Synchronous. */
+qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
+                       double *stats);
+
+/* Device pointer of instance i's amplitudes (canonical order). */
+qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps);
+
+qs_status qs_batch_destroy(qs_batch *b);
+
 /* Copies the amplitudes to / from a host buffer of 2^n amplitudes in
  * canonical order (testing, checkpoints).  Synchronous. */
 qs_status qs_state_copy_out(const qs_state *s, void *host_amps);

@@ -25,6 +25,7 @@ __all__ = [
     "qs_plan_circuit",
     "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
+    "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy",
     "library_path",
 ]
 
@@ -209,3 +210,34 @@ def qs_circuit_generate(rows, cols, depth, seed, dead=None):
     N.check(N.lib().qs_circuit_generate(rows, cols, dp, depth, seed & (2**64 - 1),
                                         out.ctypes.data, ctypes.byref(cnt)))
     return out
+
+
+def qs_batch_create(nqubits, stream=None):
+    n = np.ascontiguousarray(nqubits, dtype=np.int32)
+    h = ctypes.c_void_p()
+    N.check(N.lib().qs_batch_create(int(n.size), n.ctypes.data, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def qs_batch_run(b, gate_lists, kmax=10):
+    """Runs every instance's gate list; returns an array (count, 3 + kmax):
+    norm, entropy, uniform cross entropy, moments 1..kmax."""
+    gl = [_gates(g) for g in gate_lists]
+    offsets = np.zeros(len(gl) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([g.size for g in gl])
+    gates = np.concatenate(gl) if gl else np.zeros(0, dtype=GATE_DTYPE)
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    out = np.zeros((len(gl), 3 + kmax), dtype=np.float64)
+    N.check(N.lib().qs_batch_run(b, gates.ctypes.data if gates.size else None, offsets.ctypes.data, kmax,
+                                 out.ctypes.data))
+    return out
+
+
+def qs_batch_state(b, i):
+    p = ctypes.c_void_p()
+    N.check(N.lib().qs_batch_state(b, i, ctypes.byref(p)))
+    return p.value
+
+
+def qs_batch_destroy(b):
+    N.check(N.lib().qs_batch_destroy(b))

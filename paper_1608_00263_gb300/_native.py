@@ -66,6 +66,10 @@ SIGNATURES = {
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),
     "qs_pt_moments": (ctypes.c_int, [P, ctypes.c_int, PD, PD, PD, PD]),
     "qs_adjoint_gradient": (ctypes.c_int, [P, P, ctypes.c_size_t, P, U64, ctypes.POINTER(qs_opts), PD, P]),
+    "qs_batch_create": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.POINTER(P)]),
+    "qs_batch_run": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "qs_batch_state": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P)]),
+    "qs_batch_destroy": (ctypes.c_int, [P]),
     "qs_state_copy_out": (ctypes.c_int, [P, P]),
     "qs_state_copy_in": (ctypes.c_int, [P, P]),
     "qs_circuit_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, U64, P,

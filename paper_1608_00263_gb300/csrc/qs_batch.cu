@@ -1,0 +1,301 @@
+// qs_batch.cu -- batched ensemble of independent random circuits.
+//
+// The paper averages statistics over ensembles of circuit instances (Sec.
+// "Characterizing quantum supremacy": 10 instances per point; Sec.
+// "Convergence to Porter-Thomas": means and spreads over instances).  Here
+// every instance keeps its complex64 state resident in one device buffer;
+// instances advance in lockstep rounds: round r is one launch of the batched
+// fused-pass kernel over (instance, tile range) work items of every
+// instance's pass r (one launch per tile size).  Per-instance statistics
+// follow in two fixed-order reductions.  The device work of a run (reset,
+// rounds, statistics) is captured once into a CUDA graph and replayed while
+// the gate lists stay the same.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "qs_device.cuh"
+
+using namespace qs;
+
+namespace {
+
+constexpr int kItemTiles = 8;              // tiles per work item of a round
+constexpr uint64_t kStatChunk = 1 << 16;   // amplitudes per statistics item
+
+__global__ void k_batch_basis(float2 *amps, const uint64_t *off, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) amps[off[i]] = make_float2(1.f, 0.f);
+}
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ULL)
+{
+    const unsigned char *p = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct qs_batch {
+    int count = 0;
+    std::vector<int> n;
+    std::vector<uint64_t> off;        // element offset of each state
+    uint64_t total = 0;               // elements
+    float2 *amps = nullptr;
+    cudaStream_t user_stream = nullptr, cap_stream = nullptr;
+    int device = 0, num_sms = 1;
+    // current plan and graph
+    uint64_t key = 0;
+    bool ready = false;
+    void *dev = nullptr;              // plan + items + statistics tables
+    double *part = nullptr, *sums = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kmax_last = 0;
+    std::vector<double> host_sums;
+};
+
+static void batch_release_plan(qs_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    if (b->dev) cudaFree(b->dev);
+    if (b->part) cudaFree(b->part);
+    if (b->sums) cudaFree(b->sums);
+    b->dev = nullptr;
+    b->part = b->sums = nullptr;
+    b->ready = false;
+}
+
+extern "C" qs_status qs_batch_create(int count, const int *nqubits, void *cuda_stream, qs_batch **out)
+{
+    clear_error();
+    if (count < 1 || !nqubits || !out) return set_error(QS_ERR_INVALID_ARG, "bad batch arguments");
+    qs_batch *b = new qs_batch();
+    b->count = count;
+    b->user_stream = (cudaStream_t)cuda_stream;
+    for (int i = 0; i < count; ++i) {
+        if (nqubits[i] < 5 || nqubits[i] > 30) {
+            delete b;
+            return set_error(QS_ERR_INVALID_ARG, "instance %d: n = %d outside 5..30", i, nqubits[i]);
+        }
+        b->n.push_back(nqubits[i]);
+        b->off.push_back(b->total);
+        b->total += 1ULL << nqubits[i];
+    }
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    cudaError_t e = cudaMalloc((void **)&b->amps, b->total * sizeof(float2));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return set_error(QS_ERR_OOM, "batch states (%llu amplitudes): %s", (unsigned long long)b->total,
+                         cudaGetErrorString(e));
+    }
+    e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(b->amps);
+        delete b;
+        return set_error(QS_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_destroy(qs_batch *b)
+{
+    clear_error();
+    if (!b) return QS_OK;
+    cudaStreamSynchronize(b->user_stream);
+    batch_release_plan(b);
+    if (b->amps) cudaFree(b->amps);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps)
+{
+    clear_error();
+    if (!b || !device_amps || i < 0 || i >= b->count) return set_error(QS_ERR_INVALID_ARG, "bad instance");
+    *device_amps = b->amps + b->off[i];
+    return QS_OK;
+}
+
+// Plans every instance, lays out the concatenated plan, work items and
+// statistics items in one device buffer, and records the run as a graph.
+static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)
+{
+    const int C = b->count;
+    std::vector<Plan> plans(C);
+    std::vector<qs_status> st(C, QS_OK);
+    std::vector<std::string> msg(C);
+    const unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < nth; ++w)
+        pool.emplace_back([&, w]() {
+            for (int i = (int)w; i < C; i += (int)nth) {
+                PlanParams pp = default_plan_params(b->n[i], QS_C64, nullptr);
+                st[i] = build_plan(pp, gates + offsets[i], (size_t)(offsets[i + 1] - offsets[i]), &plans[i]);
+                if (st[i]) msg[i] = last_error_cstr();
+            }
+        });
+    for (auto &t : pool) t.join();
+    for (int i = 0; i < C; ++i)
+        if (st[i]) return set_error(st[i], "instance %d: %s", i, msg[i].c_str());
+
+    // concatenate plans (rebase phase and op indices)
+    std::vector<DevPass> passes;
+    std::vector<DevPhase> phases;
+    std::vector<DevOp> ops;
+    std::vector<int> first_pass(C);
+    int max_passes = 0;
+    for (int i = 0; i < C; ++i) {
+        first_pass[i] = (int)passes.size();
+        const int pb = (int)phases.size(), ob = (int)ops.size();
+        for (DevPass p : plans[i].passes) {
+            p.phase_begin += pb;
+            passes.push_back(p);
+        }
+        for (DevPhase h : plans[i].phases) {
+            h.op_begin += ob;
+            h.op_end += ob;
+            phases.push_back(h);
+        }
+        ops.insert(ops.end(), plans[i].ops.begin(), plans[i].ops.end());
+        max_passes = std::max(max_passes, (int)plans[i].passes.size());
+    }
+    // work items per (round, tile bits)
+    struct Launch { int round, tbits; size_t first, count; };
+    std::vector<Launch> launches;
+    std::vector<unsigned char> items;
+    const size_t isz = batch_item_bytes();
+    for (int r = 0; r < max_passes; ++r)
+        for (int tb = 5; tb <= 13; ++tb) {
+            Launch L{r, tb, items.size() / isz, 0};
+            for (int i = 0; i < C; ++i) {
+                if (r >= (int)plans[i].passes.size()) continue;
+                const DevPass &p = plans[i].passes[r];
+                if (p.t != tb) continue;
+                const uint64_t ntiles = 1ULL << (b->n[i] - p.t);
+                for (uint64_t t0 = 0; t0 < ntiles; t0 += kItemTiles) {
+                    const uint64_t t1 = std::min<uint64_t>(ntiles, t0 + kItemTiles);
+                    items.resize(items.size() + isz);
+                    batch_item_fill(items.data() + items.size() - isz, b->off[i], (uint32_t)(first_pass[i] + r),
+                                    (uint32_t)t0, (uint32_t)t1);
+                    ++L.count;
+                }
+            }
+            if (L.count) launches.push_back(L);
+        }
+    // statistics items
+    std::vector<uint64_t> s_off, s_cnt;
+    std::vector<float> s_scale;
+    std::vector<int> first_item(C + 1);
+    for (int i = 0; i < C; ++i) {
+        first_item[i] = (int)s_off.size();
+        const uint64_t N = 1ULL << b->n[i];
+        for (uint64_t a = 0; a < N; a += kStatChunk) {
+            s_off.push_back(b->off[i] + a);
+            s_cnt.push_back(std::min<uint64_t>(kStatChunk, N - a));
+            s_scale.push_back((float)std::ldexp(1.0, b->n[i]));
+        }
+    }
+    first_item[C] = (int)s_off.size();
+    const int nsi = (int)s_off.size();
+
+    // one device buffer: passes | phases | ops | items | s_off | s_cnt | s_scale | first_item | inst_off
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o_pass = 0, o_ph = align(o_pass + passes.size() * sizeof(DevPass));
+    size_t o_op = align(o_ph + phases.size() * sizeof(DevPhase));
+    size_t o_it = align(o_op + ops.size() * sizeof(DevOp));
+    size_t o_so = align(o_it + items.size());
+    size_t o_sc = align(o_so + s_off.size() * 8);
+    size_t o_ss = align(o_sc + s_cnt.size() * 8);
+    size_t o_fi = align(o_ss + s_scale.size() * 4);
+    size_t o_io = align(o_fi + first_item.size() * 4);
+    size_t total = align(o_io + b->off.size() * 8);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_pass, passes.data(), passes.size() * sizeof(DevPass));
+    std::memcpy(host.data() + o_ph, phases.data(), phases.size() * sizeof(DevPhase));
+    std::memcpy(host.data() + o_op, ops.data(), ops.size() * sizeof(DevOp));
+    if (!items.empty()) std::memcpy(host.data() + o_it, items.data(), items.size());
+    std::memcpy(host.data() + o_so, s_off.data(), s_off.size() * 8);
+    std::memcpy(host.data() + o_sc, s_cnt.data(), s_cnt.size() * 8);
+    std::memcpy(host.data() + o_ss, s_scale.data(), s_scale.size() * 4);
+    std::memcpy(host.data() + o_fi, first_item.data(), first_item.size() * 4);
+    std::memcpy(host.data() + o_io, b->off.data(), b->off.size() * 8);
+    batch_release_plan(b);
+    QS_CUDA_TRY(cudaMalloc(&b->dev, total));
+    QS_CUDA_TRY(cudaMalloc((void **)&b->part, (size_t)nsi * kStatSums * sizeof(double)));
+    QS_CUDA_TRY(cudaMalloc((void **)&b->sums, (size_t)C * kStatSums * sizeof(double)));
+    QS_CUDA_TRY(cudaMemcpy(b->dev, host.data(), total, cudaMemcpyHostToDevice));
+    unsigned char *D = (unsigned char *)b->dev;
+
+    // record: reset all states, rounds, statistics
+    if (qs_status s0 = batch_kernel_setup()) return s0;
+    QS_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    qs_status rs = QS_OK;
+    cudaMemsetAsync(b->amps, 0, b->total * sizeof(float2), b->cap_stream);
+    k_batch_basis<<<(C + 127) / 128, 128, 0, b->cap_stream>>>(b->amps, (const uint64_t *)(D + o_io), C);
+    for (const Launch &L : launches) {
+        rs = launch_batch_round(b->cap_stream, b->num_sms, b->amps, D + o_it + L.first * isz, (int)L.count, L.tbits,
+                                (const DevPass *)(D + o_pass), (const DevPhase *)(D + o_ph),
+                                (const DevOp *)(D + o_op));
+        if (rs) break;
+    }
+    if (!rs)
+        rs = launch_batch_stats(b->cap_stream, b->num_sms, b->amps, (const uint64_t *)(D + o_so),
+                                (const uint64_t *)(D + o_sc), (const float *)(D + o_ss), nsi,
+                                (const int *)(D + o_fi), C, b->part, b->sums);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rs) {
+        if (graph) cudaGraphDestroy(graph);
+        return rs;
+    }
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    b->ready = true;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
+                                  double *stats)
+{
+    clear_error();
+    if (!b || !offsets || (kmax && !stats) || kmax < 0 || kmax > kMaxMoments)
+        return set_error(QS_ERR_INVALID_ARG, "bad batch run arguments");
+    if (offsets[0] != 0) return set_error(QS_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int i = 0; i < b->count; ++i) {
+        if (offsets[i + 1] < offsets[i]) return set_error(QS_ERR_INVALID_ARG, "offsets decrease at %d", i);
+        if (qs_status s2 = validate_gates(b->n[i], gates + offsets[i], (size_t)(offsets[i + 1] - offsets[i])))
+            return set_error(s2, "instance %d: %s", i, last_error_cstr());
+    }
+    uint64_t key = fnv1a(offsets, (b->count + 1) * sizeof(uint64_t));
+    key = fnv1a(gates, (size_t)offsets[b->count] * sizeof(qs_gate), key);
+    if (!b->ready || key != b->key) {
+        if (qs_status s2 = batch_prepare(b, gates, offsets)) return s2;
+        b->key = key;
+    }
+    QS_CUDA_TRY(cudaGraphLaunch(b->exec, b->user_stream));
+    b->host_sums.resize((size_t)b->count * kStatSums);
+    QS_CUDA_TRY(cudaMemcpyAsync(b->host_sums.data(), b->sums, b->host_sums.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, b->user_stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(b->user_stream));
+    const int w = 3 + kmax;
+    if (stats)
+        for (int i = 0; i < b->count; ++i) {
+            double *o = stats + (size_t)i * w;
+            stats_from_sums(&b->host_sums[(size_t)i * kStatSums], b->n[i], kmax, &o[0], &o[1], &o[2], o + 3);
+        }
+    return QS_OK;
+}

@@ -25,6 +25,8 @@
 //     phase accesses over the banks.
 #include <cuda_fp16.h>
 
+#include <cstring>
+
 #include "qs_device.cuh"
 
 namespace qs {
@@ -569,20 +571,23 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
 // One launch = one pass over the state.  blockDim.x = 2^(t - RB).
 // TC = true: tensor-core variant (complex64, t = 13), one CTA per SM; its
 // dynamic shared memory holds the tile and the two FP16 operand buffers.
+// Runs tiles [t_begin, t_end) of one pass on `amps`: stages the pass's
+// phases and ops into shared memory, then loads, transforms and stores each
+// tile.  Shared by the single-state kernel and the batched kernel.
 template <typename R, int RB, bool TC>
-__global__ void __launch_bounds__(kThreadsMax, TC ? 1 : 2)
-k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
-             const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
-             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
+__device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__ amps,
+                                                const DevPass *__restrict__ pass_g,
+                                                const DevPhase *__restrict__ phases_g,
+                                                const DevOp *__restrict__ ops_g, uint64_t t_begin,
+                                                uint64_t t_end, const uint32_t *__restrict__ tc_words,
+                                                int *__restrict__ err_flag, FusedSmem<R, RB> &S, TcSmem &TS,
+                                                unsigned char *smem_raw)
 {
     using V = typename V2T<R>::T;
     constexpr int NS = 1 << RB;                 // register slots per thread
     constexpr int CE = 16 / (int)sizeof(V);     // elements per 16-byte unit
     constexpr int CPT = NS / CE;                // 16-byte units per thread
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     V *tile = reinterpret_cast<V *>(smem_raw);
-    __shared__ FusedSmem<R, RB> S;
-    __shared__ TcSmem TS;
 
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
@@ -683,11 +688,8 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     const bool gscale_one = (S.P.gscale_re == 1.0 && S.P.gscale_im == 0.0);
     __syncthreads();
 
-    // contiguous range of tiles per CTA; the tile base (bits of the
-    // out-of-tile qubits) advances by a masked increment
-    const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
-    const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
-    const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
+    // the tile base (bits of the out-of-tile qubits) advances by a masked
+    // increment over the contiguous tile range
     uint64_t gmask = 0;
     for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
     uint64_t base = deposit(t_begin, S.P.G, ng);
@@ -792,6 +794,50 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
         __syncthreads();
     }
     if (TC && ntc) tc_teardown(TS);
+    __syncthreads();
+}
+
+template <typename R, int RB, bool TC>
+__global__ void __launch_bounds__(kThreadsMax, TC ? 1 : 2)
+k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
+             const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
+             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FusedSmem<R, RB> S;
+    __shared__ TcSmem TS;
+    // contiguous range of tiles per CTA
+    const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
+    const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
+    const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
+    fused_pass_body<R, RB, TC>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
+                               smem_raw);
+}
+
+// Batched form: work item = (instance amplitudes, pass, tile range); the
+// CTA restages the pass for every item.  All items of a launch share one
+// tile size (blockDim.x = 2^(t - RB)).
+struct BatchItem {
+    uint64_t amp_off;       // element offset of the instance's state
+    uint32_t pass;          // index into the batch's pass array
+    uint32_t tile_begin, tile_end;
+    uint32_t pad;
+};
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(kThreadsMax, 2)
+k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict__ items, int nitems,
+             const DevPass *__restrict__ passes, const DevPhase *__restrict__ phases_g,
+             const DevOp *__restrict__ ops_g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FusedSmem<R, RB> S;
+    __shared__ TcSmem TS;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        fused_pass_body<R, RB, false>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
+                                      w.tile_end, nullptr, nullptr, S, TS, smem_raw);
+    }
 }
 
 template <typename R, int RB>
@@ -846,6 +892,34 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
         if (h) return set_error(QS_ERR_TIMEOUT, "tensor-core pass: completion wait ran out");
     }
     return QS_OK;
+}
+
+qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const void *items, int nitems,
+                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops)
+{
+    if (tile_bits < 5 || tile_bits > 13) return set_error(QS_ERR_INVALID_ARG, "batch tile bits %d", tile_bits);
+    auto kern = k_batch_pass<float, 5>;
+    const size_t smem = (size_t(1) << tile_bits) * sizeof(float2);
+    const int cap = num_sms * 2;
+    const int grid = nitems < cap ? nitems : cap;
+    kern<<<grid, 1 << (tile_bits - 5), smem, st>>>((float2 *)amps, (const BatchItem *)items, nitems, passes,
+                                                   phases, ops);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
+
+qs_status batch_kernel_setup()
+{
+    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    return QS_OK;
+}
+
+size_t batch_item_bytes() { return sizeof(BatchItem); }
+
+void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, uint32_t te)
+{
+    BatchItem w{amp_off, pass, tb, te, 0};
+    std::memcpy(dst, &w, sizeof w);
 }
 
 qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan)

@@ -186,4 +186,17 @@ qs_status adjoint_run(qs_state *s, const qs_gate *g, size_t ng, const uint64_t *
 
 size_t dtype_bytes(qs_dtype dt);
 
+// batched ensemble helpers
+constexpr int kStatSums = 12;
+qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const void *items, int nitems,
+                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops);
+size_t batch_item_bytes();
+qs_status batch_kernel_setup();
+void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, uint32_t te);
+qs_status launch_batch_stats(cudaStream_t st, int num_sms, const void *amps, const uint64_t *item_off,
+                             const uint64_t *item_cnt, const float *item_scale, int nitems,
+                             const int *first_item, int count, double *part, double *out);
+void stats_from_sums(const double *h, int n, int kmax, double *norm, double *entropy, double *uniform_ce,
+                     double *moments);
+
 }  // namespace qs

@@ -222,6 +222,92 @@ qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *en
 }
 
 // ---------------------------------------------------------------------------
+// batched statistics: item = (element offset, count) of one instance's state;
+// per-item partials are summed per instance in item order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kStatThreads)
+k_batch_stats(const float2 *__restrict__ amps, const uint64_t *__restrict__ item_off,
+              const uint64_t *__restrict__ item_cnt, const float *__restrict__ item_scale, int nitems,
+              double *__restrict__ part)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const float2 *a = amps + item_off[it];
+        const uint64_t cnt = item_cnt[it];
+        const float scaleN = item_scale[it];
+        double acc[kStatAcc];
+#pragma unroll
+        for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
+        for (uint64_t i0 = threadIdx.x; i0 < cnt; i0 += (uint64_t)blockDim.x * 64) {
+            float c[kStatAcc];
+#pragma unroll
+            for (int k = 0; k < kStatAcc; ++k) c[k] = 0.f;
+            double big[kStatAcc];
+            bool any_big = false;
+            for (uint64_t i = i0, j = 0; j < 64 && i < cnt; ++j, i += blockDim.x) {
+                const float2 v = a[i];
+                const float y = (v.x * v.x + v.y * v.y) * scaleN;
+                if (y > 4096.f) {
+                    if (!any_big) {
+#pragma unroll
+                        for (int k = 0; k < kStatAcc; ++k) big[k] = 0;
+                        any_big = true;
+                    }
+                    stat_terms<double>(((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN, big);
+                } else {
+                    stat_terms<float>(y, c);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)c[k];
+            if (any_big) {
+#pragma unroll
+                for (int k = 0; k < kStatAcc; ++k) acc[k] += big[k];
+            }
+        }
+        block_sum_store<kStatAcc>(acc, part + (size_t)it * kStatAcc);
+        __syncthreads();
+    }
+}
+
+__global__ void k_batch_stats_sum(const double *__restrict__ part, const int *__restrict__ first_item,
+                                  int count, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    for (int k = 0; k < kStatAcc; ++k) {
+        double s = 0;
+        for (int it = first_item[i]; it < first_item[i + 1]; ++it) s += part[(size_t)it * kStatAcc + k];
+        out[(size_t)i * kStatAcc + k] = s;
+    }
+}
+
+qs_status launch_batch_stats(cudaStream_t st, int num_sms, const void *amps, const uint64_t *item_off,
+                             const uint64_t *item_cnt, const float *item_scale, int nitems,
+                             const int *first_item, int count, double *part, double *out)
+{
+    const int grid = nitems < num_sms * 8 ? nitems : num_sms * 8;
+    k_batch_stats<<<grid, kStatThreads, 0, st>>>((const float2 *)amps, item_off, item_cnt, item_scale, nitems,
+                                                 part);
+    QS_LAUNCH_CHECK();
+    k_batch_stats_sum<<<(count + 127) / 128, 128, 0, st>>>(part, first_item, count, out);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
+
+void stats_from_sums(const double *h, int n, int kmax, double *norm, double *entropy, double *uniform_ce,
+                     double *moments)
+{
+    const double Nd = std::ldexp(1.0, n), lnN = n * std::log(2.0);
+    const double S = h[0] / Nd;
+    const double lnS = S > 0 ? std::log(S) : -INFINITY;
+    if (norm) *norm = S;
+    if (entropy) *entropy = S > 0 ? lnS + lnN - h[1] / h[0] : 0.0;
+    if (uniform_ce) *uniform_ce = S > 0 ? lnS + lnN - h[2] / Nd : INFINITY;
+    for (int k = 1; k <= kmax; ++k)
+        moments[k - 1] = S > 0 ? (k == 1 ? 1.0 : h[k + 1] / (Nd * std::pow(S, k))) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
 // sampler
 // ---------------------------------------------------------------------------
 // Lane l of a warp covers elements [8l, 8l+8) of a 256-amplitude chunk.  The

@@ -30,3 +30,25 @@ def normals(seed, count):
         out.append(r * math.cos(2 * math.pi * u2))
         out.append(r * math.sin(2 * math.pi * u2))
     return out[:count]
+
+
+def mix64(z):
+    """SplitMix64's output finaliser applied to z."""
+    z &= MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK
+    return z ^ (z >> 31)
+
+
+def ensemble_instance(s):
+    """Instance s of the batched ensemble: n uniform in 12..24, depth uniform
+    in 10..40, grid with 3 rows (n <= 15) or 4 rows, ceil(n / rows) columns,
+    the last rows*cols - n sites of the last row dead."""
+    n = 12 + mix64(s) % 13
+    depth = 10 + mix64(s ^ 0xD1B54A32D192ED03) % 31
+    rows = 3 if n <= 15 else 4
+    cols = -(-n // rows)
+    dead = [0] * (rows * cols)
+    for k in range(rows * cols - n):
+        dead[rows * cols - 1 - k] = 1
+    return n, depth, rows, cols, dead

@@ -1,0 +1,93 @@
+"""Batched ensemble (qs_batch_*): every instance against the FP64 oracle on
+a small ensemble, and the full 4096-instance ensemble (n 12..24, depth
+10..40) against properties and Porter-Thomas closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1608_00263_gb300 as qs
+from paper_1608_00263_gb300 import build as qs_build
+
+from seeded_inputs import ensemble_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    qs_build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def instance(s):
+    n, depth, rows, cols, dead = ensemble_instance(s)
+    g = qs.qs_circuit_generate(rows, cols, depth, s, np.array(dead, dtype=np.uint8))
+    return n, depth, g
+
+
+def device_state(b, i, n):
+    import torch
+    ptr = qs.qs_batch_state(b, i)
+
+    class _A:
+        __cuda_array_interface__ = {"shape": (2 << n,), "typestr": "<f4", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_A(), device="cuda").cpu().numpy().view(np.complex64)
+
+
+def test_small_ensemble_matches_oracle():
+    seeds = [s for s in range(200) if ensemble_instance(s)[0] <= 17][:24]
+    inst = [instance(s) for s in seeds]
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        st = qs.qs_batch_run(b, [x[2] for x in inst], kmax=4)
+        st2 = qs.qs_batch_run(b, [x[2] for x in inst], kmax=4)      # graph replay
+        assert np.array_equal(st, st2)
+        for i, (n, depth, g) in enumerate(inst):
+            ref = O.simulate(n, g)
+            psi = device_state(b, i, n)
+            err = np.linalg.norm(psi.astype(complex) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (i, n, depth, err)
+            p = O.probabilities(ref)
+            assert abs(st[i, 0] - 1) < 2e-5
+            assert st[i, 1] == pytest.approx(O.entropy(p), rel=1e-6)
+            assert st[i, 2] == pytest.approx(O.uniform_ce(p), rel=1e-6)
+            assert np.allclose(st[i, 3:], O.moments(p, 4), rtol=1e-5)
+    finally:
+        qs.qs_batch_destroy(b)
+
+
+def test_ensemble_4096():
+    import torch
+    torch.cuda.empty_cache()
+    inst = [instance(s) for s in range(4096)]
+    ns = np.array([x[0] for x in inst])
+    depths = np.array([x[1] for x in inst])
+    b = qs.qs_batch_create(ns)
+    try:
+        st = qs.qs_batch_run(b, [x[2] for x in inst], kmax=10)
+        # every state normalised to the FP32 evolution's accuracy
+        assert np.max(np.abs(st[:, 0] - 1)) < 2e-5
+        # deep instances: entropy and moments at their Porter-Thomas values
+        # (Sec. "Convergence to Porter-Thomas": convergence within ~10 cycles
+        # for the paper's grids; spread 0.75 2^{-n/2} between states)
+        deep = depths >= 30
+        assert deep.sum() > 1000
+        pt = ns * math.log(2) - 1 + O.EULER_GAMMA
+        z = (st[:, 1] - pt) / (0.75 * 2.0 ** (-ns / 2))
+        assert np.mean(np.abs(z[deep]) < 4) > 0.95, np.percentile(np.abs(z[deep]), [50, 90, 99])
+        ipr2 = st[:, 4]
+        assert abs(np.mean(ipr2[deep]) - 2) < 0.02
+        ce_pt = ns * math.log(2) + O.EULER_GAMMA
+        assert abs(np.mean(st[deep, 2] - ce_pt[deep])) < 0.01
+        # a random subset of the small instances against the oracle
+        rng = np.random.default_rng(1)
+        small = np.nonzero(ns <= 16)[0]
+        for i in rng.choice(small, size=8, replace=False):
+            n, depth, g = inst[i]
+            p = O.probabilities(O.simulate(n, g))
+            assert st[i, 1] == pytest.approx(O.entropy(p), rel=1e-6)
+    finally:
+        qs.qs_batch_destroy(b)
