@@ -60,6 +60,26 @@ def dist_env():
     return rank, world, local
 
 
+def replica_seed(rank):
+    """Circuit-seed base of a replica: ranks run disjoint circuit streams."""
+    return 1_000_003 * rank
+
+
+def job_max_ms(local_ms, dist, device):
+    """Max of a timing over all ranks (the job's wall time)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, max_ms):
+    """Whole-job throughput: units processed by all ranks / max time."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -161,7 +181,7 @@ def run_ours(args, rank, world, local):
     probs = torch.empty(1 << n, dtype=torch.float64 if W["fp64_probs"] else torch.float32,
                         device="cuda")
     samples = torch.empty(m, dtype=torch.int64, device="cuda")
-    base_seed = 1_000_003 * rank
+    base_seed = replica_seed(rank)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     apply_ms = []
@@ -203,13 +223,9 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     apply_total = sum(a.elapsed_time(b) for a, b in apply_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_max_ms(total_ms, dist, "cuda")
     passes_seen = [qs.qs_plan_circuit(n, qs.QS_C64, g, mode=mode)["passes"] for g in timed_gates]
-    cycles = depth * args.steps * world
-    value = cycles / (total_ms / 1000.0)
+    value = job_value(depth * args.steps, world, total_ms)
     passes_total = sum(passes_seen)
     pass_bytes = 16.0 * (1 << n)                 # read + write of 2^n complex64
     avg_pass_ms = apply_total / passes_total
@@ -238,11 +254,8 @@ def run_ours(args, rank, world, local):
         e2e_ms += (time.perf_counter() - t0) * 1000.0
         h2d += gates.nbytes + samples_host.nbytes
         d2h += probs_host.numel() * probs_host.element_size() + samples_host.nbytes + 8 * 14
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = depth * args.steps * world / (e2e_ms / 1000.0)
+    e2e_ms = job_max_ms(e2e_ms, dist, "cuda")
+    e2e_value = job_value(depth * args.steps, world, e2e_ms)
 
     # ---- one-off comparison of the forms (apply only, untimed region) ----
     compare = {}
