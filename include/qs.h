@@ -237,6 +237,19 @@ qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
                               const uint64_t *samples, uint64_t m, const qs_opts *opts,
                               double *loss, double *grad);
 
+/* Statistics after every cycle (Sec. "Convergence to Porter-Thomas":
+ * statistics of measurements after each cycle; Figs. evd and mvd follow
+ * entropy and inverse participation ratios with depth).  Resets the state
+ * to |0...0>, then for each run of gates with equal `cycle` field (cycle
+ * numbers must not decrease) applies that cycle (form chosen by `opts`) and
+ * records the statistics of qs_pt_moments: stats[c*(4+kmax) ..] = cycle,
+ * norm, entropy, uniform cross entropy, moments 1..kmax.  *ncycles receives
+ * the number of cycles; if stats is NULL or capacity (rows) is smaller,
+ * nothing is run (count query).  The planner fuses gates only within a cycle
+ * here, since the state must exist after each one.  Synchronous. */
+qs_status qs_cycle_statistics(qs_state *s, const qs_gate *gates, size_t ngates, const qs_opts *opts,
+                              int kmax, double *stats, size_t capacity, size_t *ncycles);
+
 /* Porter-Thomas statistics of p_U in one read of the state, FP64
  * accumulation (Sec. "Convergence to Porter-Thomas").  They are computed
  * for the normalised distribution p / S, S = sum p, so that the rounding

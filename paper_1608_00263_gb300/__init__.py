@@ -25,7 +25,7 @@ __all__ = [
     "qs_plan_circuit",
     "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
-    "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy",
+    "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "library_path",
 ]
 
@@ -241,3 +241,17 @@ def qs_batch_state(b, i):
 
 def qs_batch_destroy(b):
     N.check(N.lib().qs_batch_destroy(b))
+
+
+def qs_cycle_statistics(h, gates, kmax=10, mode=QS_MODE_FUSED):
+    """Statistics after every cycle: array (cycles, 4 + kmax) of cycle, norm,
+    entropy, uniform cross entropy, moments 1..kmax."""
+    g = _gates(gates)
+    o = _opts(mode, QS_PREC_DEFAULT, 0, 0)
+    cnt = ctypes.c_size_t(0)
+    gp = g.ctypes.data if g.size else None
+    N.check(N.lib().qs_cycle_statistics(h, gp, g.size, ctypes.byref(o), kmax, None, 0, ctypes.byref(cnt)))
+    out = np.zeros((cnt.value, 4 + kmax), dtype=np.float64)
+    N.check(N.lib().qs_cycle_statistics(h, gp, g.size, ctypes.byref(o), kmax, out.ctypes.data, cnt.value,
+                                        ctypes.byref(cnt)))
+    return out

@@ -66,6 +66,8 @@ SIGNATURES = {
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),
     "qs_pt_moments": (ctypes.c_int, [P, ctypes.c_int, PD, PD, PD, PD]),
     "qs_adjoint_gradient": (ctypes.c_int, [P, P, ctypes.c_size_t, P, U64, ctypes.POINTER(qs_opts), PD, P]),
+    "qs_cycle_statistics": (ctypes.c_int, [P, P, ctypes.c_size_t, ctypes.POINTER(qs_opts), ctypes.c_int, P,
+                                           ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "qs_batch_create": (ctypes.c_int, [ctypes.c_int, P, P, ctypes.POINTER(P)]),
     "qs_batch_run": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "qs_batch_state": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P)]),

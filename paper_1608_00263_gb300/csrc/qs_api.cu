@@ -402,3 +402,34 @@ extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size
     if (!st && loss) *loss = ce;
     return st;
 }
+
+extern "C" qs_status qs_cycle_statistics(qs_state *s, const qs_gate *gates, size_t ngates, const qs_opts *opts,
+                                         int kmax, double *stats, size_t capacity, size_t *ncycles)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
+    if (!ncycles || kmax < 0 || kmax > kMaxMoments) return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    for (size_t i = 1; i < ngates; ++i)
+        if (gates[i].cycle < gates[i - 1].cycle)
+            return set_error(QS_ERR_INVALID_ARG, "gate %zu: cycle numbers decrease", i);
+    // cycle groups
+    std::vector<size_t> starts;
+    for (size_t i = 0; i < ngates; ++i)
+        if (i == 0 || gates[i].cycle != gates[i - 1].cycle) starts.push_back(i);
+    *ncycles = starts.size();
+    if (!stats || capacity < starts.size()) return QS_OK;   // count query
+    DeviceGuard g(s->device);
+    if (qs_status st = launch_init_zero(s)) return st;
+    const int w = 4 + kmax;
+    std::vector<double> mom(kMaxMoments);
+    for (size_t c = 0; c < starts.size(); ++c) {
+        const size_t b = starts[c], e = c + 1 < starts.size() ? starts[c + 1] : ngates;
+        if (qs_status st = qs_apply_circuit(s, gates + b, e - b, opts)) return st;
+        double *row = stats + c * w;
+        row[0] = (double)gates[b].cycle;
+        if (qs_status st = stats_moments(s, kmax, mom.data(), &row[2], &row[3], &row[1])) return st;
+        for (int k = 0; k < kmax; ++k) row[4 + k] = mom[k];
+    }
+    return QS_OK;
+}

@@ -437,3 +437,29 @@ def test_full_size_34_qubits():
         assert p0 > 1 - 1e-4, p0
     finally:
         qs.qs_state_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# statistics after every cycle
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [qs.QS_MODE_FUSED, qs.QS_MODE_PLAIN])
+def test_cycle_statistics_vs_oracle(mode):
+    n = 16
+    g = qs.qs_circuit_generate(4, 4, 30, 4)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        st = qs.qs_cycle_statistics(h, g, kmax=3, mode=mode)
+    finally:
+        qs.qs_state_destroy(h)
+    assert st.shape == (31, 7)
+    psi = O.zero_state(n)
+    for c in range(31):
+        O.apply_circuit(psi, g[g["cycle"] == c])
+        p = O.probabilities(psi)
+        assert st[c, 0] == c
+        assert st[c, 2] == pytest.approx(O.entropy(p), rel=1e-6, abs=1e-6)
+        assert np.allclose(st[c, 4:], O.moments(p, 3), rtol=1e-5)
+    # Sec. pt: the H layer gives the uniform distribution, the first cycles
+    # are diagonal, later the entropy approaches ln N - 1 + gamma
+    assert st[0, 2] == pytest.approx(n * math.log(2), abs=1e-6)
+    assert abs(st[-1, 2] - (n * math.log(2) - 1 + O.EULER_GAMMA)) < 0.01
