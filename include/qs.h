@@ -250,6 +250,29 @@ qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
 qs_status qs_cycle_statistics(qs_state *s, const qs_gate *gates, size_t ngates, const qs_opts *opts,
                               int kmax, double *stats, size_t capacity, size_t *ncycles);
 
+/* Denser random circuits with periodic boundaries (appendix "Depth to
+ * reach Porter-Thomas for denser 2D circuits"), on a rows x cols torus (both
+ * even, rows * cols <= 64; qubit r*cols+c):
+ *   cycle 0: H on every qubit;
+ *   layer l = 1..layers: cycle 2l-1 single-qubit gates, cycle 2l CZ gates.
+ * The CZ cycle of layer l puts every qubit in exactly one CZ, pattern
+ * (l-1) mod 4 of H_even, V_even, H_odd, V_odd (horizontal / vertical
+ * nearest-neighbour pairs starting at an even / odd column / row, wrapping
+ * around the torus).  Single-qubit gates follow the rules of
+ * qs_circuit_generate (only after a CZ in the previous cycle, T first after
+ * H, then a SplitMix64 pick from {X^1/2, Y^1/2, T} without the previous
+ * gate), so layer 1 has CZs only.  Output, count query and errors as
+ * qs_circuit_generate. */
+qs_status qs_circuit_generate_dense(int rows, int cols, int layers, uint64_t seed,
+                                    qs_gate *out, size_t *ngates);
+
+/* Convergence to Porter-Thomas (Sec. "Convergence to Porter-Thomas", Fig.
+ * pt_depth): *first = the smallest i such that entropy[j] is within 4 sigma
+ * of ln N - 1 + gamma for every j >= i, sigma = 0.75 * 2^(-n/2) (the
+ * spread of the entropy of Porter-Thomas states), N = 2^n; count if the last
+ * entry is outside.  Host only, entropy[count] read during the call. */
+qs_status qs_pt_convergence(const double *entropy, size_t count, int n, size_t *first);
+
 /* Porter-Thomas statistics of p_U in one read of the state, FP64
  * accumulation (Sec. "Convergence to Porter-Thomas").  They are computed
  * for the normalised distribution p / S, S = sum p, so that the rounding
@@ -289,6 +312,35 @@ qs_status qs_batch_create(int count, const int *nqubits, void *cuda_stream, qs_b
  * Synchronous. */
 qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
                        double *stats);
+
+/* Samples every instance of the batch (its current states): out[i*k + j],
+ * j < k, is sample j of instance i, drawn by the inverse-CDF rule of
+ * qs_sample from u = the counter-based draw number i*k + j of the stream
+ * seeded with `seed` (see qs_sample), then each bit b < n_i flipped when the
+ * draw number (i*k + j)*64 + b of the stream seeded with
+ * seed ^ 0xD1B54A32D192ED03 is below r_mes (the measurement bit-flip errors
+ * of the digital error model, Sec. "Characterizing quantum supremacy";
+ * r_mes = 0: plain samples).  An instance with zero norm gives
+ * UINT64_MAX samples.  out is a host array of count*k entries.
+ * Synchronous. */
+qs_status qs_batch_sample(qs_batch *b, uint64_t k, uint64_t seed, double r_mes, uint64_t *out);
+
+/* One trajectory of the digital error model (Sec. "Characterizing quantum
+ * supremacy": a depolarising channel after every gate, Eq. 6): copies the
+ * gate list, inserting after each one-qubit gate, with probability r1, one
+ * of X, Y, Z (each r1/3), and after each two-qubit gate, with probability
+ * r2, one of the 15 non-identity two-qubit Paulis (each r2/15), and before
+ * the circuit an X on each qubit with probability r_init (initialisation
+ * bit flip).  Paulis are emitted as QS_RX / QS_RY / QS_RZ with theta = pi
+ * (the Pauli times the global phase -i), in the cycle of the gate they
+ * follow.  Draws: one SplitMix64 stream seeded with `seed`, u = (z >> 11)
+ * 2^-53; first one per qubit (initialisation, X if u < r_init), then one per
+ * gate in list order (one-qubit: Pauli floor(3u/r1) of X, Y, Z if u < r1;
+ * two-qubit: if u < r2, e = floor(15u/r2) + 1 read as base-4 digits
+ * (e / 4 on q0, e % 4 on q1; 0 = I, 1..3 = X, Y, Z)).  Output and count
+ * query as qs_circuit_generate (*nout in: capacity, out: count).  Host only. */
+qs_status qs_noisy_circuit(const qs_gate *gates, size_t ngates, int n, double r1, double r2,
+                           double r_init, uint64_t seed, qs_gate *out, size_t *nout);
 
 /* Device pointer of instance i's amplitudes (canonical order). */
 qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps);

@@ -14,6 +14,7 @@ generator are a reading of a figure the paper does not include: layout
 parity unpinned (soft-pinned by Table I gates per level).
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -45,6 +46,14 @@ def _load():
         lib.oracle_circuit_generate.argtypes = [
             ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_uint64, P,
             ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+        lib.oracle_circuit_generate_dense.restype = ctypes.c_int
+        lib.oracle_circuit_generate_dense.argtypes = [
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P, ctypes.c_size_t,
+            ctypes.POINTER(ctypes.c_size_t)]
+        lib.oracle_noisy_circuit.restype = ctypes.c_int
+        lib.oracle_noisy_circuit.argtypes = [
+            P, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+            ctypes.c_uint64, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
         lib.oracle_gate_matrix.restype = ctypes.c_int
         lib.oracle_gate_matrix.argtypes = [ctypes.c_int, ctypes.c_double, P]
         lib.oracle_apply_1q.restype = ctypes.c_int
@@ -116,6 +125,92 @@ def generate_circuit(rows, cols, depth, seed, dead=None):
     if rc:
         raise ValueError("oracle_circuit_generate failed: %d" % rc)
     return out
+
+
+def generate_dense_circuit(rows, cols, layers, seed):
+    """Gate list of a dense periodic-boundary circuit (appendix on denser 2D circuits)."""
+    lib = _load()
+    cnt = ctypes.c_size_t(0)
+    if lib.oracle_circuit_generate_dense(rows, cols, layers, seed, None, 0, ctypes.byref(cnt)):
+        raise ValueError("oracle_circuit_generate_dense: bad arguments")
+    out = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    if lib.oracle_circuit_generate_dense(rows, cols, layers, seed, _ptr(out), out.size,
+                                         ctypes.byref(cnt)):
+        raise ValueError("oracle_circuit_generate_dense failed")
+    return out
+
+
+def noisy_circuit(gates, n, r1, r2, r_init, seed):
+    """One trajectory of the depolarising error model (see qs_oracle.c)."""
+    lib = _load()
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    gp = _ptr(g) if g.size else None
+    cnt = ctypes.c_size_t(0)
+    if lib.oracle_noisy_circuit(gp, g.size, n, r1, r2, r_init, seed, None, 0, ctypes.byref(cnt)):
+        raise ValueError("oracle_noisy_circuit: bad arguments")
+    out = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    if lib.oracle_noisy_circuit(gp, g.size, n, r1, r2, r_init, seed, _ptr(out), out.size,
+                                ctypes.byref(cnt)):
+        raise ValueError("oracle_noisy_circuit failed")
+    return out
+
+
+FLIP_SEED_XOR = 0xD1B54A32D192ED03
+
+
+def sample_at(p, seed, counters):
+    """Inverse-CDF samples of p for the given draw counters: x = min{i : C_i >
+    u C_{N-1}}, C the sequential FP64 cumulative sum, u = sample_uniform(seed, j)."""
+    c = np.cumsum(np.asarray(p, dtype=np.float64))
+    u = np.array([sample_uniform(seed, int(j)) for j in counters])
+    x = np.searchsorted(c, u * c[-1], side="right")
+    return np.minimum(x, len(c) - 1).astype(np.uint64)
+
+
+def measurement_flips(x, n, seed, r_mes, counter):
+    """Bit b of sample number `counter` flips when draw counter*64 + b of the
+    stream seeded with seed ^ FLIP_SEED_XOR is below r_mes."""
+    s2 = (seed ^ FLIP_SEED_XOR) & (2**64 - 1)
+    x = int(x)
+    for b in range(n):
+        if sample_uniform(s2, counter * 64 + b) < r_mes:
+            x ^= 1 << b
+    return x
+
+
+def eq6_fidelity(r1, r2, r_init, r_mes, g1, g2, n):
+    """Eq. 6: alpha ~ exp(-r1 g1 - r2 g2 - r_init n - r_mes n)."""
+    return math.exp(-r1 * g1 - r2 * g2 - r_init * n - r_mes * n)
+
+
+def pt_convergence_index(entropies, n):
+    """Sec. "Convergence to Porter-Thomas" (Fig. pt_depth): the first index i
+    such that every entropy from i on is within 4 sigma of ln N - 1 + gamma,
+    sigma = 0.75 * 2^(-n/2); len(entropies) if the last one is outside."""
+    target = n * math.log(2.0) - 1.0 + EULER_GAMMA
+    sigma = 0.75 * 2.0 ** (-n / 2.0)
+    first = len(entropies)
+    for i in range(len(entropies) - 1, -1, -1):
+        if abs(entropies[i] - target) > 4.0 * sigma:
+            break
+        first = i
+    return first
+
+
+def cycle_statistics(n, gates, kmax=10):
+    """Statistics after every cycle (runs of equal `cycle`): rows of
+    (cycle, norm, entropy, uniform CE, moments 1..kmax), each from the
+    plain definitions on the exact state after that cycle."""
+    psi = zero_state(n)
+    rows = []
+    cyc = gates["cycle"]
+    starts = [i for i in range(len(gates)) if i == 0 or cyc[i] != cyc[i - 1]]
+    for ci, b in enumerate(starts):
+        e = starts[ci + 1] if ci + 1 < len(starts) else len(gates)
+        apply_circuit(psi, gates[b:e])
+        p = probabilities(psi)
+        rows.append([float(cyc[b]), norm(p), entropy(p), uniform_ce(p)] + list(moments(p, kmax)))
+    return np.array(rows)
 
 
 def gate_matrix(kind, theta=0.0):

@@ -19,6 +19,13 @@
  *       Porter-Thomas" gate rules, Fig. two_dimers caption); the exact eight
  *       CZ layouts are a reading of a missing figure: layout parity unpinned
  *       (soft-pinned by Table I gates per level).
+ *   oracle_circuit_generate_dense -- rule checks pinned (appendix "Depth to
+ *       reach Porter-Thomas for denser 2D circuits": one CZ per qubit per CZ
+ *       cycle, nearest neighbours on the torus, placement rules); the order
+ *       of the four matchings is a reading: sequence parity unpinned.
+ *   oracle_noisy_circuit     -- pinned by the error statistics of the model
+ *       (rates and uniform Pauli choice) and by Eq. 6 against the measured
+ *       cross entropy difference of noisy samples (Eqs. 5, aap).
  *   gate application         -- pinned (dense Kronecker unitary, Feynman path
  *       sum of Eqs. path1/phX/phT/phCZ, norm, time reversal).
  *   statistics, sampler, CE  -- pinned (closed forms Eqs. eu/eue, Porter-
@@ -179,6 +186,150 @@ done:
     *ngates = count;
     free(qubit_of_site); free(pair); free(in_cz_prev); free(in_cz_now); free(last_1q);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Denser circuits of the appendix "Depth to reach Porter-Thomas for denser  */
+/* 2D circuits": H on all qubits, then `layers` layers of (single-qubit      */
+/* cycle, CZ cycle) on a rows x cols torus where each CZ cycle pairs every   */
+/* qubit with one nearest neighbour.  Reading (the sequence is only said to  */
+/* resemble Fig. two_dimers, with periodic boundaries): the four perfect     */
+/* matchings, taken in the order of the sparse sequence H0 H2 V0 V2 H1 H3    */
+/* V1 V3 with consecutive pairs merged, are                                  */
+/*   0: horizontal bonds leaving an even column                              */
+/*   1: vertical bonds leaving an even row                                   */
+/*   2: horizontal bonds leaving an odd column (last column wraps to 0)      */
+/*   3: vertical bonds leaving an odd row (last row wraps to 0)              */
+/* Single-qubit placement follows Sec. "Convergence to Porter-Thomas": only  */
+/* on qubits that were in a CZ in the previous cycle (so none in layer 1,    */
+/* whose previous cycle is the H cycle), T first, then a pick from           */
+/* {X^1/2, Y^1/2, T} without the previous gate (top bit of the next          */
+/* SplitMix64 output).  Cycle numbers: 1q cycle of layer l = 2l-1, CZ cycle  */
+/* = 2l.  Qubit of site (r, c) = r*cols + c.  Returns 0, -1 (bad arguments:  */
+/* rows, cols even >= 2, at most 64 sites), -2 (cap too small).              */
+/* ------------------------------------------------------------------------ */
+int oracle_circuit_generate_dense(int rows, int cols, int layers, uint64_t seed,
+                                  oracle_gate *out, size_t cap, size_t *ngates)
+{
+    if (!ngates || layers < 0 || rows < 2 || cols < 2 || rows % 2 || cols % 2 ||
+        rows * cols > 64)
+        return -1;
+    const int n = rows * cols;
+    int last_1q[64];
+    for (int q = 0; q < n; ++q) last_1q[q] = -1;
+    uint64_t rng = seed;
+    size_t count = 0;
+#define PUT(K, A, B, CYC)                                                   \
+    do {                                                                    \
+        if (out) {                                                          \
+            if (count >= cap) { *ngates = count; return -2; }               \
+            out[count].kind = (uint8_t)(K); out[count].q0 = (uint8_t)(A);   \
+            out[count].q1 = (uint8_t)(B); out[count].pad = 0;               \
+            out[count].cycle = (uint32_t)(CYC); out[count].theta = 0.0;     \
+        }                                                                   \
+        ++count;                                                            \
+    } while (0)
+    for (int q = 0; q < n; ++q) PUT(O_H, q, 0, 0);
+    for (int layer = 1; layer <= layers; ++layer) {
+        if (layer >= 2) {
+            /* every qubit was in a CZ in the previous (CZ) cycle */
+            for (int q = 0; q < n; ++q) {
+                int g;
+                if (last_1q[q] == -1) {
+                    g = O_T;
+                } else {
+                    int allowed[2], na = 0;
+                    if (last_1q[q] != O_X_HALF) allowed[na++] = O_X_HALF;
+                    if (last_1q[q] != O_Y_HALF) allowed[na++] = O_Y_HALF;
+                    if (last_1q[q] != O_T) allowed[na++] = O_T;
+                    g = allowed[splitmix_next(&rng) >> 63];
+                }
+                PUT(g, q, 0, 2 * layer - 1);
+                last_1q[q] = g;
+            }
+        }
+        const int m = (layer - 1) % 4;
+        for (int r = 0; r < rows; ++r) {
+            for (int c = 0; c < cols; ++c) {
+                int a = r * cols + c, b;
+                if (m == 0 || m == 2) {            /* horizontal */
+                    if (c % 2 != (m == 2)) continue;
+                    b = r * cols + (c + 1) % cols;
+                } else {                           /* vertical */
+                    if (r % 2 != (m == 3)) continue;
+                    b = ((r + 1) % rows) * cols + c;
+                }
+                PUT(O_CZ, a < b ? a : b, a < b ? b : a, 2 * layer);
+            }
+        }
+    }
+#undef PUT
+    *ngates = count;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Digital error model (Sec. "Characterizing quantum supremacy", the         */
+/* simulations with errors): a depolarising channel after every gate --      */
+/* with probability r1 one of the 3 Paulis after a one-qubit gate, with      */
+/* probability r2 one of the 15 non-identity two-qubit Paulis after a        */
+/* two-qubit gate, all equally likely -- and an initialisation bit flip      */
+/* with probability r_init per qubit.  One trajectory: draws are u = (z>>11) */
+/* 2^-53 from one SplitMix64 stream seeded with `seed`, first one per qubit  */
+/* (X before the circuit if u < r_init), then one per gate.  A one-qubit     */
+/* error takes Pauli number floor(3u/r1) of (X, Y, Z); a two-qubit error     */
+/* takes e = floor(15u/r2) + 1 in 1..15 and puts Pauli e/4 on the first      */
+/* qubit and e%4 on the second (0 = none, 1..3 = X, Y, Z).  Paulis are       */
+/* written as R_X(pi), R_Y(pi), R_Z(pi) (= -i times the Pauli; the global     */
+/* phase leaves every probability unchanged).  Returns 0, -1 (bad           */
+/* arguments), -2 (cap too small; *nout = needed count).                     */
+/* ------------------------------------------------------------------------ */
+int oracle_noisy_circuit(const oracle_gate *in, size_t ngates, int n, double r1, double r2,
+                         double r_init, uint64_t seed, oracle_gate *out, size_t cap,
+                         size_t *nout)
+{
+    if (!nout || n < 1 || n > 64 || r1 < 0 || r1 > 1 || r2 < 0 || r2 > 1 || r_init < 0 ||
+        r_init > 1)
+        return -1;
+    uint64_t rng = seed;
+    size_t count = 0;
+    const int pauli_kind[4] = {-1, O_RX, O_RY, O_RZ};
+#define APPEND(K, Q, CYC, TH)                                              \
+    do {                                                                   \
+        if (out && count < cap) {                                          \
+            out[count].kind = (uint8_t)(K); out[count].q0 = (uint8_t)(Q);  \
+            out[count].q1 = 0; out[count].pad = 0;                         \
+            out[count].cycle = (uint32_t)(CYC); out[count].theta = (TH);   \
+        }                                                                  \
+        ++count;                                                           \
+    } while (0)
+    const uint32_t first_cycle = ngates ? in[0].cycle : 0;
+    for (int q = 0; q < n; ++q) {
+        double u = (double)(splitmix_next(&rng) >> 11) / 9007199254740992.0;
+        if (u < r_init) APPEND(O_RX, q, first_cycle, M_PI);
+    }
+    for (size_t i = 0; i < ngates; ++i) {
+        if (out && count < cap) out[count] = in[i];
+        ++count;
+        double u = (double)(splitmix_next(&rng) >> 11) / 9007199254740992.0;
+        int two = in[i].kind == O_CZ || in[i].kind == O_CPHASE;
+        if (two) {
+            if (u < r2) {
+                int e = (int)(15.0 * u / r2);
+                if (e > 14) e = 14;
+                e += 1;
+                if (e / 4) APPEND(pauli_kind[e / 4], in[i].q0, in[i].cycle, M_PI);
+                if (e % 4) APPEND(pauli_kind[e % 4], in[i].q1, in[i].cycle, M_PI);
+            }
+        } else if (u < r1) {
+            int w = (int)(3.0 * u / r1);
+            if (w > 2) w = 2;
+            APPEND(pauli_kind[w + 1], in[i].q0, in[i].cycle, M_PI);
+        }
+    }
+#undef APPEND
+    *nout = count;
+    return (out && count > cap) ? -2 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

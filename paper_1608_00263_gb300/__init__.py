@@ -26,6 +26,7 @@ __all__ = [
     "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
+    "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
     "library_path",
 ]
 
@@ -212,10 +213,57 @@ def qs_circuit_generate(rows, cols, depth, seed, dead=None):
     return out
 
 
+def qs_circuit_generate_dense(rows, cols, layers, seed):
+    """Dense periodic-boundary random circuit (every qubit in one CZ per CZ cycle)."""
+    cnt = ctypes.c_size_t(0)
+    N.check(N.lib().qs_circuit_generate_dense(rows, cols, layers, seed & (2**64 - 1), None,
+                                              ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    N.check(N.lib().qs_circuit_generate_dense(rows, cols, layers, seed & (2**64 - 1),
+                                              out.ctypes.data, ctypes.byref(cnt)))
+    return out
+
+
+def qs_noisy_circuit(gates, n, r1, r2, r_init, seed):
+    """One trajectory of the depolarising error model (Paulis inserted after gates)."""
+    g = _gates(gates)
+    gp = g.ctypes.data if g.size else None
+    cnt = ctypes.c_size_t(0)
+    N.check(N.lib().qs_noisy_circuit(gp, g.size, n, r1, r2, r_init, seed & (2**64 - 1), None,
+                                     ctypes.byref(cnt)))
+    out = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    N.check(N.lib().qs_noisy_circuit(gp, g.size, n, r1, r2, r_init, seed & (2**64 - 1),
+                                     out.ctypes.data, ctypes.byref(cnt)))
+    return out
+
+
+def qs_batch_sample(b, k, seed, r_mes=0.0):
+    """k samples of every instance (array (count, k)), measurement flips at rate r_mes."""
+    count = _batch_sizes.get(b)
+    if count is None:
+        raise QSError(N.QS_ERR_INVALID_ARG, "unknown batch handle")
+    out = np.zeros(count * k, dtype=np.uint64)
+    N.check(N.lib().qs_batch_sample(b, k, seed & (2**64 - 1), float(r_mes),
+                                    out.ctypes.data if out.size else None))
+    return out.reshape(count, k)
+
+
+def qs_pt_convergence(entropy, n):
+    """First index from which the entropy series stays within 4 sigma of Porter-Thomas."""
+    e = np.ascontiguousarray(entropy, dtype=np.float64)
+    first = ctypes.c_size_t(0)
+    N.check(N.lib().qs_pt_convergence(e.ctypes.data if e.size else None, e.size, n, ctypes.byref(first)))
+    return first.value
+
+
+_batch_sizes = {}     # batch handle -> instance count (for output shapes)
+
+
 def qs_batch_create(nqubits, stream=None):
     n = np.ascontiguousarray(nqubits, dtype=np.int32)
     h = ctypes.c_void_p()
     N.check(N.lib().qs_batch_create(int(n.size), n.ctypes.data, _stream(stream), ctypes.byref(h)))
+    _batch_sizes[h.value] = int(n.size)
     return h.value
 
 
@@ -240,6 +288,7 @@ def qs_batch_state(b, i):
 
 
 def qs_batch_destroy(b):
+    _batch_sizes.pop(b, None)
     N.check(N.lib().qs_batch_destroy(b))
 
 

@@ -50,6 +50,12 @@ U64 = ctypes.c_uint64
 PD = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "qs_version": (ctypes.c_char_p, []),
+    "qs_batch_sample": (ctypes.c_int, [P, U64, U64, D, P]),
+    "qs_noisy_circuit": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.c_int, D, D, D, U64, P,
+                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "qs_circuit_generate_dense": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, U64, P,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "qs_pt_convergence": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "qs_last_error": (ctypes.c_char_p, []),
     "qs_state_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]),
     "qs_state_attach": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, ctypes.POINTER(P)]),

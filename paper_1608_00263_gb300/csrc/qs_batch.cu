@@ -128,6 +128,16 @@ extern "C" qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps
     return QS_OK;
 }
 
+extern "C" qs_status qs_batch_sample(qs_batch *b, uint64_t k, uint64_t seed, double r_mes, uint64_t *out)
+{
+    clear_error();
+    if (!b || (k && !out)) return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    if (!(r_mes >= 0 && r_mes <= 1)) return set_error(QS_ERR_INVALID_ARG, "r_mes must lie in [0, 1]");
+    if (k > (1ULL << 40) / (uint64_t)b->count) return set_error(QS_ERR_INVALID_ARG, "too many samples");
+    return batch_sampler_run(b->user_stream, b->num_sms, b->amps, b->off.data(), b->n.data(), b->count, k, seed,
+                             r_mes, out);
+}
+
 // Plans every instance, lays out the concatenated plan, work items and
 // statistics items in one device buffer, and records the run as a graph.
 static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)

@@ -242,7 +242,10 @@ struct SlotIO {
 // Executes one staged op on the register slots.  `sel` is the part of a
 // diagonal op's selection outside the register set (true when the op has
 // none); diagonal ops apply branch-free with sign / identity when unmet.
-template <int RB, typename V, typename R>
+// FULL = false leaves out the cases of the parameterised gates (shears and
+// general phases on register bits), which the Clifford+T circuits never
+// stage; the smaller interpreter costs less instruction fetch per op.
+template <int RB, bool FULL, typename V, typename R>
 __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, uint64_t qmask, R &fr,
                                         R &fi, const R *phase)
 {
@@ -259,14 +262,14 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, ui
     case K_H + J: reg_h<NS, J>(a); break;                                        \
     case K_XH + J: reg_xh<NS, J>(a); break;                                      \
     case K_YH + J: reg_yh<NS, J>(a); break;                                      \
-    case K_SHX + J: reg_shear<NS, J, 0>(a, phase[0]); break;                     \
-    case K_SHY + J: reg_shear<NS, J, 1>(a, phase[0]); break;
+    case K_SHX + J: if (FULL) reg_shear<NS, J, 0>(a, phase[0]); break;                     \
+    case K_SHY + J: if (FULL) reg_shear<NS, J, 1>(a, phase[0]); break;
     QS_B(0) QS_B(1) QS_B(2) QS_B(3)
 #undef QS_B
 #define QS_M(M)                                                                  \
     case K_T + M: reg_phase<NS, M>(a, c, c, true); break;                        \
     case K_NEG + M: reg_sign<NS, M>(a, QS_SGN); break;                           \
-    case K_PH + M: reg_phase<NS, M>(a, QS_PR, QS_PI, false); break;
+    case K_PH + M: if (FULL) reg_phase<NS, M>(a, QS_PR, QS_PI, false); break;
     // one- and two-qubit gates select at most two register bits
     QS_M(1) QS_M(2) QS_M(4) QS_M(8) QS_M(3) QS_M(5) QS_M(6) QS_M(9) QS_M(10) QS_M(12)
 #undef QS_M
@@ -274,12 +277,12 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, ui
     case K_H + J: reg_h<NS, (J < RB ? J : 0)>(a); break;                         \
     case K_XH + J: reg_xh<NS, (J < RB ? J : 0)>(a); break;                       \
     case K_YH + J: reg_yh<NS, (J < RB ? J : 0)>(a); break;                       \
-    case K_SHX + J: reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;      \
-    case K_SHY + J: reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
+    case K_SHX + J: if (FULL) reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;      \
+    case K_SHY + J: if (FULL) reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
 #define QS_M4(M)                                                                 \
     case K_T + M: reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break;         \
     case K_NEG + M: reg_sign<NS, ((M) & (NS - 1))>(a, QS_SGN); break;            \
-    case K_PH + M: reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
+    case K_PH + M: if (FULL) reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
     QS_B4(4) QS_M4(16) QS_M4(17) QS_M4(18) QS_M4(20) QS_M4(24)
 #undef QS_B4
 #undef QS_M4
@@ -574,7 +577,7 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
 // Runs tiles [t_begin, t_end) of one pass on `amps`: stages the pass's
 // phases and ops into shared memory, then loads, transforms and stores each
 // tile.  Shared by the single-state kernel and the batched kernel.
-template <typename R, int RB, bool TC>
+template <typename R, int RB, bool TC, bool FULL>
 __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__ amps,
                                                 const DevPass *__restrict__ pass_g,
                                                 const DevPhase *__restrict__ phases_g,
@@ -687,6 +690,14 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     const R gsr = (R)S.P.gscale_re, gsi = (R)S.P.gscale_im;
     const bool gscale_one = (S.P.gscale_re == 1.0 && S.P.gscale_im == 0.0);
     __syncthreads();
+    // the pass-wide factor rides on the last phase's registers when that is a
+    // register phase; otherwise it is applied at the tile store
+    const bool gs_in_phase = !gscale_one && S.ph[nph - 1].kind == 0;
+    const bool gs_at_store = !gscale_one && !gs_in_phase;
+    // tile element CE (it nthr + tid) sits at swizzled byte offset
+    // sw_tid ^ swz(CE it nthr) (the swizzle is linear, the bits are disjoint)
+    const uint32_t tile_sa = smem_addr(smem_raw);
+    const uint32_t sw_tid = swz<CE>((uint32_t)(CE * tid)) * (uint32_t)sizeof(V);
 
     // the tile base (bits of the out-of-tile qubits) advances by a masked
     // increment over the contiguous tile range
@@ -705,13 +716,14 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     tc_bbuf += (1024u - (smem_addr(tc_bbuf) & 1023u)) & 1023u;
     for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
         if (TC && TS.abort) break;
+        // out-of-tile and thread bits are disjoint from it_off: OR = add
+        const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
 #pragma unroll
         for (int it = 0; it < CPT; ++it) {
-            uint32_t e = (uint32_t)(CE * (it * nthr + tid));
-            const V *src = amps + (base | tid_off | S.it_off[it]);
-            uint32_t saddr = (uint32_t)__cvta_generic_to_shared(tile + swz<CE>(e));
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(src)
+            const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tile_sa + sw),
+                         "l"(tsrc + S.it_off[it])
                          : "memory");
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -750,14 +762,26 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             const bool fpend = S.ph[ph].uniform_ops != 0;
             for (int o = ob; o < oe; ++o) {
                 const SOp<R> op = S.ops[o];
-                exec_op<RB>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
+                exec_op<RB, FULL>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
             }
-            if (fpend) {
+            bool fmul = fpend;
+            if (gs_in_phase && ph == nph - 1) {
+                const R x = fr * gsr - fi * gsi;
+                fi = fr * gsi + fi * gsr;
+                fr = x;
+                fmul = true;
+            }
+            if (fmul) {
+                if (fi == (R)0) {
 #pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    const R x = a[s].x * fr - a[s].y * fi;
-                    a[s].y = a[s].x * fi + a[s].y * fr;
-                    a[s].x = x;
+                    for (int s = 0; s < NS; ++s) mul_sign(a[s], fr);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const R x = a[s].x * fr - a[s].y * fi;
+                        a[s].y = a[s].x * fi + a[s].y * fr;
+                        a[s].x = x;
+                    }
                 }
             }
             {
@@ -774,13 +798,14 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             }
             __syncthreads();
         }
-        // ---- store the tile, applying the pass-wide factor ----
+        // ---- store the tile ----
+        V *tdst = amps + (base | tid_off);
 #pragma unroll
         for (int it = 0; it < CPT; ++it) {
-            uint32_t e = (uint32_t)(CE * (it * nthr + tid));
+            const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
             V v[CE];
-            *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(tile + swz<CE>(e));
-            if (!gscale_one) {
+            *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(smem_raw + sw);
+            if (gs_at_store) {
 #pragma unroll
                 for (int q = 0; q < CE; ++q) {
                     const R x = v[q].x * gsr - v[q].y * gsi;
@@ -788,8 +813,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                     v[q].x = x;
                 }
             }
-            *reinterpret_cast<float4 *>(amps + (base | tid_off | S.it_off[it])) =
-                *reinterpret_cast<const float4 *>(v);
+            *reinterpret_cast<float4 *>(tdst + S.it_off[it]) = *reinterpret_cast<const float4 *>(v);
         }
         __syncthreads();
     }
@@ -797,7 +821,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     __syncthreads();
 }
 
-template <typename R, int RB, bool TC>
+template <typename R, int RB, bool TC, bool FULL>
 __global__ void __launch_bounds__(kThreadsMax, TC ? 1 : 2)
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
@@ -810,8 +834,26 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
     const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
     const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
-    fused_pass_body<R, RB, TC>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
-                               smem_raw);
+    fused_pass_body<R, RB, TC, FULL>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
+                                     smem_raw);
+}
+
+// True when pass `hp` stages a shear or a general phase on register bits
+// (the interpreter cases that only the FULL kernel carries).  Mirrors the
+// device staging: a phase op with m0 = m1 = 1/sqrt2 is staged as a T phase.
+static bool pass_needs_full(const Plan &plan, const DevPass &hp)
+{
+    const int o0 = plan.phases[hp.phase_begin].op_begin;
+    const int o1 = plan.phases[hp.phase_begin + hp.nphases - 1].op_end;
+    for (int o = o0; o < o1; ++o) {
+        const DevOp &d = plan.ops[o];
+        if (d.type == OP_SHX || d.type == OP_SHY) return true;
+        if (d.type == OP_PHASE && d.rmask) {
+            const bool tphase = d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
+            if (!tphase) return true;
+        }
+    }
+    return false;
 }
 
 // Batched form: work item = (instance amplitudes, pass, tile range); the
@@ -835,7 +877,7 @@ k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict_
     __shared__ TcSmem TS;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
-        fused_pass_body<R, RB, false>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
+        fused_pass_body<R, RB, false, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
                                       w.tile_end, nullptr, nullptr, S, TS, smem_raw);
     }
 }
@@ -865,7 +907,7 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                     return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need 13-bit tiles");
                 if (!any_tc) QS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
                 any_tc = true;
-                auto kern = k_fused_pass<R, RB, true>;
+                auto kern = k_fused_pass<R, RB, true, true>;
                 const size_t smem = (size_t(1) << hp.t) * sizeof(V) + 65536 + 1024;
                 QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 const uint64_t cap = (uint64_t)s->num_sms;
@@ -876,7 +918,7 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                 return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need complex64");
             }
         } else {
-            auto kern = k_fused_pass<R, RB, false>;
+            auto kern = pass_needs_full(plan, hp) ? k_fused_pass<R, RB, false, true> : k_fused_pass<R, RB, false, false>;
             const size_t smem = (size_t(1) << hp.t) * sizeof(V);
             QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const uint64_t cap = (uint64_t)s->num_sms * 2;

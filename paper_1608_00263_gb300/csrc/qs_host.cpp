@@ -206,6 +206,149 @@ extern "C" qs_status qs_circuit_generate(int rows, int cols, const uint8_t *dead
     return QS_OK;
 }
 
+// Dense layouts with periodic boundaries (appendix "Depth to reach
+// Porter-Thomas for denser 2D circuits"): on an even rows x cols torus the
+// CZ cycle of layer l uses pattern (l-1) mod 4 of
+//   H_even: (r,c)-(r,c+1), c even      V_even: (r,c)-(r+1,c), r even
+//   H_odd:  (r,c)-(r,c+1 mod cols), c odd
+//   V_odd:  (r,c)-(r+1 mod rows,c), r odd
+// so every qubit is in exactly one CZ per CZ cycle (the eight sparse
+// layouts merged in consecutive pairs).  Layer l: cycle 2l-1 single-qubit
+// gates under the rules of Sec. "Convergence to Porter-Thomas" (a gate only
+// on a qubit in a CZ in the previous cycle, T first after H, then different
+// from the previous one), cycle 2l the CZ cycle.
+extern "C" qs_status qs_circuit_generate_dense(int rows, int cols, int layers, uint64_t seed,
+                                               qs_gate *out, size_t *ngates)
+{
+    clear_error();
+    if (rows < 2 || cols < 2 || (rows & 1) || (cols & 1) || rows * cols > 64)
+        return set_error(QS_ERR_INVALID_ARG, "dense layouts need an even torus of <= 64 sites, got %d x %d",
+                         rows, cols);
+    if (layers < 0) return set_error(QS_ERR_INVALID_ARG, "negative layer count");
+    if (!ngates) return set_error(QS_ERR_INVALID_ARG, "ngates is NULL");
+    const int n = rows * cols;
+    const size_t cap = out ? *ngates : 0;
+    size_t count = 0;
+    auto emit = [&](int kind, int a, int b, int cycle) {
+        if (out && count < cap) {
+            qs_gate &g = out[count];
+            g.kind = (uint8_t)kind; g.q0 = (uint8_t)a; g.q1 = (uint8_t)b; g.pad = 0;
+            g.cycle = (uint32_t)cycle; g.theta = 0.0;
+        }
+        ++count;
+    };
+    SplitMix64 rng(seed);
+    std::vector<int> previous(n, -1);
+    for (int q = 0; q < n; ++q) emit(QS_H, q, 0, 0);
+    for (int l = 1; l <= layers; ++l) {
+        // the previous cycle was a CZ cycle covering every qubit, except
+        // before layer 1 (the H cycle)
+        if (l > 1) {
+            for (int q = 0; q < n; ++q) {
+                int kind;
+                if (previous[q] < 0) {
+                    kind = QS_T;
+                } else {
+                    int choices[2], m = 0;
+                    for (int k : {QS_X_HALF, QS_Y_HALF, QS_T})
+                        if (k != previous[q]) choices[m++] = k;
+                    kind = choices[rng.next() >> 63];
+                }
+                emit(kind, q, 0, 2 * l - 1);
+                previous[q] = kind;
+            }
+        }
+        const int pat = (l - 1) % 4;
+        const bool vert = pat & 1, odd = pat >= 2;
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c) {
+                if ((vert ? r : c) % 2 != (odd ? 1 : 0)) continue;
+                const int r2 = vert ? (r + 1) % rows : r, c2 = vert ? c : (c + 1) % cols;
+                const int a = r * cols + c, b = r2 * cols + c2;
+                emit(QS_CZ, std::min(a, b), std::max(a, b), 2 * l);
+            }
+    }
+    if (out && count > cap) {
+        *ngates = count;
+        return set_error(QS_ERR_INVALID_ARG, "output holds %zu gates, circuit has %zu", cap, count);
+    }
+    *ngates = count;
+    return QS_OK;
+}
+
+// Digital error model of Sec. "Characterizing quantum supremacy" (the
+// depolarising channel after each gate): one trajectory of the channel.
+// Draws come from one SplitMix64 stream seeded with `seed`, u = (z >> 11)
+// 2^-53 per draw, in this order: one draw per qubit for the initialisation
+// bit flip (X if u < r_init), then one draw per gate of the list: after a
+// one-qubit gate, if u < r1 the Pauli floor(3u / r1) of (X, Y, Z); after a
+// two-qubit gate, if u < r2 the pair number e = floor(15u / r2) + 1 (base-4
+// digits (e / 4, e % 4) = (P on q0, P on q1), 0 = I, 1..3 = X, Y, Z).
+// Paulis are emitted as R_X(pi), R_Y(pi), R_Z(pi) (the Pauli up to the global
+// phase -i), in the cycle of the gate they follow.
+extern "C" qs_status qs_noisy_circuit(const qs_gate *gates, size_t ngates, int n, double r1, double r2,
+                                      double r_init, uint64_t seed, qs_gate *out, size_t *nout)
+{
+    clear_error();
+    if (!nout || n < 1 || n > 64) return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    if (!(r1 >= 0 && r1 <= 1 && r2 >= 0 && r2 <= 1 && r_init >= 0 && r_init <= 1))
+        return set_error(QS_ERR_INVALID_ARG, "error rates must lie in [0, 1]");
+    if (qs_status st = validate_gates(n, gates, ngates)) return st;
+    const size_t cap = out ? *nout : 0;
+    size_t count = 0;
+    auto put = [&](const qs_gate &g) {
+        if (out && count < cap) out[count] = g;
+        ++count;
+    };
+    auto pauli = [&](int which, int q, uint32_t cycle) {   // which: 1 X, 2 Y, 3 Z
+        static const int kind[4] = {-1, QS_RX, QS_RY, QS_RZ};
+        qs_gate g{};
+        g.kind = (uint8_t)kind[which]; g.q0 = (uint8_t)q; g.cycle = cycle; g.theta = M_PI;
+        put(g);
+    };
+    SplitMix64 rng(seed);
+    auto uniform = [&]() { return (double)(rng.next() >> 11) * (1.0 / 9007199254740992.0); };
+    const uint32_t c0 = ngates ? gates[0].cycle : 0;
+    for (int q = 0; q < n; ++q)
+        if (uniform() < r_init) pauli(1, q, c0);
+    for (size_t i = 0; i < ngates; ++i) {
+        const qs_gate &g = gates[i];
+        put(g);
+        const double u = uniform();
+        if (gate_is_two_qubit(g.kind)) {
+            if (u < r2) {
+                const int e = std::min(14, (int)(15.0 * u / r2)) + 1;
+                if (e / 4) pauli(e / 4, g.q0, g.cycle);
+                if (e % 4) pauli(e % 4, g.q1, g.cycle);
+            }
+        } else if (u < r1) {
+            pauli(std::min(2, (int)(3.0 * u / r1)) + 1, g.q0, g.cycle);
+        }
+    }
+    if (out && count > cap) {
+        *nout = count;
+        return set_error(QS_ERR_INVALID_ARG, "output holds %zu gates, trajectory has %zu", cap, count);
+    }
+    *nout = count;
+    return QS_OK;
+}
+
+// First index i of an entropy series such that every entry from i on lies
+// within 4 sigma of the Porter-Thomas entropy ln N - 1 + gamma, sigma =
+// 0.75 * 2^(-n/2) (Sec. "Convergence to Porter-Thomas", Fig. pt_depth).
+extern "C" qs_status qs_pt_convergence(const double *entropy, size_t count, int n, size_t *first)
+{
+    clear_error();
+    if ((count && !entropy) || !first || n < 1 || n > 64)
+        return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    const double h_pt = n * std::log(2.0) - 1.0 + 0.57721566490153286061;
+    const double tol = 4.0 * 0.75 * std::pow(2.0, -0.5 * n);
+    size_t i = count;
+    while (i > 0 && std::fabs(entropy[i - 1] - h_pt) <= tol) --i;
+    *first = i;
+    return QS_OK;
+}
+
 namespace qs {
 
 // ---------------------------------------------------------------------------

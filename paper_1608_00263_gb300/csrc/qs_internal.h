@@ -193,6 +193,11 @@ qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const voi
 size_t batch_item_bytes();
 qs_status batch_kernel_setup();
 void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, uint32_t te);
+// Batched sampler over instances laid out at element offsets off_h[i]
+// (2^n_h[i] complex64 each): k samples per instance into host_out[i k + j].
+qs_status batch_sampler_run(cudaStream_t st, int num_sms, const void *amps_v, const uint64_t *off_h,
+                            const int *n_h, int count, uint64_t k, uint64_t seed, double r_mes,
+                            uint64_t *host_out);
 qs_status launch_batch_stats(cudaStream_t st, int num_sms, const void *amps, const uint64_t *item_off,
                              const uint64_t *item_cnt, const float *item_scale, int nitems,
                              const int *first_item, int count, double *part, double *out);

@@ -19,7 +19,9 @@
 // rescans one chunk with exactly the arithmetic that produced the chunk's
 // sum.
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "qs_device.cuh"
 
@@ -541,6 +543,164 @@ qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *de
     }
     cudaFreeAsync(csum, s->stream);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// batched sampler: every instance of a batch, k samples each
+//
+// Chunks of 256 amplitudes never straddle instances: instance i owns global
+// chunks [cbase[i], cbase[i+1]) (its last chunk may be short).  One
+// inclusive FP64 scan runs over all chunk sums; instance i's CDF is the scan
+// minus the value before its first chunk.  Sample (i, j) draws u from the
+// counter-based stream at index i k + j and applies the measurement bit
+// flips of the error model (bit b flips if the draw at index (i k + j) 64 + b
+// of the stream seeded with seed ^ 0xD1B54A32D192ED03 is below r_mes).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int batch_instance_of(const uint64_t *cbase, int count, uint64_t c)
+{
+    int lo = 0, hi = count - 1;   // largest i with cbase[i] <= c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cbase[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_batch_chunk_sums(const float2 *__restrict__ amps, const uint64_t *__restrict__ off,
+                                   const int *__restrict__ nq, const uint64_t *__restrict__ cbase, int count,
+                                   double *__restrict__ csum)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t nchunks = cbase[count];
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += warps) {
+        const int i = batch_instance_of(cbase, count, c);
+        float p[8];
+        lane_probs<float>(amps + off[i], c - cbase[i], lane, 1ULL << nq[i], p);
+        const double incl = warp_incl_scan((double)lane_total<float>(p));
+        if (lane == 31) csum[c] = incl;
+    }
+}
+
+__global__ void k_batch_sample_search(const float2 *__restrict__ amps, const uint64_t *__restrict__ off,
+                                      const int *__restrict__ nq, const uint64_t *__restrict__ cbase, int count,
+                                      const double *__restrict__ cincl, uint64_t k, uint64_t seed, double r_mes,
+                                      uint64_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t m = (uint64_t)count * k;
+    const uint64_t flip_seed = seed ^ 0xD1B54A32D192ED03ULL;
+    for (uint64_t j0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; j0 < m;
+         j0 += warps * 32) {
+        const uint64_t j = j0 + lane;
+        int inst = 0;
+        double tloc = 0;
+        uint64_t chunk = 0;
+        bool ok = false;
+        if (j < m) {
+            inst = (int)(j / k);
+            const uint64_t c0 = cbase[inst], c1 = cbase[inst + 1];
+            const double before = c0 ? cincl[c0 - 1] : 0.0;
+            const double total = cincl[c1 - 1] - before;
+            ok = total > 0;
+            const double u = (double)(splitmix_out(seed, j) >> 11) * (1.0 / 9007199254740992.0);
+            const double target = before + u * total;
+            uint64_t lo = c0, hi = c1 - 1;
+            while (lo < hi) {
+                const uint64_t mid = lo + (hi - lo) / 2;
+                if (cincl[mid] > target) hi = mid; else lo = mid + 1;
+            }
+            chunk = lo;
+            tloc = target - (lo ? cincl[lo - 1] : 0.0);
+        }
+        const int cnt = (int)((m - j0) < 32 ? (m - j0) : 32);
+        for (int q = 0; q < cnt; ++q) {
+            const uint64_t c = __shfl_sync(0xffffffffu, chunk, q);
+            const double tq = __shfl_sync(0xffffffffu, tloc, q);
+            const int iq = __shfl_sync(0xffffffffu, inst, q);
+            const uint64_t lc = c - cbase[iq];
+            float p[8];
+            lane_probs<float>(amps + off[iq], lc, lane, 1ULL << nq[iq], p);
+            const float lt = lane_total<float>(p);
+            const double incl = warp_incl_scan((double)lt);
+            const double excl = incl - (double)lt;
+            const unsigned hit = __ballot_sync(0xffffffffu, incl > tq);
+            const unsigned nz = __ballot_sync(0xffffffffu, lt > 0.f);
+            const int L = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);
+            uint64_t res = 0;
+            if (lane == L) {
+                float acc = 0.f;
+                int pick = -1, last_nz = -1;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    acc += p[t];
+                    if (p[t] > 0.f) last_nz = t;
+                    if (pick < 0 && p[t] > 0.f && excl + (double)acc > tq) pick = t;
+                }
+                if (pick < 0) pick = last_nz < 0 ? 0 : last_nz;
+                res = lc * kChunk + (uint64_t)L * 8 + (uint64_t)pick;
+            }
+            res = __shfl_sync(0xffffffffu, res, L);
+            if (lane == q) {
+                if (ok) {
+                    for (int b = 0; b < nq[iq]; ++b) {
+                        const double v = (double)(splitmix_out(flip_seed, j * 64 + (uint64_t)b) >> 11) *
+                                         (1.0 / 9007199254740992.0);
+                        if (v < r_mes) res ^= 1ULL << b;
+                    }
+                } else {
+                    res = ~0ULL;      // instance with zero norm: no sample
+                }
+                out[j0 + q] = res;
+            }
+        }
+    }
+}
+
+qs_status batch_sampler_run(cudaStream_t st, int num_sms, const void *amps_v, const uint64_t *off_h,
+                            const int *n_h, int count, uint64_t k, uint64_t seed, double r_mes, uint64_t *host_out)
+{
+    const float2 *amps = static_cast<const float2 *>(amps_v);
+    std::vector<uint64_t> cb(count + 1, 0);
+    for (int i = 0; i < count; ++i) cb[i + 1] = cb[i] + (((1ULL << n_h[i]) + kChunk - 1) / kChunk);
+    const uint64_t nchunks = cb[count];
+    const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
+    const uint64_t m = (uint64_t)count * k;
+    // one scratch buffer: instance tables, chunk sums, block totals, samples
+    const size_t b_off = (size_t)count * 8, b_cb = (size_t)(count + 1) * 8, b_n = (size_t)count * 4;
+    const size_t o_cb = b_off, o_n = o_cb + b_cb, o_cs = (o_n + b_n + 15) / 16 * 16;
+    const size_t o_bt = o_cs + nchunks * 8, o_out = o_bt + (nblk + 1) * 8;
+    const size_t bytes = o_out + m * 8;
+    char *buf = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync((void **)&buf, bytes, st));
+    std::vector<char> host(o_cs);
+    std::memcpy(host.data(), off_h, b_off);
+    std::memcpy(host.data() + o_cb, cb.data(), b_cb);
+    std::memcpy(host.data() + o_n, n_h, b_n);
+    qs_status status = QS_OK;
+    cudaError_t e = cudaMemcpyAsync(buf, host.data(), o_cs, cudaMemcpyHostToDevice, st);
+    const uint64_t *d_off = (const uint64_t *)buf, *d_cb = (const uint64_t *)(buf + o_cb);
+    const int *d_n = (const int *)(buf + o_n);
+    double *csum = (double *)(buf + o_cs), *btot = (double *)(buf + o_bt);
+    uint64_t *d_out = (uint64_t *)(buf + o_out);
+    if (e == cudaSuccess) {
+        const int th = 256;
+        k_batch_chunk_sums<<<grid_for(nchunks * 32, th, num_sms, 16), th, 0, st>>>(amps, d_off, d_n, d_cb, count,
+                                                                                csum);
+        k_scan_block_totals<<<(unsigned)nblk, kScanThreads, 0, st>>>(csum, nchunks, btot);
+        k_scan_totals<<<1, kScanThreads, 0, st>>>(btot, (int)nblk);
+        k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, st>>>(csum, nchunks, btot);
+        if (m)
+            k_batch_sample_search<<<grid_for((m + 31) / 32 * 32, th, num_sms, 16), th, 0, st>>>(
+                amps, d_off, d_n, d_cb, count, csum, k, seed, r_mes, d_out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && m) e = cudaMemcpyAsync(host_out, d_out, m * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) status = set_error(QS_ERR_CUDA, "batch sampler: %s", cudaGetErrorString(e));
+    cudaFreeAsync(buf, st);
+    return status;
 }
 
 // ---------------------------------------------------------------------------
