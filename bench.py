@@ -288,13 +288,15 @@ def run_ours(args, rank, world, local):
         n34 = forms_34(qs, torch, hbm_peak)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
 
-    ens = None
+    ens = noisy = single = None
     if rank == 0 and not args.no_compare and args.workload == DEFAULT_WORKLOAD:
         if h is not None:
             qs.qs_state_destroy(h)
         h = None
         torch.cuda.empty_cache()
         ens = ensemble_4096(qs, torch, hbm_peak)
+        noisy = noisy_trajectories(qs, torch)
+        single = single_error_sweep(qs, torch)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
 
     cpu = None
@@ -321,7 +323,8 @@ def run_ours(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "apply_cycles_per_s": round(depth * args.steps / (apply_total / 1000.0), 3),
         "passes_per_circuit": passes_total / args.steps,
-        "roofline": {"kernel": "k_fused_pass<float,5,%s>" % ("false" if args.mode == "fused" else "true"),
+        "roofline": {"kernel": ("k_fused_pass<float,5,false,false>" if args.mode == "fused"
+                                else "k_fused_pass<float,5,true,true>"),
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
@@ -334,6 +337,8 @@ def run_ours(args, rank, world, local):
         "forms": compare,
         "n34": n34,
         "ensemble": ens,
+        "noisy": noisy,
+        "single_error": single,
     }
     if cpu:
         out["cpu_baseline"] = cpu
@@ -424,6 +429,79 @@ def ensemble_4096(qs, torch, hbm_peak):
     return {"instances": 4096, "state_gb": round(bytes_state / 1e9, 1), "first_run_s": round(first, 3),
             "replay_s": round(dt, 4), "cycles_per_s": round(cycles / dt, 1),
             "mean_norm": round(float(np.mean(st[:, 0])), 7)}
+
+
+def noisy_trajectories(qs, torch, T=4096, r=0.005):
+    """Digital error model on the batched engine (Fig. pal setting: 5 x 4
+    qubits, depth 40, r2 = r_init = r_mes = r, r1 = r/10): T trajectories,
+    one sample each, cross entropy difference under the ideal circuit
+    against Eq. 6.  Timed: trajectories on the GPU + batched sampling."""
+    import numpy as np
+    rows, cols, depth = 4, 5, 40
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, 0)
+    g1 = int(np.sum(g["kind"] != qs.QS_CZ))
+    g2 = int(np.sum(g["kind"] == qs.QS_CZ))
+    t0 = time.perf_counter()
+    lists = [qs.qs_noisy_circuit(g, n, r / 10, r, r, 7000 + t) for t in range(T)]
+    gen_s = time.perf_counter() - t0
+    b = qs.qs_batch_create([n] * T)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        t0 = time.perf_counter()
+        qs.qs_batch_run(b, lists, kmax=0)
+        x = qs.qs_batch_sample(b, 1, 321, r).reshape(-1)
+        run_s = time.perf_counter() - t0
+        qs.qs_apply_circuit(h, g)
+        ce, dh = qs.qs_cross_entropy(h, x)
+    finally:
+        qs.qs_batch_destroy(b)
+        qs.qs_state_destroy(h)
+    alpha = math.exp(-(r / 10) * g1 - r * g2 - 2 * r * n)
+    return {"trajectories": T, "qubits": n, "depth": depth, "r": r, "host_generate_s": round(gen_s, 3),
+            "gpu_run_s": round(run_s, 3), "trajectories_per_s": round(T / run_s, 1),
+            "delta_h": round(dh, 4), "eq6_alpha": round(alpha, 4)}
+
+
+def single_error_sweep(qs, torch):
+    """Fig. 1error setting (5 x 4 qubits, depth 40): one batch instance per
+    error location (every cycle, qubit, X and Z: 1640 circuits), Pearson
+    correlation of each with the ideal output and the error-averaged
+    distribution.  Timed: GPU run + correlations + mean distribution."""
+    import numpy as np
+    rows, cols, depth = 4, 5, 40
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, 0)
+    locs = [(c, q, pauli) for c in range(depth + 1) for q in range(n) for pauli in (1, 3)]
+    lists = [qs.qs_single_error_circuit(g, n, c, q, pauli) for c, q, pauli in locs]
+    b = qs.qs_batch_create([n] * len(lists))
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        t0 = time.perf_counter()
+        qs.qs_batch_run(b, lists, kmax=0)
+        qs.qs_apply_circuit(h, g)
+        corr = qs.qs_batch_correlation(b, h)
+        avg = qs.qs_batch_mean_probabilities(b, n)
+        run_s = time.perf_counter() - t0
+        p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        qs.qs_probabilities(h, p)
+        p = p.cpu().numpy()
+    finally:
+        qs.qs_batch_destroy(b)
+        qs.qs_state_destroy(h)
+    cyc = np.array([c for c, _, _ in locs])
+    zs = np.array([pauli == 3 for _, _, pauli in locs])
+    N = float(1 << n)
+    def mean_corr(mask):
+        return round(float(np.mean(corr[mask])), 4)
+    return {"locations": len(locs), "qubits": n, "depth": depth, "gpu_run_s": round(run_s, 3),
+            "circuits_per_s": round(len(locs) / run_s, 1),
+            "mean_corr_X": {"cycles_0_4": mean_corr(~zs & (cyc <= 4)), "cycles_10_30": mean_corr(~zs & (cyc >= 10) & (cyc <= 30)),
+                            "cycles_36_40": mean_corr(~zs & (cyc >= 36))},
+            "mean_corr_Z": {"cycles_0_4": mean_corr(zs & (cyc <= 4)), "cycles_10_30": mean_corr(zs & (cyc >= 10) & (cyc <= 30)),
+                            "cycles_36_40": mean_corr(zs & (cyc >= 36))},
+            "ideal_N_sum_p2": round(float(N * np.sum(p * p)), 4),
+            "averaged_N_sum_p2": round(float(N * np.sum(avg * avg)), 4)}
 
 
 def load_traffic(mode, n):

@@ -325,6 +325,31 @@ qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offset
  * Synchronous. */
 qs_status qs_batch_sample(qs_batch *b, uint64_t k, uint64_t seed, double r_mes, uint64_t *out);
 
+/* One discrete error at a chosen location (appendix "Residual correlations
+ * after discrete errors", Fig. 1error): copies the gate list (cycle numbers
+ * must not decrease) and inserts the Pauli `pauli` (1 = X, 2 = Y, 3 = Z,
+ * emitted as R_X / R_Y / R_Z(pi)) on `qubit` after the last gate whose cycle
+ * is <= `cycle` (cycle 0 = right after the H layer).  Output and count
+ * query as qs_circuit_generate (ngates + 1 gates).  Host only. */
+qs_status qs_single_error_circuit(const qs_gate *gates, size_t ngates, int n, uint32_t cycle,
+                                  int qubit, int pauli, qs_gate *out, size_t *nout);
+
+/* Residual correlations after discrete errors (appendix "Residual
+ * correlations after discrete errors", Figs. zcorr / xcorr): corr[i] =
+ * Pearson correlation over the 2^n basis states between instance i's output
+ * distribution and the reference state's, both complex64 of the same n
+ * (e.g. the circuit with one Pauli inserted vs the ideal circuit).  Sums of
+ * p_i p_ref, p_i^2, p_i, p_ref^2, p_ref are accumulated in FP64 over FP32
+ * products; corr = cov / sqrt(var_i var_ref) (0 if a variance is zero).
+ * Synchronous. */
+qs_status qs_batch_correlation(qs_batch *b, const qs_state *ref, double *corr);
+
+/* Mean output distribution over all instances (same n), out[x] =
+ * (1/count) sum_i |<x|psi_i>|^2 in FP64, host array of 2^n doubles: the
+ * error-averaged distribution of Fig. 1error when the instances carry one
+ * Pauli error each.  Synchronous. */
+qs_status qs_batch_mean_probabilities(qs_batch *b, double *out);
+
 /* One trajectory of the digital error model (Sec. "Characterizing quantum
  * supremacy": a depolarising channel after every gate, Eq. 6): copies the
  * gate list, inserting after each one-qubit gate, with probability r1, one

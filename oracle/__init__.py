@@ -183,6 +183,28 @@ def eq6_fidelity(r1, r2, r_init, r_mes, g1, g2, n):
     return math.exp(-r1 * g1 - r2 * g2 - r_init * n - r_mes * n)
 
 
+def single_error_circuit(gates, cycle, qubit, pauli):
+    """Appendix "Residual correlations after discrete errors": the circuit
+    with one Pauli (1 X, 2 Y, 3 Z; written R_P(pi)) on `qubit` placed after
+    every gate of cycles <= `cycle` and before the rest."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    at = int(np.sum(g["cycle"] <= cycle))
+    e = np.zeros(1, dtype=GATE_DTYPE)
+    e[0]["kind"] = {1: 5, 2: 6, 3: 7}[pauli]      # R_X, R_Y, R_Z
+    e[0]["q0"] = qubit
+    e[0]["cycle"] = cycle
+    e[0]["theta"] = math.pi
+    return np.concatenate([g[:at], e, g[at:]])
+
+
+def pearson(p, q):
+    """Correlation coefficient of two distributions over the basis states."""
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    dp, dq = p - p.mean(), q - q.mean()
+    return float(np.sum(dp * dq) / math.sqrt(np.sum(dp * dp) * np.sum(dq * dq)))
+
+
 def pt_convergence_index(entropies, n):
     """Sec. "Convergence to Porter-Thomas" (Fig. pt_depth): the first index i
     such that every entropy from i on is within 4 sigma of ln N - 1 + gamma,

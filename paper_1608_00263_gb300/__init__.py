@@ -27,6 +27,7 @@ __all__ = [
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
+    "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit",
     "library_path",
 ]
 
@@ -246,6 +247,33 @@ def qs_batch_sample(b, k, seed, r_mes=0.0):
     N.check(N.lib().qs_batch_sample(b, k, seed & (2**64 - 1), float(r_mes),
                                     out.ctypes.data if out.size else None))
     return out.reshape(count, k)
+
+
+def qs_single_error_circuit(gates, n, cycle, qubit, pauli):
+    """The gate list with one Pauli (1 X, 2 Y, 3 Z) on `qubit` after cycle `cycle`."""
+    g = _gates(gates)
+    cnt = ctypes.c_size_t(g.size + 1)
+    out = np.zeros(g.size + 1, dtype=GATE_DTYPE)
+    N.check(N.lib().qs_single_error_circuit(g.ctypes.data if g.size else None, g.size, n, cycle, qubit, pauli,
+                                            out.ctypes.data, ctypes.byref(cnt)))
+    return out
+
+
+def qs_batch_correlation(b, ref):
+    """Pearson correlation of every instance's distribution with the reference state's."""
+    count = _batch_sizes.get(b)
+    if count is None:
+        raise QSError(N.QS_ERR_INVALID_ARG, "unknown batch handle")
+    out = np.zeros(count, dtype=np.float64)
+    N.check(N.lib().qs_batch_correlation(b, ref, out.ctypes.data))
+    return out
+
+
+def qs_batch_mean_probabilities(b, n):
+    """Mean distribution over the batch's instances (all of n qubits)."""
+    out = np.zeros(1 << n, dtype=np.float64)
+    N.check(N.lib().qs_batch_mean_probabilities(b, out.ctypes.data))
+    return out
 
 
 def qs_pt_convergence(entropy, n):

@@ -138,6 +138,52 @@ extern "C" qs_status qs_batch_sample(qs_batch *b, uint64_t k, uint64_t seed, dou
                              r_mes, out);
 }
 
+extern "C" qs_status qs_batch_correlation(qs_batch *b, const qs_state *ref, double *corr)
+{
+    clear_error();
+    if (!b || !ref || !corr) return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    if (ref->dt != QS_C64) return set_error(QS_ERR_INVALID_ARG, "reference state must be complex64");
+    for (int i = 0; i < b->count; ++i)
+        if (b->n[i] != ref->n)
+            return set_error(QS_ERR_INVALID_ARG, "instance %d has %d qubits, reference %d", i, b->n[i], ref->n);
+    // the reference is read on the batch's stream after its own pending work
+    if (ref->stream != b->user_stream) {
+        cudaError_t e = cudaStreamSynchronize(ref->stream);
+        if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "reference stream: %s", cudaGetErrorString(e));
+    }
+    std::vector<double> h((size_t)b->count * 5);
+    if (qs_status st = batch_overlap_run(b->user_stream, b->num_sms, b->amps, ref->amps, b->off.data(), b->count,
+                                         ref->n, h.data()))
+        return st;
+    const double N = std::ldexp(1.0, ref->n);
+    for (int i = 0; i < b->count; ++i) {
+        const double *v = &h[(size_t)i * 5];
+        const double ma = v[2] / N, mb = v[4] / N;
+        const double cov = v[0] / N - ma * mb;
+        const double va = v[1] / N - ma * ma, vb = v[3] / N - mb * mb;
+        corr[i] = (va > 0 && vb > 0) ? cov / std::sqrt(va * vb) : 0.0;
+    }
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_mean_probabilities(qs_batch *b, double *out)
+{
+    clear_error();
+    if (!b || !out) return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    for (int i = 1; i < b->count; ++i)
+        if (b->n[i] != b->n[0]) return set_error(QS_ERR_INVALID_ARG, "instances differ in size");
+    const uint64_t N = 1ULL << b->n[0];
+    double *d = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync((void **)&d, N * sizeof(double), b->user_stream));
+    qs_status st = batch_mean_probs_run(b->user_stream, b->num_sms, b->amps, b->count, b->n[0], d);
+    cudaError_t e = cudaSuccess;
+    if (st == QS_OK) e = cudaMemcpyAsync(out, d, N * sizeof(double), cudaMemcpyDeviceToHost, b->user_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->user_stream);
+    cudaFreeAsync(d, b->user_stream);
+    if (st == QS_OK && e != cudaSuccess) st = set_error(QS_ERR_CUDA, "mean probabilities: %s", cudaGetErrorString(e));
+    return st;
+}
+
 // Plans every instance, lays out the concatenated plan, work items and
 // statistics items in one device buffer, and records the run as a graph.
 static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)

@@ -333,6 +333,34 @@ extern "C" qs_status qs_noisy_circuit(const qs_gate *gates, size_t ngates, int n
     return QS_OK;
 }
 
+// One discrete error (appendix "Residual correlations after discrete
+// errors"): the gate list with Pauli `pauli` (1 X, 2 Y, 3 Z, written as
+// R_P(pi)) on `qubit` inserted after the last gate whose cycle is <= `cycle`.
+extern "C" qs_status qs_single_error_circuit(const qs_gate *gates, size_t ngates, int n, uint32_t cycle,
+                                             int qubit, int pauli, qs_gate *out, size_t *nout)
+{
+    clear_error();
+    if (!nout || qubit < 0 || qubit >= n || pauli < 1 || pauli > 3)
+        return set_error(QS_ERR_INVALID_ARG, "bad arguments");
+    if (qs_status st = validate_gates(n, gates, ngates)) return st;
+    const size_t need = ngates + 1;
+    if (out && *nout < need) {
+        *nout = need;
+        return set_error(QS_ERR_INVALID_ARG, "output holds %zu gates, need %zu", *nout, need);
+    }
+    *nout = need;
+    if (!out) return QS_OK;
+    size_t at = 0;
+    while (at < ngates && gates[at].cycle <= cycle) ++at;
+    static const int kind[4] = {-1, QS_RX, QS_RY, QS_RZ};
+    for (size_t i = 0; i < at; ++i) out[i] = gates[i];
+    qs_gate e{};
+    e.kind = (uint8_t)kind[pauli]; e.q0 = (uint8_t)qubit; e.cycle = cycle; e.theta = M_PI;
+    out[at] = e;
+    for (size_t i = at; i < ngates; ++i) out[i + 1] = gates[i];
+    return QS_OK;
+}
+
 // First index i of an entropy series such that every entry from i on lies
 // within 4 sigma of the Porter-Thomas entropy ln N - 1 + gamma, sigma =
 // 0.75 * 2^(-n/2) (Sec. "Convergence to Porter-Thomas", Fig. pt_depth).

@@ -198,6 +198,14 @@ void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, ui
 qs_status batch_sampler_run(cudaStream_t st, int num_sms, const void *amps_v, const uint64_t *off_h,
                             const int *n_h, int count, uint64_t k, uint64_t seed, double r_mes,
                             uint64_t *host_out);
+// Per-instance overlap sums with a reference complex64 state of the same n
+// (instances at element offsets off_h, all of n qubits): host_sums[i*5 ..] =
+// sum p_i p_ref, sum p_i^2, sum p_i, sum p_ref^2, sum p_ref.
+qs_status batch_overlap_run(cudaStream_t st, int num_sms, const void *amps, const void *ref,
+                            const uint64_t *off_h, int count, int n, double *host_sums);
+// Mean distribution over `count` consecutive instances of n qubits.
+qs_status batch_mean_probs_run(cudaStream_t st, int num_sms, const void *amps, int count, int n,
+                               double *device_out);
 qs_status launch_batch_stats(cudaStream_t st, int num_sms, const void *amps, const uint64_t *item_off,
                              const uint64_t *item_cnt, const float *item_scale, int nitems,
                              const int *first_item, int count, double *part, double *out);

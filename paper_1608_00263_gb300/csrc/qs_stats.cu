@@ -18,6 +18,7 @@
 // 256-amplitude chunk (N/32 bytes), scans those, and for each sample
 // rescans one chunk with exactly the arithmetic that produced the chunk's
 // sum.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -701,6 +702,127 @@ qs_status batch_sampler_run(cudaStream_t st, int num_sms, const void *amps_v, co
     if (e != cudaSuccess) status = set_error(QS_ERR_CUDA, "batch sampler: %s", cudaGetErrorString(e));
     cudaFreeAsync(buf, st);
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// batch against a reference state (appendix "Residual correlations after
+// discrete errors"): per instance i the sums S_ab = sum_x p_i(x) p_ref(x),
+// S_aa = sum p_i^2, S_a = sum p_i, S_bb, S_b, in items of one instance chunk
+// (FP32 products over strips of 64 elements per thread, FP64 across strips,
+// fixed-order block and item reductions); and the mean distribution
+// (1/count) sum_i p_i(x) (Fig. 1error), summed over instances in index order.
+// ---------------------------------------------------------------------------
+constexpr int kOvlAcc = 5;
+
+__global__ void __launch_bounds__(kStatThreads)
+k_batch_overlap(const float2 *__restrict__ amps, const float2 *__restrict__ ref,
+                const uint64_t *__restrict__ item_off, const uint64_t *__restrict__ item_ref,
+                const uint64_t *__restrict__ item_cnt, int nitems, double *__restrict__ part)
+{
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const float2 *a = amps + item_off[it];
+        const float2 *r = ref + item_ref[it];
+        const uint64_t cnt = item_cnt[it];
+        double acc[kOvlAcc] = {0, 0, 0, 0, 0};
+        for (uint64_t i0 = threadIdx.x; i0 < cnt; i0 += (uint64_t)blockDim.x * 64) {
+            float c[kOvlAcc] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            for (uint64_t i = i0, j = 0; j < 64 && i < cnt; ++j, i += blockDim.x) {
+                const float2 u = a[i], v = r[i];
+                const float pa = u.x * u.x + u.y * u.y, pb = v.x * v.x + v.y * v.y;
+                c[0] = fmaf(pa, pb, c[0]);
+                c[1] = fmaf(pa, pa, c[1]);
+                c[2] += pa;
+                c[3] = fmaf(pb, pb, c[3]);
+                c[4] += pb;
+            }
+#pragma unroll
+            for (int k = 0; k < kOvlAcc; ++k) acc[k] += (double)c[k];
+        }
+        block_sum_store<kOvlAcc>(acc, part + (size_t)it * kOvlAcc);
+        __syncthreads();
+    }
+}
+
+__global__ void k_batch_overlap_sum(const double *__restrict__ part, const int *__restrict__ first_item,
+                                    int count, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    for (int k = 0; k < kOvlAcc; ++k) {
+        double s = 0;
+        for (int it = first_item[i]; it < first_item[i + 1]; ++it) s += part[(size_t)it * kOvlAcc + k];
+        out[(size_t)i * kOvlAcc + k] = s;
+    }
+}
+
+__global__ void k_batch_mean_probs(const float2 *__restrict__ amps, uint64_t N, int count,
+                                   double *__restrict__ out)
+{
+    const double inv = 1.0 / count;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        double s = 0;
+        for (int i = 0; i < count; ++i) {
+            const float2 u = amps[(uint64_t)i * N + x];
+            s += (double)(u.x * u.x + u.y * u.y);
+        }
+        out[x] = s * inv;
+    }
+}
+
+// Sums per instance into host_sums[i * 5 + {S_ab, S_aa, S_a, S_bb, S_b}].
+qs_status batch_overlap_run(cudaStream_t st, int num_sms, const void *amps_v, const void *ref_v,
+                            const uint64_t *off_h, int count, int n, double *host_sums)
+{
+    const float2 *amps = static_cast<const float2 *>(amps_v);
+    const float2 *ref = static_cast<const float2 *>(ref_v);
+    const uint64_t N = 1ULL << n, chunk = std::min<uint64_t>(N, 1ULL << 16), per = N / chunk;
+    const int nitems = (int)(per * (uint64_t)count);
+    std::vector<uint64_t> tab(3 * (size_t)nitems);
+    std::vector<int> first(count + 1);
+    for (int i = 0; i < count; ++i) {
+        first[i] = (int)(i * per);
+        for (uint64_t c = 0; c < per; ++c) {
+            const size_t it = (size_t)(i * per + c);
+            tab[it] = off_h[i] + c * chunk;
+            tab[nitems + it] = c * chunk;
+            tab[2 * (size_t)nitems + it] = chunk;
+        }
+    }
+    first[count] = nitems;
+    const size_t b_tab = tab.size() * 8, b_first = (size_t)(count + 1) * 4;
+    const size_t o_first = b_tab, o_part = (o_first + b_first + 15) / 16 * 16;
+    const size_t o_out = o_part + (size_t)nitems * kOvlAcc * 8;
+    const size_t bytes = o_out + (size_t)count * kOvlAcc * 8;
+    char *buf = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync((void **)&buf, bytes, st));
+    cudaError_t e = cudaMemcpyAsync(buf, tab.data(), b_tab, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + o_first, first.data(), b_first, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        const uint64_t *d_tab = (const uint64_t *)buf;
+        double *part = (double *)(buf + o_part), *out = (double *)(buf + o_out);
+        const int grid = nitems < num_sms * 8 ? nitems : num_sms * 8;
+        k_batch_overlap<<<grid, kStatThreads, 0, st>>>(amps, ref, d_tab, d_tab + nitems, d_tab + 2 * (size_t)nitems,
+                                                       nitems, part);
+        k_batch_overlap_sum<<<(count + 127) / 128, 128, 0, st>>>(part, (const int *)(buf + o_first), count, out);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_sums, out, (size_t)count * kOvlAcc * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "batch overlap: %s", cudaGetErrorString(e));
+    return QS_OK;
+}
+
+qs_status batch_mean_probs_run(cudaStream_t st, int num_sms, const void *amps_v, int count, int n,
+                               double *device_out)
+{
+    const uint64_t N = 1ULL << n;
+    k_batch_mean_probs<<<grid_for(N, 256, num_sms, 8), 256, 0, st>>>(static_cast<const float2 *>(amps_v), N,
+                                                                     count, device_out);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
 }
 
 // ---------------------------------------------------------------------------
