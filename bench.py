@@ -188,15 +188,22 @@ def run_ours(args, rank, world, local):
     timed_gates = []
     results = {}
 
-    def step(i, timed):
+    def prepare(i):
+        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, base_seed + i, dead)  # a1
+        qs.qs_prepare_circuit(h, gates, mode=mode)                                      # a3 (host plan)
+        return gates
+
+    # Host planning is pipelined with the device: circuit i+1 is generated and
+    # planned while the GPU evolves circuit i (the state keeps two plans), so
+    # each timed step holds one generate + plan and one evolution + read-out.
+    def step(i, timed, gates):
         seed = base_seed + i
-        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed, dead)   # a1
         qs.qs_state_reset(h)                                                         # a2
-        qs.qs_prepare_circuit(h, gates, mode=mode)                                   # a3 (host plan)
         e0, e1 = ev(), ev()
         e0.record(stream)
         qs.qs_apply_circuit(h, gates, mode=mode)                                     # a4-a6
         e1.record(stream)
+        nxt = prepare(i + 1)                                                         # overlaps a4-a6
         qs.qs_probabilities(h, probs, fp64=W["fp64_probs"])                          # a7
         st = qs.qs_pt_moments(h, 10)                                                 # a8
         qs.qs_sample(h, m, 1000 + seed, out=samples)                                 # a9
@@ -205,9 +212,11 @@ def run_ours(args, rank, world, local):
             apply_ms.append((e0, e1))
             timed_gates.append(gates)
         results["last"] = dict(entropy=st["entropy"], norm=st["norm"], delta_h=dh, ce=ce)
+        return nxt
 
+    gates_next = prepare(0)
     for i in range(args.warmup):
-        step(i, False)
+        gates_next = step(i, False, gates_next)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -217,7 +226,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     t_start.record(stream)
     for i in range(args.steps):
-        step(args.warmup + i, True)
+        gates_next = step(args.warmup + i, True, gates_next)
     t_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()

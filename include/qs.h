@@ -156,11 +156,15 @@ qs_status qs_state_reset(qs_state *s);
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
                            const qs_opts *opts);
 
-/* Plans `gates` for this state and uploads the plan to the device without
- * launching anything (synchronous).  A following qs_apply_circuit with the
- * same gate list and options reuses the plan, so its call only launches
- * kernels.  Validation as for qs_apply_circuit; QS_MODE_PLAIN needs no plan
- * and returns QS_OK. */
+/* Plans `gates` for this state on the host and enqueues the plan upload on
+ * the state's stream without launching any kernel.  A following
+ * qs_apply_circuit with the same gate list and options reuses the plan, so
+ * its call only launches kernels.  The state keeps two plans: preparing the
+ * next circuit while the device still evolves the state with the other plan
+ * does not wait for the device (the host blocks only when the slot it
+ * replaces is still in use by earlier enqueued work).  `gates` may be
+ * released on return.  Validation as for qs_apply_circuit; QS_MODE_PLAIN
+ * needs no plan and returns QS_OK. */
 qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
                              const qs_opts *opts);
 

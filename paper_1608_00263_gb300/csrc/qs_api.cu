@@ -22,6 +22,18 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device-side address of page-locked host memory (cudaHostAlloc /
+// cudaHostRegister: mapped into the device's address space), else nullptr.
+void *pinned_device_view(void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 qs_status check_state(const qs_state *s)
 {
     if (!s) return set_error(QS_ERR_INVALID_ARG, "state is NULL");
@@ -88,7 +100,11 @@ void free_state(qs_state *s)
     if (s->owns && s->amps) cudaFree(s->amps);
     if (s->ws_f64) cudaFree(s->ws_f64);
     if (s->ws_u64) cudaFree(s->ws_u64);
-    if (s->plan_cache.dev) cudaFree(s->plan_cache.dev);
+    for (DevicePlanSlot &c : s->plan_cache.slot) {
+        if (c.dev) cudaFree(c.dev);
+        if (c.staging) cudaFreeHost(c.staging);
+        if (c.done) cudaEventDestroy(c.done);
+    }
     delete s;
 }
 
@@ -164,13 +180,20 @@ extern "C" qs_status qs_state_reset(qs_state *s)
 }
 
 static qs_status get_plan(qs_state *s, const qs_gate *gates, size_t ng, const qs_opts *o,
-                          const Plan **plan, const void **dev)
+                          const Plan **plan, const void **dev, DevicePlanSlot **slot_out = nullptr)
 {
     PlanParams pp = default_plan_params(s->n, s->dt, o);
     uint64_t key = fnv1a(gates, ng * sizeof(qs_gate));
     key = fnv1a(&pp, sizeof pp, key);
-    DevicePlanCache &c = s->plan_cache;
-    if (!(c.dev && c.key == key && c.ngates == ng)) {
+    DevicePlanCache &pc = s->plan_cache;
+    DevicePlanSlot *c = nullptr;
+    for (DevicePlanSlot &x : pc.slot)
+        if (x.valid && x.key == key && x.ngates == ng) c = &x;
+    if (!c) {
+        // least recently used slot; wait until the device is done with it
+        c = pc.slot[0].last_use <= pc.slot[1].last_use ? &pc.slot[0] : &pc.slot[1];
+        if (c->done) QS_CUDA_TRY(cudaEventSynchronize(c->done));
+        c->valid = false;
         Plan p;
         if (qs_status st = build_plan(pp, gates, ng, &p)) return st;
         const size_t b_pass = p.passes.size() * sizeof(DevPass);
@@ -178,34 +201,48 @@ static qs_status get_plan(qs_state *s, const qs_gate *gates, size_t ng, const qs
         const size_t b_ops = p.ops.size() * sizeof(DevOp);
         const size_t b_blk = p.tc_words.size() * sizeof(uint32_t);
         const size_t total = b_pass + b_phase + b_ops + b_blk + 16;
-        std::vector<unsigned char> host(total, 0);
-        std::memcpy(host.data(), p.passes.data(), b_pass);
-        std::memcpy(host.data() + b_pass, p.phases.data(), b_phase);
-        std::memcpy(host.data() + b_pass + b_phase, p.ops.data(), b_ops);
-        if (b_blk) std::memcpy(host.data() + b_pass + b_phase + b_ops, p.tc_words.data(), b_blk);
-        if (c.dev && c.dev_bytes < total) {
-            QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
-            cudaFree(c.dev);
-            c.dev = nullptr;
-        }
-        if (!c.dev) {
-            cudaError_t e = cudaMalloc(&c.dev, total);
+        if (c->bytes < total) {
+            if (c->dev) cudaFree(c->dev);
+            if (c->staging) cudaFreeHost(c->staging);
+            c->dev = c->staging = nullptr;
+            c->bytes = 0;
+            const size_t cap = total + total / 2;
+            cudaError_t e = cudaMalloc(&c->dev, cap);
+            if (e == cudaSuccess) e = cudaMallocHost(&c->staging, cap);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                c.dev = nullptr;
+                if (c->dev) cudaFree(c->dev);
+                c->dev = nullptr;
+                c->staging = nullptr;
                 return set_error(QS_ERR_OOM, "plan upload: %s", cudaGetErrorString(e));
             }
-            c.dev_bytes = total;
+            c->bytes = cap;
         }
-        // synchronous copy: the previous plan may still be in use on the stream
-        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
-        QS_CUDA_TRY(cudaMemcpy(c.dev, host.data(), total, cudaMemcpyHostToDevice));
-        c.key = key;
-        c.ngates = ng;
-        c.plan = std::move(p);
+        unsigned char *h = static_cast<unsigned char *>(c->staging);
+        std::memset(h, 0, total);
+        std::memcpy(h, p.passes.data(), b_pass);
+        std::memcpy(h + b_pass, p.phases.data(), b_phase);
+        std::memcpy(h + b_pass + b_phase, p.ops.data(), b_ops);
+        if (b_blk) std::memcpy(h + b_pass + b_phase + b_ops, p.tc_words.data(), b_blk);
+        QS_CUDA_TRY(cudaMemcpyAsync(c->dev, h, total, cudaMemcpyHostToDevice, s->stream));
+        if (!c->done) QS_CUDA_TRY(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+        QS_CUDA_TRY(cudaEventRecord(c->done, s->stream));
+        c->key = key;
+        c->ngates = ng;
+        c->plan = std::move(p);
+        c->valid = true;
     }
-    *plan = &c.plan;
-    *dev = c.dev;
+    c->last_use = ++pc.clock;
+    *plan = &c->plan;
+    *dev = c->dev;
+    if (slot_out) *slot_out = c;
+    return QS_OK;
+}
+
+// Marks the slot busy until the work just enqueued on the stream completes.
+static qs_status slot_in_use(qs_state *s, DevicePlanSlot *c)
+{
+    QS_CUDA_TRY(cudaEventRecord(c->done, s->stream));
     return QS_OK;
 }
 
@@ -230,16 +267,20 @@ extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t 
             return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside %d..%d", opts->tile_log2, rb, rb + 8);
         const Plan *plan;
         const void *dev;
-        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev)) return st;
-        return run_fused_plan(s, *plan, dev);
+        DevicePlanSlot *slot;
+        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
+        if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
+        return slot_in_use(s, slot);
     }
     if (mode == QS_MODE_FUSED_TC) {
         if (opts && opts->precision != QS_PREC_DEFAULT && opts->precision != QS_PREC_FP16X3)
             return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
         const Plan *plan;
         const void *dev;
-        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev)) return st;
-        return run_fused_plan(s, *plan, dev);
+        DevicePlanSlot *slot;
+        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
+        if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
+        return slot_in_use(s, slot);
     }
     return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
 }
@@ -270,7 +311,13 @@ extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_f
     const uint64_t N = 1ULL << s->n;
     const size_t esz = out_is_fp64 ? 8 : 4;
     if (is_device_ptr(out)) return launch_probabilities(s, out, out_is_fp64, 0, N);
-    // host output: convert in device chunks and copy back
+    if (void *view = pinned_device_view(out)) {
+        // page-locked host output: the kernel writes it directly (one pass)
+        if (qs_status st = launch_probabilities(s, view, out_is_fp64, 0, N)) return st;
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        return QS_OK;
+    }
+    // pageable host output: convert in device chunks and copy back
     const uint64_t chunk = N < (1ULL << 24) ? N : (1ULL << 24);
     void *buf = nullptr;
     QS_CUDA_TRY(cudaMallocAsync(&buf, chunk * esz, s->stream));

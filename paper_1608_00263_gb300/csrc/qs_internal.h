@@ -15,6 +15,8 @@
 #else
 struct CUstream_st;
 typedef CUstream_st *cudaStream_t;
+struct CUevent_st;
+typedef CUevent_st *cudaEvent_t;
 #endif
 
 namespace qs {
@@ -139,12 +141,24 @@ double plan_bytes(const Plan &p, qs_dtype dt);
 // ---------------------------------------------------------------------------
 // State handle
 // ---------------------------------------------------------------------------
-struct DevicePlanCache {
+// Two plan slots per state: a plan can be built and uploaded (stream-ordered,
+// from pinned memory) while the device still runs the other slot's plan, so
+// host planning of the next circuit overlaps the current evolution.
+struct DevicePlanSlot {
+    bool valid = false;
     uint64_t key = 0;          // hash of (gates, options)
     size_t ngates = 0;
     void *dev = nullptr;       // passes | phases | ops | blocks on device
-    size_t dev_bytes = 0;
+    void *staging = nullptr;   // pinned host source of the upload
+    size_t bytes = 0;          // capacity of dev and staging
+    cudaEvent_t done = nullptr;   // after the slot's last upload or apply
+    uint64_t last_use = 0;
     Plan plan;
+};
+
+struct DevicePlanCache {
+    DevicePlanSlot slot[2];
+    uint64_t clock = 0;
 };
 
 }  // namespace qs

@@ -176,6 +176,13 @@ def test_probabilities(state20):
     host32 = np.empty(1 << 20, dtype=np.float32)
     qs.qs_probabilities(h, host32, fp64=False)
     assert np.sum(np.abs(host32 - p)) < 1e-5
+    # page-locked host output is written by the kernel directly
+    pinned = torch.full((1 << 20,), -1.0, dtype=torch.float64).pin_memory()
+    qs.qs_probabilities(h, pinned, fp64=True)
+    assert np.array_equal(pinned.numpy(), pd)
+    pinned32 = torch.full((1 << 20,), -1.0, dtype=torch.float32).pin_memory()
+    qs.qs_probabilities(h, pinned32, fp64=False)
+    assert np.array_equal(pinned32.numpy(), host32)
 
 
 def test_pt_moments(state20):
