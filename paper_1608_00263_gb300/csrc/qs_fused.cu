@@ -242,9 +242,10 @@ struct SlotIO {
 // Executes one staged op on the register slots.  `sel` is the part of a
 // diagonal op's selection outside the register set (true when the op has
 // none); diagonal ops apply branch-free with sign / identity when unmet.
-// FULL = false leaves out the cases of the parameterised gates (shears and
-// general phases on register bits), which the Clifford+T circuits never
-// stage; the smaller interpreter costs less instruction fetch per op.
+// FULL = false leaves out the cases of the parameterised gates (shears,
+// general phases and T-valued phases on two register bits), which the
+// Clifford+T circuits never stage; the smaller interpreter costs less
+// instruction fetch per op.
 template <int RB, bool FULL, typename V, typename R>
 __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, uint64_t qmask, R &fr,
                                         R &fi, const R *phase)
@@ -267,7 +268,7 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, ui
     QS_B(0) QS_B(1) QS_B(2) QS_B(3)
 #undef QS_B
 #define QS_M(M)                                                                  \
-    case K_T + M: reg_phase<NS, M>(a, c, c, true); break;                        \
+    case K_T + M: if (FULL || !((M) & ((M) - 1))) reg_phase<NS, M>(a, c, c, true); break; \
     case K_NEG + M: reg_sign<NS, M>(a, QS_SGN); break;                           \
     case K_PH + M: if (FULL) reg_phase<NS, M>(a, QS_PR, QS_PI, false); break;
     // one- and two-qubit gates select at most two register bits
@@ -280,7 +281,7 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, ui
     case K_SHX + J: if (FULL) reg_shear<NS, (J < RB ? J : 0), 0>(a, phase[0]); break;      \
     case K_SHY + J: if (FULL) reg_shear<NS, (J < RB ? J : 0), 1>(a, phase[0]); break;
 #define QS_M4(M)                                                                 \
-    case K_T + M: reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break;         \
+    case K_T + M: if (FULL || !((M) & ((M) - 1))) reg_phase<NS, ((M) & (NS - 1))>(a, c, c, true); break; \
     case K_NEG + M: reg_sign<NS, ((M) & (NS - 1))>(a, QS_SGN); break;            \
     case K_PH + M: if (FULL) reg_phase<NS, ((M) & (NS - 1))>(a, QS_PR, QS_PI, false); break;
     QS_B4(4) QS_M4(16) QS_M4(17) QS_M4(18) QS_M4(20) QS_M4(24)
@@ -331,7 +332,7 @@ struct SPhase {
     uint32_t pb[kMaxRegBits];   // swizzled tile byte offset of each register bit
     int32_t op_begin, op_end;
     int32_t paired;             // register bit 0 is tile bit 0 (16-byte slots)
-    int32_t uniform_ops;        // phase has thread-uniform diagonal ops
+    int32_t uniform_begin;      // first op of the thread-uniform diagonal tail
     int32_t kind;               // 0 register phase, 1 tensor-core block phase
     int32_t slot;               // kind 1: slot of the block in tensor memory
     int32_t scale_exp;          // kind 1: FP16 operand scale 2^scale_exp
@@ -613,10 +614,12 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             S.ph[ph].kind = D.kind;
             // keep scaled values below 2^14 whatever the deferred factors
             S.ph[ph].scale_exp = 14 - (D.defer_before + 1) / 2;
-            int u = 0;
-            for (int o = D.op_begin; o < D.op_end; ++o)
-                u |= (ops_g[o].type == OP_PHASE || ops_g[o].type == OP_NEG) && ops_g[o].rmask == 0;
-            S.ph[ph].uniform_ops = u;
+            // the planner puts the thread-uniform diagonal ops last
+            int ub = D.op_end;
+            while (ub > D.op_begin && (ops_g[ub - 1].type == OP_PHASE || ops_g[ub - 1].type == OP_NEG) &&
+                   ops_g[ub - 1].rmask == 0)
+                --ub;
+            S.ph[ph].uniform_begin = ub - phases_g[S.P.phase_begin].op_begin;
         }
         uint32_t e = 0;
         uint64_t q = 0;
@@ -758,11 +761,23 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             else
                 SlotIO<NS, 0>::template load<V>(a, reinterpret_cast<const char *>(smem_raw), T.phys, pb);
             R fr = (R)1, fi = (R)0;             // thread-uniform pending factor
-            const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end;
-            const bool fpend = S.ph[ph].uniform_ops != 0;
-            for (int o = ob; o < oe; ++o) {
+            const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end, ub = S.ph[ph].uniform_begin;
+            const bool fpend = ub < oe;
+            for (int o = ob; o < ub; ++o) {
                 const SOp<R> op = S.ops[o];
                 exec_op<RB, FULL>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
+            }
+            // tail: diagonal ops selected outside the register set multiply
+            // the thread's pending factor (no interpreter dispatch)
+            for (int o = ub; o < oe; ++o) {
+                const SOp<R> op = S.ops[o];
+                if ((idx_th & op.qmask) == op.qmask) {
+                    const bool neg = (op.code & ~K_COND) == K_UNEG;
+                    const R pr = neg ? (R)-1 : S.phase[op.aux][0], pi = neg ? (R)0 : S.phase[op.aux][1];
+                    const R x = fr * pr - fi * pi;
+                    fi = fr * pi + fi * pr;
+                    fr = x;
+                }
             }
             bool fmul = fpend;
             if (gs_in_phase && ph == nph - 1) {
@@ -838,9 +853,10 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
                                      smem_raw);
 }
 
-// True when pass `hp` stages a shear or a general phase on register bits
-// (the interpreter cases that only the FULL kernel carries).  Mirrors the
-// device staging: a phase op with m0 = m1 = 1/sqrt2 is staged as a T phase.
+// True when pass `hp` stages a shear, a general phase on register bits or a
+// T-valued phase on two register bits (the interpreter cases that only the
+// FULL kernel carries).  Mirrors the device staging: a phase op with m0 = m1
+// = 1/sqrt2 is staged as a T phase.
 static bool pass_needs_full(const Plan &plan, const DevPass &hp)
 {
     const int o0 = plan.phases[hp.phase_begin].op_begin;
@@ -850,7 +866,7 @@ static bool pass_needs_full(const Plan &plan, const DevPass &hp)
         if (d.type == OP_SHX || d.type == OP_SHY) return true;
         if (d.type == OP_PHASE && d.rmask) {
             const bool tphase = d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
-            if (!tphase) return true;
+            if (!tphase || (d.rmask & (d.rmask - 1))) return true;
         }
     }
     return false;

@@ -876,6 +876,12 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
                 pdone[gi] = 1;
                 --prem;
             }
+            // diagonal ops whose selection lies wholly outside the register
+            // set only scale a thread's slots by a constant: they commute
+            // with every other op of the phase and go to its end
+            std::stable_partition(P.ops.begin() + ph.op_begin, P.ops.end(), [](const DevOp &o) {
+                return !((o.type == OP_PHASE || o.type == OP_NEG) && o.rmask == 0);
+            });
             ph.op_end = (int)P.ops.size();
             P.phases.push_back(ph);
             ++dp.nphases;

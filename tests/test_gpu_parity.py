@@ -106,6 +106,24 @@ def test_grid_4x5_depth25(dtype, mode, seed):
     assert rel_l2(psi, ref) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_fused_t_valued_phases(dtype):
+    """Phases equal to the T phase e^{i pi/4} on one or two qubits (RZ(pi/4),
+    CPHASE(pi/4)) next to H, T and CZ: the staged T form on one register bit
+    and the general form on two."""
+    n = 12
+    rng = np.random.default_rng(3)
+    g = np.zeros(400, dtype=qs.GATE_DTYPE)
+    for i in range(400):
+        k = [qs.QS_H, qs.QS_T, qs.QS_CZ, qs.QS_RZ, qs.QS_CPHASE, qs.QS_X_HALF][i % 6]
+        g[i]["kind"] = k
+        a, b = rng.choice(n, size=2, replace=False)
+        g[i]["q0"], g[i]["q1"] = a, b
+        g[i]["theta"] = math.pi / 4
+    ref = O.simulate(n, g)
+    assert rel_l2(gpu_run(n, g, dtype), ref) < TOL[dtype]
+
+
 def test_grid_4x6_depth30_c64():
     g = qs.qs_circuit_generate(4, 6, 30, 5)
     ref = O.simulate(24, g)
