@@ -302,7 +302,7 @@ def run_ours(args, rank, world, local):
         n34 = forms_34(qs, torch, hbm_peak)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
 
-    ens = noisy = single = None
+    ens = noisy = single = small = grad = None
     if rank == 0 and not args.no_compare and args.workload == DEFAULT_WORKLOAD:
         if h is not None:
             qs.qs_state_destroy(h)
@@ -311,6 +311,8 @@ def run_ours(args, rank, world, local):
         ens = ensemble_4096(qs, torch, hbm_peak)
         noisy = noisy_trajectories(qs, torch)
         single = single_error_sweep(qs, torch)
+        small = grid20_forms(qs, torch)
+        grad = adjoint_24(qs, torch)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
 
     cpu = None
@@ -353,6 +355,8 @@ def run_ours(args, rank, world, local):
         "ensemble": ens,
         "noisy": noisy,
         "single_error": single,
+        "grid4x5_n20_d25": small,
+        "adjoint": grad,
     }
     if cpu:
         out["cpu_baseline"] = cpu
@@ -475,6 +479,71 @@ def noisy_trajectories(qs, torch, T=4096, r=0.005):
     return {"trajectories": T, "qubits": n, "depth": depth, "r": r, "host_generate_s": round(gen_s, 3),
             "gpu_run_s": round(run_s, 3), "trajectories_per_s": round(T / run_s, 1),
             "delta_h": round(dh, 4), "eq6_alpha": round(alpha, 4)}
+
+
+def grid20_forms(qs, torch):
+    """4 x 5 grid, 20 qubits, depth 25, seeds 0..9 (the paper averages 10
+    instances): apply-only cycles/s of the fused form for complex64 and
+    complex128 (the 8.4 / 16.8 MB states are L2-resident), and the sample
+    cross entropy of 1e5 samples (sampler seed 1000 + circuit seed)."""
+    n, depth = 20, 25
+    out = {}
+    for name, dt in (("c64", qs.QS_C64), ("c128", qs.QS_C128)):
+        h = qs.qs_state_create(n, dt)
+        try:
+            ms_tot, dh_tot = 0.0, 0.0
+            for seed in range(10):
+                g = qs.qs_circuit_generate(4, 5, depth, seed)
+                qs.qs_state_reset(h)
+                qs.qs_prepare_circuit(h, g)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                qs.qs_apply_circuit(h, g)
+                b.record()
+                torch.cuda.synchronize()
+                ms_tot += a.elapsed_time(b)
+                x = qs.qs_sample(h, 100000, 1000 + seed)
+                dh_tot += qs.qs_cross_entropy(h, x)[1]
+            out[name] = {"apply_ms_mean": round(ms_tot / 10, 4), "cycles_per_s": round(10 * depth / (ms_tot / 1e3), 1),
+                         "delta_h_mean": round(dh_tot / 10, 4)}
+        finally:
+            qs.qs_state_destroy(h)
+    return out
+
+
+def adjoint_24(qs, torch):
+    """Gradient configuration: 4 x 6 grid, 24 qubits, depth 30, every
+    single-qubit gate and CZ parameterised (R_X / R_Y / R_Z, CPHASE), loss
+    over 1e5 samples of the nominal circuit: time of one adjoint gradient
+    (forward evolution + reverse sweep over all gates)."""
+    import numpy as np
+    g = qs.qs_circuit_generate(4, 6, 30, 0)
+    nom = g.copy()
+    for x in nom:
+        k = int(x["kind"])
+        if k == qs.QS_X_HALF:
+            x["kind"], x["theta"] = qs.QS_RX, math.pi / 2
+        elif k == qs.QS_Y_HALF:
+            x["kind"], x["theta"] = qs.QS_RY, math.pi / 2
+        elif k == qs.QS_T:
+            x["kind"], x["theta"] = qs.QS_RZ, math.pi / 4
+        elif k == qs.QS_CZ:
+            x["kind"], x["theta"] = qs.QS_CPHASE, math.pi
+    nparam = int(np.sum(nom["kind"] != qs.QS_H))
+    h = qs.qs_state_create(24, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(h, nom)
+        x = qs.qs_sample(h, 100000, 8)
+        qs.qs_adjoint_gradient(h, nom, x)            # warm-up (plans, workspace)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, grad = qs.qs_adjoint_gradient(h, nom, x)
+        dt = time.perf_counter() - t0
+    finally:
+        qs.qs_state_destroy(h)
+    return {"qubits": 24, "depth": 30, "gates": int(nom.size), "parameters": nparam,
+            "samples": 100000, "gradient_ms": round(dt * 1e3, 2), "loss": round(loss, 6)}
 
 
 def single_error_sweep(qs, torch):

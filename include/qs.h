@@ -371,6 +371,10 @@ qs_status qs_batch_mean_probabilities(qs_batch *b, double *out);
 qs_status qs_noisy_circuit(const qs_gate *gates, size_t ngates, int n, double r1, double r2,
                            double r_init, uint64_t seed, qs_gate *out, size_t *nout);
 
+/* qs_batch_run without statistics: resets every state and applies instance
+ * i's gates (same arguments and rules, kmax = 0). */
+qs_status qs_batch_apply(qs_batch *b, const qs_gate *gates, const uint64_t *offsets);
+
 /* Device pointer of instance i's amplitudes (canonical order). */
 qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps);
 

@@ -27,7 +27,7 @@ __all__ = [
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
-    "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit",
+    "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit", "qs_batch_apply",
     "library_path",
 ]
 
@@ -307,6 +307,15 @@ def qs_batch_run(b, gate_lists, kmax=10):
     N.check(N.lib().qs_batch_run(b, gates.ctypes.data if gates.size else None, offsets.ctypes.data, kmax,
                                  out.ctypes.data))
     return out
+
+
+def qs_batch_apply(b, gate_lists):
+    """Resets every instance and applies its gate list (no statistics)."""
+    gl = [_gates(g) for g in gate_lists]
+    offsets = np.zeros(len(gl) + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum([g.size for g in gl])
+    gates = np.ascontiguousarray(np.concatenate(gl) if gl else np.zeros(0, dtype=GATE_DTYPE), dtype=GATE_DTYPE)
+    N.check(N.lib().qs_batch_apply(b, gates.ctypes.data if gates.size else None, offsets.ctypes.data))
 
 
 def qs_batch_state(b, i):

@@ -51,6 +51,7 @@ PD = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "qs_version": (ctypes.c_char_p, []),
     "qs_batch_correlation": (ctypes.c_int, [P, P, P]),
+    "qs_batch_apply": (ctypes.c_int, [P, P, P]),
     "qs_single_error_circuit": (ctypes.c_int, [P, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
                                                ctypes.c_int, P, ctypes.POINTER(ctypes.c_size_t)]),
     "qs_batch_mean_probabilities": (ctypes.c_int, [P, P]),

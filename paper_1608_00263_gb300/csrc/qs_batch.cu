@@ -355,3 +355,8 @@ extern "C" qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint6
         }
     return QS_OK;
 }
+
+extern "C" qs_status qs_batch_apply(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)
+{
+    return qs_batch_run(b, gates, offsets, 0, nullptr);
+}

@@ -54,7 +54,7 @@ def test_trajectories_and_batch_samples_match_oracle():
     assert sum(len(h) > len(g) for h in lists) > T // 2      # most trajectories have errors
     b = qs.qs_batch_create([n] * T)
     try:
-        qs.qs_batch_run(b, lists, kmax=0)
+        qs.qs_batch_apply(b, lists)
         got = qs.qs_batch_sample(b, k, seed, r_mes)
         assert got.shape == (T, k)
         mism = 0
@@ -111,7 +111,7 @@ def test_noisy_cross_entropy_tracks_eq6(r):
     b = qs.qs_batch_create([n] * T)
     h = qs.qs_state_create(n, qs.QS_C64)
     try:
-        qs.qs_batch_run(b, lists, kmax=0)
+        qs.qs_batch_apply(b, lists)
         x = qs.qs_batch_sample(b, 1, 123, rm).reshape(-1)
         qs.qs_apply_circuit(h, g)
         ce, dh = qs.qs_cross_entropy(h, x)
