@@ -55,9 +55,7 @@ enum : uint32_t {
 template <int CE>
 __host__ __device__ __forceinline__ uint32_t swz(uint32_t e)
 {
-    uint32_t u = e / CE;
-    uint32_t f = ((u >> 3) ^ (u >> 6) ^ (u >> 9) ^ (u >> 12)) & 7u;
-    return e ^ (f * CE);
+    return tile_swizzle(e, CE);
 }
 
 // ---- register-bit operations (J = register bit, compile time) -------------
@@ -604,8 +602,6 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     // ---- stage phases, ops and per-thread phase tables (once per CTA) ----
     for (int ph = 0; ph < nph; ++ph) {
         const DevPhase &D = phases_g[S.P.phase_begin + ph];
-        uint32_t regmask = 0;
-        for (int j = 0; j < RB; ++j) regmask |= 1u << D.R[j];
         if (tid == 0) {
             for (int j = 0; j < RB; ++j) S.ph[ph].pb[j] = swz<CE>(1u << D.R[j]) * (uint32_t)sizeof(V);
             S.ph[ph].op_begin = D.op_begin - phases_g[S.P.phase_begin].op_begin;
@@ -621,14 +617,17 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                 --ub;
             S.ph[ph].uniform_begin = ub - phases_g[S.P.phase_begin].op_begin;
         }
+        // thread-index bit k sits on tile bit T[k] (the planner picks the
+        // lane bits that spread the phase's accesses over the banks)
         uint32_t e = 0;
         uint64_t q = 0;
-        for (int b = 0, k = 0; b < t; ++b) {
-            if ((regmask >> b) & 1u) continue;
-            const uint32_t bit = (tid >> k) & 1u;
-            e |= bit << b;
-            q |= (uint64_t)bit << S.P.L[b];
-            ++k;
+        if (D.kind == 0) {
+            for (int k = 0; k < t - RB; ++k) {
+                const int b = D.T[k];
+                const uint32_t bit = (tid >> k) & 1u;
+                e |= bit << b;
+                q |= (uint64_t)bit << S.P.L[b];
+            }
         }
         S.th[ph][tid].phys = swz<CE>(e) * (uint32_t)sizeof(V);
         S.th[ph][tid].qoff = q;

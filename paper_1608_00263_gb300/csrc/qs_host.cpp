@@ -511,6 +511,63 @@ static uint64_t choose_tile(const std::vector<PGate> &g, const std::vector<int> 
     return choose_local(g, cand, done, n, local, pool, want - added, allq);
 }
 
+// Shared-memory wavefronts of one phase's slot loads (the stores mirror
+// them) for a choice of lane bits: a wavefront serves one 4-byte word per
+// bank, so an access of the 32 lanes costs the largest number of distinct
+// words in one bank.  The swizzle is linear, so another slot's addresses are
+// this slot's XOR a constant, which permutes the banks: every slot costs the
+// same and slot 0 is evaluated (complex64 slots pair into 16-byte accesses
+// when register bit 0 is tile bit 0).
+static int phase_wavefronts(const uint8_t *R, int r, const int *lane, int nl, int esz)
+{
+    const uint32_t CE = 16 / esz;
+    const bool paired = esz == 8 && R[0] == 0;
+    const int per = (paired ? 16 : esz) / 4;   // 4-byte words per lane access
+    uint32_t w[32 * 4];
+    int nw = 0;
+    for (int l = 0; l < (1 << nl); ++l) {
+        uint32_t e = 0;
+        for (int k = 0; k < nl; ++k) e |= (uint32_t)((l >> k) & 1) << lane[k];
+        const uint32_t w0 = tile_swizzle(e, CE) * (uint32_t)esz / 4;
+        for (int i = 0; i < per; ++i) w[nw++] = w0 + (uint32_t)i;
+    }
+    std::sort(w, w + nw);
+    nw = (int)(std::unique(w, w + nw) - w);
+    int cnt[32] = {0}, worst = 0;
+    for (int i = 0; i < nw; ++i) worst = std::max(worst, ++cnt[w[i] & 31]);
+    return worst * ((1 << r) >> (paired ? 1 : 0));
+}
+
+// Thread-bit order of a register phase: the non-register tile bits, with the
+// five lane bits (or all of them, if fewer) chosen to minimise the phase's
+// shared-memory wavefronts; ties keep the lowest bits.
+static void choose_thread_bits(const uint8_t *R, int r, int t, int esz, uint8_t *T)
+{
+    int tb[kMaxTileBits], nt = 0;
+    for (int b = 0; b < t; ++b) {
+        bool reg = false;
+        for (int j = 0; j < r; ++j) reg |= R[j] == b;
+        if (!reg) tb[nt++] = b;
+    }
+    const int nl = std::min(5, nt);
+    int best_mask = (1 << nl) - 1, best = 1 << 30;
+    if (nt > nl) {
+        for (int m = 0; m < (1 << nt); ++m) {
+            if (__builtin_popcount(m) != nl) continue;
+            int lane[5], k = 0;
+            for (int i = 0; i < nt; ++i)
+                if ((m >> i) & 1) lane[k++] = tb[i];
+            const int c = phase_wavefronts(R, r, lane, nl, esz);
+            if (c < best || (c == best && m < best_mask)) { best = c; best_mask = m; }
+        }
+    }
+    int k = 0;
+    for (int i = 0; i < nt; ++i)
+        if ((best_mask >> i) & 1) T[k++] = (uint8_t)tb[i];
+    for (int i = 0; i < nt; ++i)
+        if (!((best_mask >> i) & 1)) T[k++] = (uint8_t)tb[i];
+}
+
 static int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 
 // A tensor-core block phase is chosen when it absorbs at least this many
@@ -678,6 +735,7 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t);
     pp.k = kTcBits;
     pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
+    pp.esz = dt == QS_C128 ? 16 : 8;
     pp.r = std::min(pp.r, pp.t);
     return pp;
 }
@@ -805,6 +863,7 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
                 if (!used) ph.R[j++] = (uint8_t)b;
             }
             std::sort(ph.R, ph.R + dp.r);
+            choose_thread_bits(ph.R, dp.r, dp.t, pp.esz, ph.T);
             for (int q = 0; q < n; ++q) reg_bit_of[q] = -1;
             for (int i2 = 0; i2 < dp.r; ++i2) reg_bit_of[dp.L[ph.R[i2]]] = i2;
             ph.op_begin = (int)P.ops.size();

@@ -78,8 +78,10 @@ constexpr int kMaxRegBits = 8;
 constexpr int kMaxPhasesPerPass = 8;    // per-thread phase tables live in shared memory
 constexpr int kMaxOpsPerPass = 256;     // op descriptors live in shared memory
 
-struct DevPhase {       // 32 bytes
+struct DevPhase {       // 40 bytes
     uint8_t R[kMaxRegBits];  // tile bit of each register (or block) bit
+    uint8_t T[8];            // register phases: tile bit of thread-index bit k
+                             // (bits 0..4 are the lane bits of a warp)
     int32_t op_begin, op_end;
     int32_t kind;            // 0: register phase, 1: tensor-core block phase
     int32_t tc_block;        // kind 1: index of the block matrix
@@ -130,7 +132,24 @@ struct PlanParams {
     int mode;        // QS_MODE_FUSED or QS_MODE_FUSED_TC
     int k;           // TC block bits
     int tc_ok;       // tensor-core phases allowed (complex64, 13-bit tiles)
+    int esz = 8;     // bytes per amplitude (8 complex64, 16 complex128)
 };
+
+// XOR swizzle of the shared-memory tile (element e -> element index): the
+// element's 16-byte unit u = e / CE (CE elements per unit) has bits 0..2
+// XORed with a fold of its higher bits.  Linear over GF(2).  Shared by the
+// kernels and the planner's bank-conflict model.
+#ifdef __CUDACC__
+#define QS_HD __host__ __device__
+#else
+#define QS_HD
+#endif
+QS_HD inline uint32_t tile_swizzle(uint32_t e, uint32_t CE)
+{
+    const uint32_t u = e / CE;
+    const uint32_t f = ((u >> 3) ^ (u >> 6) ^ (u >> 9) ^ (u >> 12)) & 7u;
+    return e ^ (f * CE);
+}
 
 qs_status build_plan(const PlanParams &pp, const qs_gate *g, size_t ng, Plan *out);
 uint16_t f64_to_f16_bits(double x);
