@@ -468,21 +468,19 @@ static uint64_t choose_local(const std::vector<PGate> &g, const std::vector<int>
     return local;
 }
 
-// Tile choice of a pass with a short lookahead: for the first kLookSteps
-// additions, the kLookTop candidates with the most applicable gates are
+// Tile choice of a pass with a lookahead: for the first `look_steps`
+// additions, the `look_top` candidates with the most applicable gates are
 // each completed greedily to the full tile and scored by the gates the
 // completed tile applies; the remaining additions are greedy.  Fewer passes
-// than the plain greedy choice on the paper's circuits (about 4 % at 30
-// qubits, 8 % at 34), at a few milliseconds of host time.
-constexpr int kLookSteps = 2;
-constexpr int kLookTop = 6;
-
+// than the plain greedy choice on the paper's circuits: 4 % at 30 qubits
+// (2 steps, 6 candidates, a few milliseconds), 14 % at 34 qubits (every
+// step and candidate, ~0.2 s of host time against ~2 s of evolution).
 static uint64_t choose_tile(const std::vector<PGate> &g, const std::vector<int> &cand,
                             const std::vector<char> &done, int n, uint64_t base, uint64_t pool,
-                            int want, uint64_t allq)
+                            int want, uint64_t allq, int look_steps, int look_top)
 {
     uint64_t local = base;
-    for (int step = 0; step < want && step < kLookSteps; ++step) {
+    for (int step = 0; step < want && step < look_steps; ++step) {
         std::vector<int> first;
         first_pending(g, cand, done, n, &first);
         struct C { int cnt, first, q; };
@@ -497,7 +495,7 @@ static uint64_t choose_tile(const std::vector<PGate> &g, const std::vector<int> 
         std::sort(cs.begin(), cs.end(), [](const C &a, const C &b) {
             return a.cnt != b.cnt ? a.cnt > b.cnt : (a.first != b.first ? a.first < b.first : a.q < b.q);
         });
-        if ((int)cs.size() > kLookTop) cs.resize(kLookTop);
+        if ((int)cs.size() > look_top) cs.resize(look_top);
         int best_q = -1, best = -1;
         for (const C &c : cs) {
             const uint64_t full = choose_local(g, cand, done, n, local | (1ULL << c.q), pool, want - step - 1, allq);
@@ -736,6 +734,8 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     pp.k = kTcBits;
     pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
     pp.esz = dt == QS_C128 ? 16 : 8;
+    // a deeper lookahead pays where a pass costs the most
+    if (n >= 32) pp.look_steps = pp.look_top = 64;
     pp.r = std::min(pp.r, pp.t);
     return pp;
 }
@@ -774,7 +774,8 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
     const uint64_t low = (pp.c >= 64) ? ~0ULL : ((1ULL << pp.c) - 1);
     std::vector<int> pass_gates, phase_gates;
     while (remaining) {
-        uint64_t local = choose_tile(g, all, done, n, low & allq, allq & ~low, pp.t - pp.c, allq);
+        uint64_t local = choose_tile(g, all, done, n, low & allq, allq & ~low, pp.t - pp.c, allq, pp.look_steps,
+                                     pp.look_top);
         int cnt;
         collect(g, all, done, local, &pass_gates, &cnt, allq);
         if (cnt == 0) return set_error(QS_ERR_INVALID_ARG, "planner made no progress");

@@ -133,6 +133,8 @@ struct PlanParams {
     int k;           // TC block bits
     int tc_ok;       // tensor-core phases allowed (complex64, 13-bit tiles)
     int esz = 8;     // bytes per amplitude (8 complex64, 16 complex128)
+    int look_steps = 2;   // tile choice: additions scored by greedy completion
+    int look_top = 6;     // ... among this many best-scoring candidates
 };
 
 // XOR swizzle of the shared-memory tile (element e -> element index): the
