@@ -378,8 +378,11 @@ struct FusedSmem {
 // tensor memory (loaded once per CTA), B in shared memory (canonical
 // K-major layout without swizzle: 8 x 16-byte core matrices, 128 bytes
 // apart along K, 2048 bytes apart along the 128 columns), D in tensor memory.
+// Each CTA holds 256 tensor-memory columns (D, one block) and B takes the
+// tile's own shared buffer, so two CTAs share an SM and one CTA's tile
+// traffic and MMA wait overlap the other's work.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kTmemCols = 512;              // D: 0..127, blocks: 128 + 128 s
+constexpr uint32_t kTmemCols = 256;              // D: 0..127, block: 128..255 (two CTAs per SM)
 constexpr int kTcWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -472,24 +475,36 @@ __device__ __forceinline__ void tc_teardown(TcSmem &TS)
     }
 }
 
-// One block phase on the shared tile (all 256 threads).
+// One block phase on the shared tile (all 256 threads).  The FP16 operands
+// take the tile's own buffer: every thread first moves its 32 amplitudes
+// (4 units of 8 block rows of one column) to registers, then writes their
+// hi / lo halves in the MMA layout; after the products complete, the
+// accumulator is scattered back into the tile.
 __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, float2 *tile,
-                                         unsigned char *bbuf, uint32_t parity, int *err_flag)
+                                         uint32_t parity, int *err_flag)
 {
     const float sc = ldexpf(1.f, scale_exp), inv_sc = ldexpf(1.f, -scale_exp);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char *bhi = bbuf, *blo = bbuf + 32768;
+    unsigned char *bhi = reinterpret_cast<unsigned char *>(tile), *blo = bhi + 32768;
     const uint32_t *blk = TS.blk_off[slot], *col = TS.col_off[slot];
-    // ---- tile (FP32) -> B hi / lo (FP16, canonical layout) ----
-#pragma unroll 1
+    float2 xv[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int u = tid + 256 * i;
+        const uint32_t base = col[u & 127] ^ blk[(u >> 7) * 8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[i][j] = tile[base ^ blk[j]];
+    }
+    __syncthreads();
+    // ---- registers (FP32) -> B hi / lo (FP16, canonical layout) ----
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int u = tid + 256 * i;
         const int nu = u & 127, bg = u >> 7;
-        const uint32_t base = col[nu] ^ blk[bg * 8];
         uint32_t hre[4], him[4], lre[4], lim[4];
 #pragma unroll
         for (int j = 0; j < 8; j += 2) {
-            float2 x0 = tile[base ^ blk[j]], x1 = tile[base ^ blk[j + 1]];
+            float2 x0 = xv[i][j], x1 = xv[i][j + 1];
             x0.x *= sc; x0.y *= sc; x1.x *= sc; x1.y *= sc;
             const __half2 hr = __floats2half2_rn(x0.x, x1.x);
             const __half2 hm = __floats2half2_rn(x0.y, x1.y);
@@ -713,9 +728,6 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     const bool prefetch_runs = (t - kRunBits) >= 0 && (1 << (t - kRunBits)) == nthr &&
                                S.P.L[kRunBits - 1] == kRunBits - 1;
     const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
-    // FP16 operand buffers after the tile, 1024-byte aligned in the shared window
-    unsigned char *tc_bbuf = smem_raw + (size_t(1) << t) * sizeof(V);
-    tc_bbuf += (1024u - (smem_addr(tc_bbuf) & 1023u)) & 1023u;
     for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
         if (TC && TS.abort) break;
         // out-of-tile and thread bits are disjoint from it_off: OR = add
@@ -741,7 +753,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         for (int ph = 0; ph < nph; ++ph) {
             if constexpr (TC) {
                 if (S.ph[ph].kind == 1) {
-                    tc_phase(TS, S.ph[ph].slot, S.ph[ph].scale_exp, tile, tc_bbuf, tc_parity, err_flag);
+                    tc_phase(TS, S.ph[ph].slot, S.ph[ph].scale_exp, tile, tc_parity, err_flag);
                     tc_parity ^= 1u;
                     if (TS.abort) break;
                     continue;
@@ -836,14 +848,18 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
 }
 
 template <typename R, int RB, bool TC, bool FULL>
-__global__ void __launch_bounds__(kThreadsMax, TC ? 1 : 2)
+__global__ void __launch_bounds__(kThreadsMax, 2)
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
              uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
     __shared__ FusedSmem<R, RB> S;
     __shared__ TcSmem TS;
+    // the tensor-core form starts the tile (its MMA operand buffer) on a
+    // 1024-byte boundary of the shared window; the launch adds the slack
+    unsigned char *smem_raw = smem_dyn;
+    if (TC) smem_raw += (1024u - (smem_addr(smem_dyn) & 1023u)) & 1023u;
     // contiguous range of tiles per CTA
     const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
     const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
@@ -923,9 +939,9 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                 if (!any_tc) QS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
                 any_tc = true;
                 auto kern = k_fused_pass<R, RB, true, true>;
-                const size_t smem = (size_t(1) << hp.t) * sizeof(V) + 65536 + 1024;
+                const size_t smem = (size_t(1) << hp.t) * sizeof(V) + 1024;
                 QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                const uint64_t cap = (uint64_t)s->num_sms;
+                const uint64_t cap = (uint64_t)s->num_sms * 2;
                 const int grid = (int)(ntiles < cap ? ntiles : cap);
                 kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, dwords,
                                                          err);

@@ -97,7 +97,7 @@ struct DevPhase {       // 40 bytes
 // elements (lower K in the low half): 128 rows x (64 hi words, 64 lo words).
 constexpr int kTcBits = 6;
 constexpr int kTcWordsPerBlock = 128 * 128;
-constexpr int kMaxTcPerPass = 3;        // TMEM: accumulator + 3 blocks (hi, lo)
+constexpr int kMaxTcPerPass = 1;        // TMEM per CTA: accumulator + 1 block (hi, lo); 2 CTAs per SM
 
 struct DevPass {
     int32_t t;              // tile bits
