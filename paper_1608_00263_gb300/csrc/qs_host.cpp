@@ -510,22 +510,21 @@ static uint64_t choose_tile(const std::vector<PGate> &g, const std::vector<int> 
 }
 
 // Shared-memory wavefronts of one phase's slot loads (the stores mirror
-// them) for a choice of lane bits: a wavefront serves one 4-byte word per
-// bank, so an access of the 32 lanes costs the largest number of distinct
-// words in one bank.  The swizzle is linear, so another slot's addresses are
-// this slot's XOR a constant, which permutes the banks: every slot costs the
-// same and slot 0 is evaluated (complex64 slots pair into 16-byte accesses
-// when register bit 0 is tile bit 0).
-static int phase_wavefronts(const uint8_t *R, int r, const int *lane, int nl, int esz)
+// them).  A warp's shared access is served per group of lanes -- 16 lanes
+// for 8-byte accesses, 8 for 16-byte ones -- and a group costs the largest
+// number of distinct 4-byte words that fall in one bank.  The group's lanes
+// differ in the `g` tile bits `grp`; the other lane bits and every register
+// slot only XOR a constant into the (linear) swizzled addresses, which
+// permutes the banks, so one group of slot 0 gives the cost of all.
+static int group_wavefronts(const int *grp, int g, int esz, bool paired)
 {
     const uint32_t CE = 16 / esz;
-    const bool paired = esz == 8 && R[0] == 0;
     const int per = (paired ? 16 : esz) / 4;   // 4-byte words per lane access
-    uint32_t w[32 * 4];
+    uint32_t w[16 * 4];
     int nw = 0;
-    for (int l = 0; l < (1 << nl); ++l) {
+    for (int l = 0; l < (1 << g); ++l) {
         uint32_t e = 0;
-        for (int k = 0; k < nl; ++k) e |= (uint32_t)((l >> k) & 1) << lane[k];
+        for (int k = 0; k < g; ++k) e |= (uint32_t)((l >> k) & 1) << grp[k];
         const uint32_t w0 = tile_swizzle(e, CE) * (uint32_t)esz / 4;
         for (int i = 0; i < per; ++i) w[nw++] = w0 + (uint32_t)i;
     }
@@ -533,12 +532,13 @@ static int phase_wavefronts(const uint8_t *R, int r, const int *lane, int nl, in
     nw = (int)(std::unique(w, w + nw) - w);
     int cnt[32] = {0}, worst = 0;
     for (int i = 0; i < nw; ++i) worst = std::max(worst, ++cnt[w[i] & 31]);
-    return worst * ((1 << r) >> (paired ? 1 : 0));
+    return worst;
 }
 
-// Thread-bit order of a register phase: the non-register tile bits, with the
-// five lane bits (or all of them, if fewer) chosen to minimise the phase's
-// shared-memory wavefronts; ties keep the lowest bits.
+// Thread-bit order of a register phase: among the non-register tile bits,
+// the lowest lane bits (4 for 8-byte slot accesses, 3 for 16-byte ones) are
+// the set that minimises the lane group's shared-memory wavefronts (ties keep
+// the lowest bits); the remaining non-register bits follow in ascending order.
 static void choose_thread_bits(const uint8_t *R, int r, int t, int esz, uint8_t *T)
 {
     int tb[kMaxTileBits], nt = 0;
@@ -547,17 +547,16 @@ static void choose_thread_bits(const uint8_t *R, int r, int t, int esz, uint8_t 
         for (int j = 0; j < r; ++j) reg |= R[j] == b;
         if (!reg) tb[nt++] = b;
     }
-    const int nl = std::min(5, nt);
-    int best_mask = (1 << nl) - 1, best = 1 << 30;
-    if (nt > nl) {
-        for (int m = 0; m < (1 << nt); ++m) {
-            if (__builtin_popcount(m) != nl) continue;
-            int lane[5], k = 0;
-            for (int i = 0; i < nt; ++i)
-                if ((m >> i) & 1) lane[k++] = tb[i];
-            const int c = phase_wavefronts(R, r, lane, nl, esz);
-            if (c < best || (c == best && m < best_mask)) { best = c; best_mask = m; }
-        }
+    const bool paired = esz == 8 && R[0] == 0;
+    const int g = std::min(paired || esz == 16 ? 3 : 4, nt);
+    int best_mask = (1 << g) - 1, best = 1 << 30;
+    for (int m = 0; m < (1 << nt); ++m) {
+        if (__builtin_popcount(m) != g) continue;
+        int grp[4], k = 0;
+        for (int i = 0; i < nt; ++i)
+            if ((m >> i) & 1) grp[k++] = tb[i];
+        const int c = group_wavefronts(grp, g, esz, paired);
+        if (c < best || (c == best && m < best_mask)) { best = c; best_mask = m; }
     }
     int k = 0;
     for (int i = 0; i < nt; ++i)
