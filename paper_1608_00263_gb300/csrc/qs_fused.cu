@@ -373,7 +373,10 @@ struct FusedSmem {
 // or im (k >= 64) of the tile amplitude (block index k mod 64, col), scaled
 // by 2^14 / 2^ceil(d/2), d = deferred 1/sqrt2 factors pending in the tile:
 // |value| <= 2^(d/2) ||psi||, ||psi|| ~ 1, so scaled values stay below the
-// FP16 maximum (the scale is a power of two: exact).  FP16 hi + lo splits of A and B, three products (hi hi, hi lo,
+// FP16 maximum (the scale is a power of two: exact).  Rows of A and D
+// interleave the real and imaginary parts of the 64 output block rows, so
+// neighbouring lanes of the epilogue store the two halves of one amplitude.
+// FP16 hi + lo splits of A and B, three products (hi hi, hi lo,
 // lo hi) and FP32 accumulation give ~22 significant bits.  A lives in
 // tensor memory (loaded once per CTA), B in shared memory (canonical
 // K-major layout without swizzle: 8 x 16-byte core matrices, 128 bytes
@@ -567,8 +570,8 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
     // ---- D (TMEM) -> tile: warp w reads lanes 32 (w & 3) .., columns 64 (w >> 2) .. ----
     {
         const int m = 32 * (warp & 3) + lane;
-        const uint32_t rowoff = blk[m & 63];
-        const int comp = m >> 6;
+        const uint32_t rowoff = blk[m >> 1];     // rows interleave re / im
+        const int comp = m & 1;
         float *tf = reinterpret_cast<float *>(tile);
 #pragma unroll 1
         for (int c = 0; c < 2; ++c) {

@@ -620,6 +620,41 @@ static uint64_t choose_tc_block(const std::vector<PGate> &g, const std::vector<i
     return block;
 }
 
+// Order of the block bits of a tensor-core phase.  The accumulator leaves
+// tensor memory one row per lane: a warp holds block rows 16w'..16w'+15
+// (index bits 0..3), real and imaginary parts on neighbouring lanes, and
+// stores them as 4-byte words.  The four block bits put on index bits 0..3
+// are the ones whose swizzled words fall in the fewest rounds per bank (zero
+// conflicts when they spread over all banks); the other two follow.
+static void order_tc_block(int *bq, uint8_t *R)
+{
+    int best = 1 << 30, best_m = 0x0f;
+    for (int m = 0; m < (1 << kTcBits); ++m) {
+        if (__builtin_popcount(m) != 4) continue;
+        int sel[4], k = 0;
+        for (int j = 0; j < kTcBits; ++j)
+            if ((m >> j) & 1) sel[k++] = R[j];
+        uint32_t w[32];
+        for (int i = 0; i < 16; ++i) {
+            uint32_t e = 0;
+            for (int b = 0; b < 4; ++b) e |= (uint32_t)((i >> b) & 1) << sel[b];
+            const uint32_t x = tile_swizzle(e, 2);
+            w[2 * i] = 2 * x;
+            w[2 * i + 1] = 2 * x + 1;
+        }
+        int cnt[32] = {0}, worst = 0;
+        for (int i = 0; i < 32; ++i) worst = std::max(worst, ++cnt[w[i] & 31]);
+        if (worst < best || (worst == best && m < best_m)) { best = worst; best_m = m; }
+    }
+    int nb[kTcBits];
+    uint8_t nr[kTcBits];
+    int k = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int j = 0; j < kTcBits; ++j)
+            if ((((best_m >> j) & 1) != 0) == (pass == 0)) { nb[k] = bq[j]; nr[k] = R[j]; ++k; }
+    for (int j = 0; j < kTcBits; ++j) { bq[j] = nb[j]; R[j] = nr[j]; }
+}
+
 // Block unitary (64 x 64, row-major, complex as re/im pairs) of `gates` on
 // block qubits bq[0..5] (block bit j <-> qubit bq[j]), applied in order.
 static void block_unitary(const std::vector<PGate> &g, const std::vector<int> &gates,
@@ -704,9 +739,11 @@ static void pack_block(const std::vector<Cplx> &U, std::vector<uint32_t> *words)
     for (int m = 0; m < MK; ++m) {
         uint16_t hi[2 * 64], lo[2 * 64];
         for (int k = 0; k < MK; ++k) {
-            const Cplx &u = U[(size_t)(m % D) * D + (k % D)];
+            // output rows interleave re / im of block row m / 2; input
+            // columns are the re block then the im block
+            const Cplx &u = U[(size_t)(m / 2) * D + (k % D)];
             double a;
-            if (m < D) a = k < D ? u.re : -u.im;
+            if (!(m & 1)) a = k < D ? u.re : -u.im;
             else a = k < D ? u.im : u.re;
             hi[k] = f64_to_f16_bits(a);
             lo[k] = f64_to_f16_bits(a - f16_bits_to_f64(hi[k]));
@@ -817,6 +854,7 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
                     int bq[kTcBits], j = 0;
                     for (int q = 0; q < n; ++q)
                         if ((blk >> q) & 1) { bq[j] = q; ph.R[j++] = (uint8_t)tile_bit_of[q]; }
+                    order_tc_block(bq, ph.R);
                     ph.kind = 1;
                     ph.tc_block = (int)(P.tc_words.size() / kTcWordsPerBlock);
                     ph.defer_before = deferred;

@@ -92,9 +92,12 @@ struct DevPhase {       // 40 bytes
 };
 
 // Tensor-core block phase: a k = 6 qubit block unitary U (64 x 64 complex)
-// realified to A = [[Re U, -Im U], [Im U, Re U]] (128 x 128), split into
-// FP16 hi + lo, stored row-major as 32-bit words of two consecutive K
-// elements (lower K in the low half): 128 rows x (64 hi words, 64 lo words).
+// realified to A (128 x 128): row 2i is (Re U_i, -Im U_i) and row 2i+1 is
+// (Im U_i, Re U_i) over the K columns (re block, then im block), i.e. the
+// rows of [[Re U, -Im U], [Im U, Re U]] with real and imaginary output rows
+// interleaved; split into FP16 hi + lo, stored row-major as 32-bit words of
+// two consecutive K elements (lower K in the low half): 128 rows x (64 hi
+// words, 64 lo words).
 constexpr int kTcBits = 6;
 constexpr int kTcWordsPerBlock = 128 * 128;
 constexpr int kMaxTcPerPass = 1;        // TMEM per CTA: accumulator + 1 block (hi, lo); 2 CTAs per SM

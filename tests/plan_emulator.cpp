@@ -21,7 +21,7 @@ extern "C" double emul_f16_back(uint16_t h) { return f16_bits_to_f64(h); }
 
 // Tensor-core phase: apply the stored block matrix (hi + lo, decoded) to
 // every column of the tile: the 64 amplitudes over the block bits, as
-// realified vectors [re; im].
+// realified vectors [re; im]; output rows interleave re and im.
 static void apply_tc(const Plan &plan, const DevPass &P, const DevPhase &H, std::vector<cd> &tile)
 {
     const uint32_t *w = plan.tc_words.data() + (size_t)H.tc_block * kTcWordsPerBlock;
@@ -52,7 +52,7 @@ static void apply_tc(const Plan &plan, const DevPass &P, const DevPhase &H, std:
         for (int b = 0; b < 64; ++b) {
             uint64_t e = col;
             for (int j = 0; j < kTcBits; ++j) e |= (uint64_t)((b >> j) & 1) << H.R[j];
-            tile[e] = cd(o[b], o[64 + b]);
+            tile[e] = cd(o[2 * b], o[2 * b + 1]);
         }
     }
 }
