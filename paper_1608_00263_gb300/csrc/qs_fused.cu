@@ -193,48 +193,60 @@ template <> struct CtzT<0> { static constexpr int value = 0; };
 
 // Loads / stores the register slots of a phase from / to the shared tile,
 // visiting slots in Gray-code order so that each address differs from the
-// previous one by one register bit (one XOR with that bit's offset).
+// previous one by one register bit (one XOR with that bit's offset); the two
+// halves of the slots run as two interleaved chains.
 // COUNT slots (or slot pairs when SHIFT = 1: register bit 0 is tile bit 0,
 // so slots s and s+1 are one 16-byte unit).
 template <int COUNT, int SHIFT>
 struct SlotIO {
     // offsets are in bytes from the start of the tile
+    // two Gray-code chains, one per half of the slots (top register bit
+    // clear / set): half the dependent address XORs per load sequence
+    static constexpr int kTop = CtzT<COUNT>::value - 1;
     template <int I, typename V>
-    struct Step {
-        static __device__ __forceinline__ void ld(V *a, const char *tile, uint32_t off, const uint32_t *pb)
+    struct Step2 {
+        static __device__ __forceinline__ void ld(V *a, const char *tile, uint32_t o0, uint32_t o1, const uint32_t *pb)
         {
-            if (I) off ^= pb[SHIFT + CtzT<I>::value];
-            constexpr int s = (I ^ (I >> 1)) << SHIFT;
+            if (I) { o0 ^= pb[SHIFT + CtzT<I>::value]; o1 ^= pb[SHIFT + CtzT<I>::value]; }
+            constexpr int s0 = (I ^ (I >> 1)) << SHIFT;
+            constexpr int s1 = s0 + ((COUNT / 2) << SHIFT);
             if (SHIFT) {
-                const float4 v = *reinterpret_cast<const float4 *>(tile + off);
-                a[s].x = v.x; a[s].y = v.y; a[s + 1].x = v.z; a[s + 1].y = v.w;
+                const float4 v = *reinterpret_cast<const float4 *>(tile + o0);
+                const float4 w = *reinterpret_cast<const float4 *>(tile + o1);
+                a[s0].x = v.x; a[s0].y = v.y; a[s0 + 1].x = v.z; a[s0 + 1].y = v.w;
+                a[s1].x = w.x; a[s1].y = w.y; a[s1 + 1].x = w.z; a[s1 + 1].y = w.w;
             } else {
-                a[s] = *reinterpret_cast<const V *>(tile + off);
+                a[s0] = *reinterpret_cast<const V *>(tile + o0);
+                a[s1] = *reinterpret_cast<const V *>(tile + o1);
             }
-            Step<I + 1, V>::ld(a, tile, off, pb);
+            Step2<I + 1, V>::ld(a, tile, o0, o1, pb);
         }
-        static __device__ __forceinline__ void st(const V *a, char *tile, uint32_t off, const uint32_t *pb)
+        static __device__ __forceinline__ void st(const V *a, char *tile, uint32_t o0, uint32_t o1, const uint32_t *pb)
         {
-            if (I) off ^= pb[SHIFT + CtzT<I>::value];
-            constexpr int s = (I ^ (I >> 1)) << SHIFT;
-            if (SHIFT)
-                *reinterpret_cast<float4 *>(tile + off) = make_float4(a[s].x, a[s].y, a[s + 1].x, a[s + 1].y);
-            else
-                *reinterpret_cast<V *>(tile + off) = a[s];
-            Step<I + 1, V>::st(a, tile, off, pb);
+            if (I) { o0 ^= pb[SHIFT + CtzT<I>::value]; o1 ^= pb[SHIFT + CtzT<I>::value]; }
+            constexpr int s0 = (I ^ (I >> 1)) << SHIFT;
+            constexpr int s1 = s0 + ((COUNT / 2) << SHIFT);
+            if (SHIFT) {
+                *reinterpret_cast<float4 *>(tile + o0) = make_float4(a[s0].x, a[s0].y, a[s0 + 1].x, a[s0 + 1].y);
+                *reinterpret_cast<float4 *>(tile + o1) = make_float4(a[s1].x, a[s1].y, a[s1 + 1].x, a[s1 + 1].y);
+            } else {
+                *reinterpret_cast<V *>(tile + o0) = a[s0];
+                *reinterpret_cast<V *>(tile + o1) = a[s1];
+            }
+            Step2<I + 1, V>::st(a, tile, o0, o1, pb);
         }
     };
     template <typename V>
-    struct Step<COUNT, V> {
-        static __device__ __forceinline__ void ld(V *, const char *, uint32_t, const uint32_t *) {}
-        static __device__ __forceinline__ void st(const V *, char *, uint32_t, const uint32_t *) {}
+    struct Step2<COUNT / 2, V> {
+        static __device__ __forceinline__ void ld(V *, const char *, uint32_t, uint32_t, const uint32_t *) {}
+        static __device__ __forceinline__ void st(const V *, char *, uint32_t, uint32_t, const uint32_t *) {}
     };
     template <typename V>
     static __device__ __forceinline__ void load(V *a, const char *tile, uint32_t off, const uint32_t *pb)
-    { Step<0, V>::ld(a, tile, off, pb); }
+    { Step2<0, V>::ld(a, tile, off, off ^ pb[SHIFT + kTop], pb); }
     template <typename V>
     static __device__ __forceinline__ void store(const V *a, char *tile, uint32_t off, const uint32_t *pb)
-    { Step<0, V>::st(a, tile, off, pb); }
+    { Step2<0, V>::st(a, tile, off, off ^ pb[SHIFT + kTop], pb); }
 };
 
 // Executes one staged op on the register slots.  `sel` is the part of a
