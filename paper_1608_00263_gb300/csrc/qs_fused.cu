@@ -574,11 +574,22 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
                          : "r"(mb), "r"(parity));
         }
         if (!done) {
+            // give up on this launch: the products may still be in flight,
+            // so wait once more (bounded) before the caller releases the
+            // tensor memory, and skip the epilogue
             TS.abort = 1;
             atomicExch(err_flag, 1);
+            for (int it = 0; it < kTcWaitLimit && !done; ++it) {
+                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             " selp.u32 %0, 1, 0, p;\n}"
+                             : "=r"(done)
+                             : "r"(mb), "r"(parity));
+            }
         }
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (TS.abort) return;
     // ---- D (TMEM) -> tile: warp w reads lanes 32 (w & 3) .., columns 64 (w >> 2) .. ----
     {
         const int m = 32 * (warp & 3) + lane;
