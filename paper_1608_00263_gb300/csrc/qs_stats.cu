@@ -35,6 +35,25 @@ constexpr int kChunk = 256;    // sampler chunk (amplitudes)
 // ---------------------------------------------------------------------------
 // probabilities
 // ---------------------------------------------------------------------------
+// FP32 -> FP64 by integer operations (exact): this GPU's FP64 pipe is
+// narrow, and one conversion per amplitude would bound the pass.  Zero and
+// normal values take the integer path; subnormals (and inf / nan) the
+// hardware conversion.
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if ((b & 0x7FFFFFFFu) == 0) return 0.0;
+    if (e == 0 || e == 0xFFu) return (double)f;
+    const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                       ((uint64_t)(b & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+// |psi|^2 of a complex64 amplitude: formed in FP32 (one FMA), the state's
+// own precision, then widened exactly when the output is FP64.
+__device__ __forceinline__ float prob32(float2 v) { return fmaf(v.x, v.x, v.y * v.y); }
+
 template <typename R, typename O>
 __global__ void k_probs(const typename V2T<R>::T *__restrict__ a, O *__restrict__ out,
                         uint64_t first, uint64_t count)
@@ -42,12 +61,30 @@ __global__ void k_probs(const typename V2T<R>::T *__restrict__ a, O *__restrict_
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         auto v = a[first + i];
-        if (sizeof(O) == 8) {
-            double re = (double)v.x, im = (double)v.y;
-            out[i] = (O)(re * re + im * im);
+        if constexpr (sizeof(R) == 4) {
+            const float p = prob32(v);
+            if constexpr (sizeof(O) == 8) out[i] = widen_f32(p);
+            else out[i] = p;
         } else {
             out[i] = (O)(v.x * v.x + v.y * v.y);
         }
+    }
+}
+
+// complex64, two amplitudes per thread and step (16-byte loads, 8- or
+// 16-byte stores); the same values as k_probs.
+template <typename O>
+__global__ void k_probs_c64x2(const float4 *__restrict__ a2, O *__restrict__ out, uint64_t first2,
+                              uint64_t count2)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count2; i += stride) {
+        const float4 v = a2[first2 + i];
+        const float p0 = prob32(make_float2(v.x, v.y)), p1 = prob32(make_float2(v.z, v.w));
+        if constexpr (sizeof(O) == 8)
+            reinterpret_cast<double2 *>(out)[i] = make_double2(widen_f32(p0), widen_f32(p1));
+        else
+            reinterpret_cast<float2 *>(out)[i] = make_float2(p0, p1);
     }
 }
 
@@ -55,11 +92,23 @@ qs_status launch_probabilities(const qs_state *s, void *out, int fp64, uint64_t 
                                uint64_t count)
 {
     const int th = 256;
-    const int grid = grid_for(count, th, s->num_sms, 16);
     if (s->dt == QS_C64) {
-        if (fp64) k_probs<float, double><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (double *)out, first, count);
-        else k_probs<float, float><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (float *)out, first, count);
+        const bool pairs = !(first & 1) && !(count & 1) && !((uintptr_t)out & (fp64 ? 15 : 7));
+        if (pairs) {
+            const int grid = grid_for(count / 2, th, s->num_sms, 32);
+            if (fp64)
+                k_probs_c64x2<double><<<grid, th, 0, s->stream>>>((const float4 *)s->amps, (double *)out, first / 2,
+                                                                  count / 2);
+            else
+                k_probs_c64x2<float><<<grid, th, 0, s->stream>>>((const float4 *)s->amps, (float *)out, first / 2,
+                                                                 count / 2);
+        } else {
+            const int grid = grid_for(count, th, s->num_sms, 32);
+            if (fp64) k_probs<float, double><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (double *)out, first, count);
+            else k_probs<float, float><<<grid, th, 0, s->stream>>>((const float2 *)s->amps, (float *)out, first, count);
+        }
     } else {
+        const int grid = grid_for(count, th, s->num_sms, 16);
         if (fp64) k_probs<double, double><<<grid, th, 0, s->stream>>>((const double2 *)s->amps, (double *)out, first, count);
         else k_probs<double, float><<<grid, th, 0, s->stream>>>((const double2 *)s->amps, (float *)out, first, count);
     }
@@ -112,6 +161,25 @@ __device__ __forceinline__ void stat_terms(T y, T (&c)[kStatAcc])
 }
 
 // complex64: FP32 per element and per 128-element partial, FP64 across.
+// Each step issues eight 16-byte loads before using them (enough bytes in
+// flight per SM to keep HBM busy).  Elements with y^10 beyond the FP32
+// range (y > 2^12, vanishingly rare) go straight to the FP64 accumulators.
+__device__ __forceinline__ void stat_pair(const float4 v, float scaleN, float (&c)[kStatAcc],
+                                          double (&acc)[kStatAcc])
+{
+    const float y0 = (v.x * v.x + v.y * v.y) * scaleN;
+    const float y1 = (v.z * v.z + v.w * v.w) * scaleN;
+    if (y0 > 4096.f || y1 > 4096.f) {
+        const double d0 = ((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN;
+        const double d1 = ((double)v.z * v.z + (double)v.w * v.w) * (double)scaleN;
+        stat_terms<double>(d0, acc);
+        stat_terms<double>(d1, acc);
+    } else {
+        stat_terms<float>(y0, c);
+        stat_terms<float>(y1, c);
+    }
+}
+
 __global__ void __launch_bounds__(kStatThreads)
 k_stats_c64(const float4 *__restrict__ a4, uint64_t nquads, float scaleN, double *__restrict__ part)
 {
@@ -124,34 +192,19 @@ k_stats_c64(const float4 *__restrict__ a4, uint64_t nquads, float scaleN, double
         float c[kStatAcc];
 #pragma unroll
         for (int k = 0; k < kStatAcc; ++k) c[k] = 0.f;
-        double big[kStatAcc];
-        bool any_big = false;
-        for (int it = 0; it < 64 && w < nquads; ++it, w += stride) {
-            float4 v = a4[w];
-            float y0 = (v.x * v.x + v.y * v.y) * scaleN;
-            float y1 = (v.z * v.z + v.w * v.w) * scaleN;
-            // y^10 overflows FP32 above ~2^12.8: such (rare) elements go to FP64
-            if (y0 > 4096.f || y1 > 4096.f) {
-                if (!any_big) {
+        for (int it = 0; it < 8 && w < nquads; ++it, w += 8 * stride) {
+            float4 v[8];
 #pragma unroll
-                    for (int k = 0; k < kStatAcc; ++k) big[k] = 0;
-                    any_big = true;
-                }
-                double d0 = ((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN;
-                double d1 = ((double)v.z * v.z + (double)v.w * v.w) * (double)scaleN;
-                stat_terms<double>(d0, big);
-                stat_terms<double>(d1, big);
-            } else {
-                stat_terms<float>(y0, c);
-                stat_terms<float>(y1, c);
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t wu = w + (uint64_t)u * stride;
+                v[u] = wu < nquads ? a4[wu] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (w + (uint64_t)u * stride < nquads) stat_pair(v[u], scaleN, c, acc);
         }
 #pragma unroll
         for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)c[k];
-        if (any_big) {
-#pragma unroll
-            for (int k = 0; k < kStatAcc; ++k) acc[k] += big[k];
-        }
     }
     block_sum_store<kStatAcc>(acc, part + (size_t)blockIdx.x * kStatAcc);
 }
@@ -187,7 +240,7 @@ qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *en
     int grid;
     double *part = s->ws_f64;
     if (s->dt == QS_C64 && N >= 2) {
-        grid = grid_for(N / 2, kStatThreads, s->num_sms, 4);
+        grid = grid_for(N / 2, kStatThreads, s->num_sms, 8);
         k_stats_c64<<<grid, kStatThreads, 0, s->stream>>>((const float4 *)s->amps, N / 2,
                                                            (float)std::ldexp(1.0, s->n), part);
     } else if (s->dt == QS_C64) {
@@ -314,10 +367,11 @@ void stats_from_sums(const double *h, int n, int kmax, double *norm, double *ent
 // sampler
 // ---------------------------------------------------------------------------
 // Lane l of a warp covers elements [8l, 8l+8) of a 256-amplitude chunk.  The
-// lane total is accumulated in the element type's precision (FP32 for
-// complex64, FP64 for complex128) and widened to FP64; the chunk sum is the
-// FP64 inclusive warp scan of the lane totals.  The search kernel repeats
-// exactly this arithmetic, so chunk sums and in-chunk prefixes agree.
+// lane totals and their inclusive warp scan are formed in the element type's
+// precision (FP32 for complex64, FP64 for complex128) and widened exactly to
+// FP64; the chunk sum is the scan's last lane.  The search kernels repeat
+// exactly this arithmetic, so chunk sums and in-chunk prefixes agree (the
+// chunk offsets themselves are FP64 scans of the chunk sums).
 template <typename R>
 __device__ __forceinline__ void lane_probs(const typename V2T<R>::T *a, uint64_t chunk, int lane,
                                            uint64_t N, R (&p)[8])
@@ -355,6 +409,31 @@ __device__ __forceinline__ double warp_incl_scan(double v)
     return v;
 }
 
+__device__ __forceinline__ float warp_incl_scan_f(float v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        float u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// In-chunk prefix of a lane: inclusive and exclusive scan of the lane totals.
+__device__ __forceinline__ void chunk_scan(double lt, double &incl, double &excl)
+{
+    incl = warp_incl_scan(lt);
+    excl = incl - lt;
+}
+__device__ __forceinline__ void chunk_scan(float lt, double &incl, double &excl)
+{
+    const float fi = warp_incl_scan_f(lt);
+    const float fe = __shfl_up_sync(0xffffffffu, fi, 1);
+    incl = widen_f32(fi);
+    excl = (threadIdx.x & 31) ? widen_f32(fe) : 0.0;
+}
+
 // One warp per chunk.
 template <typename R>
 __global__ void k_chunk_sums(const typename V2T<R>::T *__restrict__ a, uint64_t N, uint64_t nchunks,
@@ -365,7 +444,8 @@ __global__ void k_chunk_sums(const typename V2T<R>::T *__restrict__ a, uint64_t 
     for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += warps) {
         R p[8];
         lane_probs<R>(a, c, lane, N, p);
-        double incl = warp_incl_scan((double)lane_total<R>(p));
+        double incl, excl;
+        chunk_scan(lane_total<R>(p), incl, excl);
         if (lane == 31) csum[c] = incl;
     }
 }
@@ -482,8 +562,8 @@ __global__ void k_sample_search(const typename V2T<R>::T *__restrict__ a, uint64
             R p[8];
             lane_probs<R>(a, c, lane, N, p);
             const R lt = lane_total<R>(p);
-            const double incl = warp_incl_scan((double)lt);
-            const double excl = incl - (double)lt;
+            double incl, excl;
+            chunk_scan(lt, incl, excl);
             unsigned hit = __ballot_sync(0xffffffffu, incl > tq);
             unsigned nz = __ballot_sync(0xffffffffu, lt > (R)0);
             int L = hit ? __ffs(hit) - 1 : 31 - __clz(nz);   // rounding edge: last non-empty lane
@@ -578,7 +658,8 @@ __global__ void k_batch_chunk_sums(const float2 *__restrict__ amps, const uint64
         const int i = batch_instance_of(cbase, count, c);
         float p[8];
         lane_probs<float>(amps + off[i], c - cbase[i], lane, 1ULL << nq[i], p);
-        const double incl = warp_incl_scan((double)lane_total<float>(p));
+        double incl, excl;
+        chunk_scan(lane_total<float>(p), incl, excl);
         if (lane == 31) csum[c] = incl;
     }
 }
@@ -624,8 +705,8 @@ __global__ void k_batch_sample_search(const float2 *__restrict__ amps, const uin
             float p[8];
             lane_probs<float>(amps + off[iq], lc, lane, 1ULL << nq[iq], p);
             const float lt = lane_total<float>(p);
-            const double incl = warp_incl_scan((double)lt);
-            const double excl = incl - (double)lt;
+            double incl, excl;
+            chunk_scan(lt, incl, excl);
             const unsigned hit = __ballot_sync(0xffffffffu, incl > tq);
             const unsigned nz = __ballot_sync(0xffffffffu, lt > 0.f);
             const int L = hit ? __ffs(hit) - 1 : (nz ? 31 - __clz(nz) : 0);

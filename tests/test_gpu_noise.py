@@ -32,16 +32,22 @@ def device_state(b, i, n):
 
 def check_samples(got, p_ref, p_dev, n, seed, k, i, r_mes):
     """Sample j of instance i: identical to the oracle's rule on the oracle
-    state, except where FP32 rounding of the state moves a CDF boundary; then
-    it must be the oracle's rule applied to the GPU's own state."""
+    state, except where rounding moves a CDF boundary (the FP32 state, and
+    the FP32 prefix sums inside a 256-amplitude chunk); such a sample, with
+    its measurement flips undone, must still invert the GPU state's CDF
+    within that rounding (1e-6 of the total)."""
     mism = 0
+    c = np.cumsum(p_dev)
+    tol = 1e-6 * c[-1]
     for j in range(k):
         ctr = i * k + j
         want = O.measurement_flips(int(O.sample_at(p_ref, seed, [ctr])[0]), n, seed, r_mes, ctr)
         if int(got[j]) != want:
             mism += 1
-            own = O.measurement_flips(int(O.sample_at(p_dev, seed, [ctr])[0]), n, seed, r_mes, ctr)
-            assert int(got[j]) == own, (i, j, int(got[j]), want, own)
+            x = int(got[j]) ^ O.measurement_flips(0, n, seed, r_mes, ctr)
+            t = O.sample_uniform(seed, ctr) * c[-1]
+            lo = c[x - 1] if x > 0 else 0.0
+            assert lo - tol <= t <= c[x] + tol, (i, j, int(got[j]), want, t, lo, c[x])
     return mism
 
 
