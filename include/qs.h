@@ -142,10 +142,18 @@ qs_status qs_state_attach(int n, qs_dtype dt, void *device_amps,
  * NULL is accepted.  Synchronises the state's stream first. */
 qs_status qs_state_destroy(qs_state *s);
 
-/* Device pointer of the amplitudes (interleaved re, im). */
+/* Device pointer of the amplitudes (interleaved re, im).  Once the caller
+ * holds the pointer, resets are written at once and the library assumes
+ * nothing about the contents (see qs_state_reset). */
 qs_status qs_state_amplitudes(const qs_state *s, void **device_amps);
 
-/* Sets the state to |0...0>. */
+/* Sets the state to |0...0>.  For a state whose memory the caller cannot
+ * reach (created by qs_state_create, pointer never taken) the write is
+ * deferred to the next call that uses the state, and a following
+ * qs_apply_circuit whose gates open with H on every qubit writes the
+ * uniform superposition 2^(-n/2) in their place (Sec. "Convergence to
+ * Porter-Thomas": cycle 0 is that layer), one pass instead of several.
+ * Attached states, and states whose pointer was taken, are written at once. */
 qs_status qs_state_reset(qs_state *s);
 
 /* Applies `ngates` gates (host array, read during the call) in order:

@@ -34,6 +34,29 @@ void *pinned_device_view(void *p)
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Writes a deferred reset before the state is read or changed.
+qs_status materialize(const qs_state *s)
+{
+    if (!s->zero_pending) return QS_OK;
+    s->zero_pending = false;
+    return launch_init_zero(const_cast<qs_state *>(s));
+}
+
+// n when the gate list opens with H on every qubit (n gates, each qubit
+// once), else 0: on |0...0> that layer is the uniform superposition.
+size_t leading_h_layer(const qs_gate *g, size_t ng, int n)
+{
+    if (ng < (size_t)n) return 0;
+    uint64_t seen = 0;
+    for (int i = 0; i < n; ++i) {
+        if (g[i].kind != QS_H) return 0;
+        const uint64_t b = 1ULL << g[i].q0;
+        if (seen & b) return 0;
+        seen |= b;
+    }
+    return (size_t)n;
+}
+
 qs_status check_state(const qs_state *s)
 {
     if (!s) return set_error(QS_ERR_INVALID_ARG, "state is NULL");
@@ -131,6 +154,7 @@ extern "C" qs_status qs_state_create(int n, qs_dtype dt, void *cuda_stream, qs_s
         free_state(s);
         return st;
     }
+    s->is_zero = true;
     *out = s;
     return QS_OK;
 }
@@ -147,6 +171,7 @@ extern "C" qs_status qs_state_attach(int n, qs_dtype dt, void *device_amps, void
     if (st) return st;
     s->amps = device_amps;
     s->owns = false;
+    s->escaped = true;
     if ((st = alloc_workspace(s))) {
         free_state(s);
         return st;
@@ -167,6 +192,9 @@ extern "C" qs_status qs_state_amplitudes(const qs_state *s, void **device_amps)
     clear_error();
     if (qs_status st = check_state(s)) return st;
     if (!device_amps) return set_error(QS_ERR_INVALID_ARG, "device_amps is NULL");
+    DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
+    s->escaped = true;
     *device_amps = s->amps;
     return QS_OK;
 }
@@ -176,7 +204,13 @@ extern "C" qs_status qs_state_reset(qs_state *s)
     clear_error();
     if (qs_status st = check_state(s)) return st;
     DeviceGuard g(s->device);
-    return launch_init_zero(s);
+    s->is_zero = true;
+    if (s->escaped) {
+        s->zero_pending = false;
+        return launch_init_zero(s);
+    }
+    s->zero_pending = true;   // written by the next use (or skipped, see qs_apply_circuit)
+    return QS_OK;
 }
 
 static qs_status get_plan(qs_state *s, const qs_gate *gates, size_t ng, const qs_opts *o,
@@ -254,35 +288,39 @@ extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t 
     if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
     if (opts && opts->autotune != 0) return set_error(QS_ERR_UNSUPPORTED, "autotune is not built");
     const int mode = opts ? opts->mode : QS_MODE_FUSED;
+    if (mode != QS_MODE_PLAIN && mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
+        return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    const int rb = s->dt == QS_C128 ? 4 : 5;
+    if (mode == QS_MODE_FUSED && opts && opts->tile_log2 && (opts->tile_log2 < rb || opts->tile_log2 > rb + 8))
+        return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside %d..%d", opts->tile_log2, rb, rb + 8);
+    if (mode == QS_MODE_FUSED_TC && opts && opts->precision != QS_PREC_DEFAULT && opts->precision != QS_PREC_FP16X3)
+        return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
     if (ngates == 0) return QS_OK;
     DeviceGuard g(s->device);
-    const int rb = s->dt == QS_C128 ? 4 : 5;
-    if (mode == QS_MODE_PLAIN || ((mode == QS_MODE_FUSED || mode == QS_MODE_FUSED_TC) && s->n < rb)) {
+    // Sec. pt, cycle 0: on |0...0> a leading layer of Hadamards on every
+    // qubit gives the uniform superposition, written in one pass
+    if (s->is_zero && !s->escaped) {
+        if (const size_t h = leading_h_layer(gates, ngates, s->n)) {
+            s->zero_pending = false;
+            if (qs_status st = launch_init_uniform(s)) return st;
+            gates += h;
+            ngates -= h;
+        }
+    }
+    if (qs_status st = materialize(s)) return st;
+    s->is_zero = false;
+    if (ngates == 0) return QS_OK;
+    if (mode == QS_MODE_PLAIN || s->n < rb) {
         for (size_t i = 0; i < ngates; ++i)
             if (qs_status st = launch_plain_gate(s, gates[i])) return st;
         return QS_OK;
     }
-    if (mode == QS_MODE_FUSED) {
-        if (opts && opts->tile_log2 && (opts->tile_log2 < rb || opts->tile_log2 > rb + 8))
-            return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside %d..%d", opts->tile_log2, rb, rb + 8);
-        const Plan *plan;
-        const void *dev;
-        DevicePlanSlot *slot;
-        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
-        if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
-        return slot_in_use(s, slot);
-    }
-    if (mode == QS_MODE_FUSED_TC) {
-        if (opts && opts->precision != QS_PREC_DEFAULT && opts->precision != QS_PREC_FP16X3)
-            return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
-        const Plan *plan;
-        const void *dev;
-        DevicePlanSlot *slot;
-        if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
-        if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
-        return slot_in_use(s, slot);
-    }
-    return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    const Plan *plan;
+    const void *dev;
+    DevicePlanSlot *slot;
+    if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
+    if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
+    return slot_in_use(s, slot);
 }
 
 extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
@@ -297,6 +335,14 @@ extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_
     if (mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
         return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
     DeviceGuard g(s->device);
+    // a leading Hadamard layer is written as the uniform state when the
+    // circuit starts from |0...0> (the usual reset + apply): plan the rest
+    if (!s->escaped) {
+        const size_t h = leading_h_layer(gates, ngates, s->n);
+        gates += h;
+        ngates -= h;
+        if (ngates == 0) return QS_OK;
+    }
     const Plan *plan;
     const void *dev;
     return get_plan(s, gates, ngates, opts, &plan, &dev);
@@ -308,6 +354,7 @@ extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_f
     if (qs_status st = check_state(s)) return st;
     if (!out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
     DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
     const uint64_t N = 1ULL << s->n;
     const size_t esz = out_is_fp64 ? 8 : 4;
     if (is_device_ptr(out)) return launch_probabilities(s, out, out_is_fp64, 0, N);
@@ -340,6 +387,7 @@ extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uin
     if (qs_status st = check_state(s)) return st;
     if (k && !out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
     DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
     if (k == 0) return sampler_run(s, 0, seed, nullptr);
     if (is_device_ptr(out)) return sampler_run(s, k, seed, out);
     uint64_t *buf = nullptr;
@@ -363,6 +411,7 @@ extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples
     if (m == 0) return set_error(QS_ERR_INVALID_ARG, "empty sample");
     if (!samples) return set_error(QS_ERR_INVALID_ARG, "samples is NULL");
     DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
     double c = 0;
     qs_status st;
     if (is_device_ptr(samples)) {
@@ -391,6 +440,7 @@ extern "C" qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments,
     if (kmax < 0 || kmax > kMaxMoments) return set_error(QS_ERR_INVALID_ARG, "kmax %d outside 0..%d", kmax, kMaxMoments);
     if (kmax > 0 && !moments) return set_error(QS_ERR_INVALID_ARG, "moments is NULL");
     DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
     return stats_moments(s, kmax, moments, entropy, uniform_ce, norm);
 }
 
@@ -400,6 +450,7 @@ extern "C" qs_status qs_state_copy_out(const qs_state *s, void *host_amps)
     if (qs_status st = check_state(s)) return st;
     if (!host_amps) return set_error(QS_ERR_INVALID_ARG, "host_amps is NULL");
     DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
     const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
     QS_CUDA_TRY(cudaMemcpyAsync(host_amps, s->amps, bytes, cudaMemcpyDefault, s->stream));
     QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
@@ -413,6 +464,8 @@ extern "C" qs_status qs_state_copy_in(qs_state *s, const void *host_amps)
     if (!host_amps) return set_error(QS_ERR_INVALID_ARG, "host_amps is NULL");
     DeviceGuard g(s->device);
     const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
+    s->zero_pending = false;
+    s->is_zero = false;
     QS_CUDA_TRY(cudaMemcpyAsync(s->amps, host_amps, bytes, cudaMemcpyDefault, s->stream));
     QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return QS_OK;
@@ -428,7 +481,9 @@ extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size
     if (m == 0 || !samples) return set_error(QS_ERR_INVALID_ARG, "empty sample");
     if (ngates && !grad) return set_error(QS_ERR_INVALID_ARG, "grad is NULL");
     DeviceGuard g(s->device);
+    s->zero_pending = false;
     if (qs_status st = launch_init_zero(s)) return st;
+    s->is_zero = true;
     if (qs_status st = qs_apply_circuit(s, gates, ngates, opts)) return st;
     uint64_t *buf = nullptr;
     const uint64_t *dx = samples;
@@ -467,7 +522,9 @@ extern "C" qs_status qs_cycle_statistics(qs_state *s, const qs_gate *gates, size
     *ncycles = starts.size();
     if (!stats || capacity < starts.size()) return QS_OK;   // count query
     DeviceGuard g(s->device);
+    s->zero_pending = false;
     if (qs_status st = launch_init_zero(s)) return st;
+    s->is_zero = true;
     const int w = 4 + kmax;
     std::vector<double> mom(kMaxMoments);
     for (size_t c = 0; c < starts.size(); ++c) {

@@ -200,6 +200,14 @@ struct qs_state {
     size_t ws_f64_count;
     uint64_t *ws_u64;        // small integer scratch (flags, counters)
     qs::DevicePlanCache plan_cache;
+    // |0...0> bookkeeping, for applying a leading layer of Hadamards as one
+    // uniform write: is_zero -- the state is |0...0> (written, or pending:
+    // zero_pending defers the reset's write to the next use); escaped -- the
+    // caller can reach the memory (attached, or after qs_state_amplitudes),
+    // so resets are written at once and nothing is assumed about it.
+    bool is_zero = false;
+    mutable bool zero_pending = false;
+    mutable bool escaped = false;
 };
 
 namespace qs {
@@ -207,6 +215,8 @@ namespace qs {
 // Launchers (defined in the .cu files).  All are asynchronous on `st` and
 // return QS_ERR_CUDA (with message) on a launch failure.
 qs_status launch_init_zero(qs_state *s);
+// Every amplitude = 2^(-n/2): H^{(x)n} |0...0>.
+qs_status launch_init_uniform(qs_state *s);
 qs_status launch_plain_gate(qs_state *s, const qs_gate &g);
 qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan);
 qs_status run_tc_plan(qs_state *s, const Plan &plan, const void *dev_plan,

@@ -7,6 +7,8 @@
 // Details": a diagonal gate with a 1 on the diagonal touches only the
 // amplitudes it changes (T: the half with bit q set, 8N bytes for complex64;
 // CZ / CPHASE: the quarter with both bits set, 4N bytes).
+#include <cmath>
+
 #include "qs_device.cuh"
 
 namespace qs {
@@ -135,6 +137,42 @@ qs_status launch_init_zero(qs_state *s)
         k_set_basis0<float><<<1, 1, 0, s->stream>>>((float2 *)s->amps);
     else
         k_set_basis0<double><<<1, 1, 0, s->stream>>>((double2 *)s->amps);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
+
+// H on every qubit of |0...0>: the uniform superposition, two complex64 (or
+// one complex128) amplitudes per 16-byte store.
+template <typename R>
+__global__ void k_fill_uniform(float4 *a, uint64_t units, R v)
+{
+    float4 u;
+    if constexpr (sizeof(R) == 4) {
+        u = make_float4(v, 0.f, v, 0.f);
+    } else {
+        const double2 d = make_double2(v, 0.0);
+        u = *reinterpret_cast<const float4 *>(&d);
+    }
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < units; i += stride) a[i] = u;
+}
+
+qs_status launch_init_uniform(qs_state *s)
+{
+    const uint64_t N = 1ULL << s->n;
+    const double v = std::pow(2.0, -0.5 * s->n);
+    const int th = 256;
+    if (s->dt == QS_C64 && N >= 2) {
+        const uint64_t units = N / 2;
+        k_fill_uniform<float><<<grid_for(units, th, s->num_sms, 16), th, 0, s->stream>>>((float4 *)s->amps, units,
+                                                                                      (float)v);
+    } else if (s->dt == QS_C64) {
+        const float2 one = make_float2((float)v, 0.f);
+        QS_CUDA_TRY(cudaMemcpyAsync(s->amps, &one, sizeof one, cudaMemcpyHostToDevice, s->stream));
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    } else {
+        k_fill_uniform<double><<<grid_for(N, th, s->num_sms, 16), th, 0, s->stream>>>((float4 *)s->amps, N, v);
+    }
     QS_LAUNCH_CHECK();
     return QS_OK;
 }

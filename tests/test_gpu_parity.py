@@ -131,6 +131,41 @@ def test_grid_4x6_depth30_c64():
         assert rel_l2(gpu_run(24, g, qs.QS_C64, mode=mode), ref) < 1e-5
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_leading_hadamard_layer_only_from_basis_zero(dtype):
+    """A circuit opening with H on every qubit is written as the uniform
+    state only when the state is |0...0>: a second apply, an explicit reset,
+    a reset after the caller took the pointer, and a reset that is read
+    before any apply all give the oracle's result."""
+    n = 12
+    g = qs.qs_circuit_generate(3, 4, 10, 3)
+    perm = g.copy()
+    perm[:n] = g[:n][::-1]                      # the H layer in another qubit order
+    h = qs.qs_state_create(n, dtype)
+    try:
+        qs.qs_apply_circuit(h, g)
+        qs.qs_apply_circuit(h, perm)             # not from |0...0>: no fold
+        ref2 = O.simulate(n, np.concatenate([g, perm]))
+        assert rel_l2(qs.qs_state_copy_out(h, n, dtype), ref2) < TOL[dtype]
+        qs.qs_state_reset(h)
+        host = np.empty(1 << n, dtype=np.float64)
+        qs.qs_probabilities(h, host, fp64=True)  # a deferred reset is written before the read
+        assert host[0] == 1 and np.count_nonzero(host) == 1
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, perm)
+        assert rel_l2(qs.qs_state_copy_out(h, n, dtype), O.simulate(n, perm)) < TOL[dtype]
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g[:n])            # the layer alone: exactly uniform
+        psi = qs.qs_state_copy_out(h, n, dtype)
+        assert np.allclose(psi, 2.0 ** (-n / 2), rtol=1e-6, atol=0)
+        qs.qs_state_amplitudes(h)                # the caller can now write the memory
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g)
+        assert rel_l2(qs.qs_state_copy_out(h, n, dtype), O.simulate(n, g)) < TOL[dtype]
+    finally:
+        qs.qs_state_destroy(h)
+
+
 def test_invalid_gate_launches_nothing():
     n = 10
     h = qs.qs_state_create(n, qs.QS_C64)
