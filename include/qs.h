@@ -187,6 +187,24 @@ qs_status qs_plan_circuit(int n, qs_dtype dt, const qs_gate *gates,
  * Asynchronous for device `out`; synchronous for host `out`. */
 qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64);
 
+/* As qs_probabilities, but stream-ordered for every kind of `out` except
+ * pageable host memory (which is served synchronously, as by
+ * qs_probabilities).  For page-locked host `out` (cudaHostAlloc /
+ * cudaHostRegister) the probabilities are formed in a library-owned device
+ * buffer (2^n floats or doubles, allocated on first use and kept with the
+ * state) on the state's stream and copied to `out` by the copy engine on a
+ * second stream, so the copy overlaps the work the caller enqueues next
+ * (e.g. the next circuit).  `out` holds the probabilities of the state as
+ * it was at the call once qs_state_sync(s) has returned; until then the
+ * caller must neither read nor free it.  Successive asynchronous read-outs
+ * of one state are copied in call order.  QS_ERR_OOM if the device buffer
+ * cannot be allocated. */
+qs_status qs_probabilities_async(const qs_state *s, void *out, int out_is_fp64);
+
+/* Waits for all work of the state: its stream and any asynchronous
+ * read-out copies (qs_probabilities_async).  QS_ERR_CUDA on a device error. */
+qs_status qs_state_sync(const qs_state *s);
+
 /* Draws k bitstrings from p_U (inverse-CDF sampling, Sec. "Characterizing
  * quantum supremacy", step 2 of the procedure).  Sample j uses the uniform
  * u_j = (SplitMix64 output j of a stream seeded with `seed`) >> 11, times

@@ -23,7 +23,8 @@ __all__ = [
     "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
-    "qs_probabilities", "qs_sample", "qs_sample_noalloc", "qs_cross_entropy", "qs_pt_moments",
+    "qs_probabilities", "qs_probabilities_async", "qs_state_sync", "qs_sample", "qs_sample_noalloc",
+    "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
@@ -132,6 +133,18 @@ def qs_probabilities(h, out, fp64=True):
     """Writes |<x|psi>|^2 into `out` (torch tensor, numpy array or address)."""
     N.check(N.lib().qs_probabilities(h, _ptr(out), 1 if fp64 else 0))
     return out
+
+
+def qs_probabilities_async(h, out, fp64=True):
+    """As qs_probabilities, stream-ordered; page-locked host `out` is filled
+    by the copy engine while later work runs: complete after qs_state_sync."""
+    N.check(N.lib().qs_probabilities_async(h, _ptr(out), 1 if fp64 else 0))
+    return out
+
+
+def qs_state_sync(h):
+    """Waits for the state's stream and its asynchronous read-out copies."""
+    N.check(N.lib().qs_state_sync(h))
 
 
 def qs_sample(h, k, seed, out=None):

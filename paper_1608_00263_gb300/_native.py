@@ -72,6 +72,8 @@ SIGNATURES = {
     "qs_plan_circuit": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t,
                                        ctypes.POINTER(qs_opts), ctypes.POINTER(qs_plan_stats)]),
     "qs_probabilities": (ctypes.c_int, [P, P, ctypes.c_int]),
+    "qs_probabilities_async": (ctypes.c_int, [P, P, ctypes.c_int]),
+    "qs_state_sync": (ctypes.c_int, [P]),
     "qs_sample": (ctypes.c_int, [P, U64, U64, P]),
     "qs_sample_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, U64, U64, P]),
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),

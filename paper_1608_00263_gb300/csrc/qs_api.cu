@@ -1,5 +1,6 @@
 // qs_api.cu -- the C ABI entry points of include/qs.h (host side): argument
 // validation, memory classification, planning and dispatch to the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -42,21 +43,6 @@ qs_status materialize(const qs_state *s)
     return launch_init_zero(const_cast<qs_state *>(s));
 }
 
-// n when the gate list opens with H on every qubit (n gates, each qubit
-// once), else 0: on |0...0> that layer is the uniform superposition.
-size_t leading_h_layer(const qs_gate *g, size_t ng, int n)
-{
-    if (ng < (size_t)n) return 0;
-    uint64_t seen = 0;
-    for (int i = 0; i < n; ++i) {
-        if (g[i].kind != QS_H) return 0;
-        const uint64_t b = 1ULL << g[i].q0;
-        if (seen & b) return 0;
-        seen |= b;
-    }
-    return (size_t)n;
-}
-
 qs_status check_state(const qs_state *s)
 {
     if (!s) return set_error(QS_ERR_INVALID_ARG, "state is NULL");
@@ -91,6 +77,8 @@ qs_status alloc_workspace(qs_state *s)
     QS_CUDA_TRY(cudaMalloc((void **)&s->ws_f64, kWsDoubles * sizeof(double)));
     s->ws_f64_count = kWsDoubles;
     QS_CUDA_TRY(cudaMalloc((void **)&s->ws_u64, 64 * sizeof(uint64_t)));
+    QS_CUDA_TRY(cudaHostAlloc(&s->hbox, kHostBoxBytes, cudaHostAllocMapped));
+    QS_CUDA_TRY(cudaHostGetDevicePointer(&s->hbox_dev, s->hbox, 0));
     return QS_OK;
 }
 
@@ -120,9 +108,16 @@ void free_state(qs_state *s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    if (s->ro_stream) cudaStreamSynchronize(s->ro_stream);
+    if (s->ro_buf) cudaFree(s->ro_buf);
+    if (s->ro_ready) cudaEventDestroy(s->ro_ready);
+    if (s->ro_done) cudaEventDestroy(s->ro_done);
+    if (s->ro_stream) cudaStreamDestroy(s->ro_stream);
     if (s->owns && s->amps) cudaFree(s->amps);
     if (s->ws_f64) cudaFree(s->ws_f64);
     if (s->ws_u64) cudaFree(s->ws_u64);
+    if (s->hbox) cudaFreeHost(s->hbox);
+    if (s->stage) cudaFreeHost(s->stage);
     for (DevicePlanSlot &c : s->plan_cache.slot) {
         if (c.dev) cudaFree(c.dev);
         if (c.staging) cudaFreeHost(c.staging);
@@ -358,6 +353,8 @@ extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_f
     const uint64_t N = 1ULL << s->n;
     const size_t esz = out_is_fp64 ? 8 : 4;
     if (is_device_ptr(out)) return launch_probabilities(s, out, out_is_fp64, 0, N);
+    // an asynchronous read-out still copying may target the same host memory
+    if (s->ro_done) QS_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ro_done, 0));
     if (void *view = pinned_device_view(out)) {
         // page-locked host output: the kernel writes it directly (one pass)
         if (qs_status st = launch_probabilities(s, view, out_is_fp64, 0, N)) return st;
@@ -381,6 +378,72 @@ extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_f
     return st;
 }
 
+extern "C" qs_status qs_probabilities_async(const qs_state *s, void *out, int out_is_fp64)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (!out) return set_error(QS_ERR_INVALID_ARG, "out is NULL");
+    if (is_device_ptr(out) || !pinned_device_view(out)) return qs_probabilities(s, out, out_is_fp64);
+    DeviceGuard g(s->device);
+    if (qs_status st = materialize(s)) return st;
+    const uint64_t N = 1ULL << s->n;
+    const size_t bytes = N * (out_is_fp64 ? 8 : 4);
+    if (!s->ro_done) {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ready = nullptr, done = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (ready) cudaEventDestroy(ready);
+            if (cs) cudaStreamDestroy(cs);
+            return set_error(QS_ERR_CUDA, "read-out stream: %s", cudaGetErrorString(e));
+        }
+        s->ro_stream = cs;
+        s->ro_ready = ready;
+        s->ro_done = done;
+    }
+    if (s->ro_bytes < bytes) {
+        // the buffer is replaced only after its last copy has finished
+        QS_CUDA_TRY(cudaStreamSynchronize(s->ro_stream));
+        if (s->ro_buf) cudaFree(s->ro_buf);
+        s->ro_buf = nullptr;
+        s->ro_bytes = 0;
+        cudaError_t e = cudaMalloc(&s->ro_buf, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->ro_buf = nullptr;
+            return set_error(QS_ERR_OOM, "read-out buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        }
+        s->ro_bytes = bytes;
+    }
+    // the buffer is free once the previous copy has finished (an event never
+    // recorded is complete)
+    QS_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ro_done, 0));
+    if (qs_status st = launch_probabilities(s, s->ro_buf, out_is_fp64, 0, N)) return st;
+    QS_CUDA_TRY(cudaEventRecord(s->ro_ready, s->stream));
+    QS_CUDA_TRY(cudaStreamWaitEvent(s->ro_stream, s->ro_ready, 0));
+    // 64 MB pieces: the small device-to-host copies of later calls (scalar
+    // results, samples) share the copy engine and would otherwise wait for
+    // the whole read-out, and with them the host's next launches
+    constexpr size_t kPiece = size_t(64) << 20;
+    for (size_t f = 0; f < bytes; f += kPiece)
+        QS_CUDA_TRY(cudaMemcpyAsync((char *)out + f, (const char *)s->ro_buf + f, std::min(kPiece, bytes - f),
+                                    cudaMemcpyDeviceToHost, s->ro_stream));
+    QS_CUDA_TRY(cudaEventRecord(s->ro_done, s->ro_stream));
+    return QS_OK;
+}
+
+extern "C" qs_status qs_state_sync(const qs_state *s)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    DeviceGuard g(s->device);
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (s->ro_stream) QS_CUDA_TRY(cudaStreamSynchronize(s->ro_stream));
+    return QS_OK;
+}
+
 extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
 {
     clear_error();
@@ -390,17 +453,15 @@ extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uin
     if (qs_status st = materialize(s)) return st;
     if (k == 0) return sampler_run(s, 0, seed, nullptr);
     if (is_device_ptr(out)) return sampler_run(s, k, seed, out);
-    uint64_t *buf = nullptr;
-    QS_CUDA_TRY(cudaMallocAsync((void **)&buf, k * sizeof(uint64_t), s->stream));
-    qs_status st = sampler_run(s, k, seed, buf);
-    if (!st) {
-        cudaError_t e = cudaMemcpyAsync(out, buf, k * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) st = set_error(QS_ERR_CUDA, "sample copy: %s", cudaGetErrorString(e));
-    }
-    cudaFreeAsync(buf, s->stream);
-    cudaStreamSynchronize(s->stream);
-    return st;
+    // host output: the search kernel writes page-locked memory directly
+    // (the caller's, or the state's mapped staging, then copied on the host)
+    void *view = pinned_device_view(out), *stage = nullptr;
+    if (!view)
+        if (qs_status st = stage_view(s, k * sizeof(uint64_t), &stage, &view)) return st;
+    if (qs_status st = sampler_run(s, k, seed, (uint64_t *)view)) return st;
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (stage) std::memcpy(out, stage, k * sizeof(uint64_t));
+    return QS_OK;
 }
 
 extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples, uint64_t m,
@@ -416,14 +477,15 @@ extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples
     qs_status st;
     if (is_device_ptr(samples)) {
         st = cross_entropy_run(s, samples, m, &c);
+    } else if (void *view = pinned_device_view(const_cast<uint64_t *>(samples))) {
+        // page-locked host samples are read by the kernel in place
+        st = cross_entropy_run(s, (const uint64_t *)view, m, &c);
     } else {
-        uint64_t *buf = nullptr;
-        QS_CUDA_TRY(cudaMallocAsync((void **)&buf, m * sizeof(uint64_t), s->stream));
-        cudaError_t e = cudaMemcpyAsync(buf, samples, m * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream);
-        st = e == cudaSuccess ? cross_entropy_run(s, buf, m, &c)
-                              : set_error(QS_ERR_CUDA, "sample upload: %s", cudaGetErrorString(e));
-        cudaFreeAsync(buf, s->stream);
-        cudaStreamSynchronize(s->stream);
+        // pageable host samples: copied into the mapped staging on the host
+        void *stage = nullptr, *dv = nullptr;
+        if ((st = stage_view(s, m * sizeof(uint64_t), &stage, &dv))) return st;
+        std::memcpy(stage, samples, m * sizeof(uint64_t));
+        st = cross_entropy_run(s, (const uint64_t *)dv, m, &c);
     }
     if (st) return st;
     const double euler_gamma = 0.57721566490153286061;

@@ -25,10 +25,22 @@ namespace {
 constexpr int kItemTiles = 8;              // tiles per work item of a round
 constexpr uint64_t kStatChunk = 1 << 16;   // amplitudes per statistics item
 
-__global__ void k_batch_basis(float2 *amps, const uint64_t *off, int count)
+// Initial states, one statistics item (<= 2^16 amplitudes of one instance,
+// a multiple of 32 at a 32-amplitude boundary) per block iteration: every
+// amplitude fill[j] (2^(-n/2) where the instance's circuit opens with a
+// Hadamard layer: the uniform state; else 0), then the item's first
+// amplitude first[j] (1 at the start of an instance in |0...0>).
+__global__ void k_batch_init(float2 *amps, const uint64_t *item_off, const uint64_t *item_cnt,
+                             const float *fill, const float *first, int nitems)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) amps[off[i]] = make_float2(1.f, 0.f);
+    for (int j = blockIdx.x; j < nitems; j += gridDim.x) {
+        float4 *a = reinterpret_cast<float4 *>(amps + item_off[j]);
+        const uint64_t units = item_cnt[j] / 2;
+        const float v = fill[j];
+        const float4 u = make_float4(v, 0.f, v, 0.f);
+        for (uint64_t e = threadIdx.x; e < units; e += blockDim.x) a[e] = u;
+        if (threadIdx.x == 0) a[0] = make_float4(first[j], 0.f, v, 0.f);
+    }
 }
 
 uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ULL)
@@ -192,13 +204,20 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     std::vector<Plan> plans(C);
     std::vector<qs_status> st(C, QS_OK);
     std::vector<std::string> msg(C);
+    // an instance whose circuit opens with a Hadamard layer starts from the
+    // uniform state (written by k_batch_init) and plans the rest
+    std::vector<size_t> hl(C);
+    for (int i = 0; i < C; ++i)
+        hl[i] = leading_h_layer(gates + offsets[i], (size_t)(offsets[i + 1] - offsets[i]), b->n[i]);
     const unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
     for (unsigned w = 0; w < nth; ++w)
         pool.emplace_back([&, w]() {
             for (int i = (int)w; i < C; i += (int)nth) {
+                const size_t ng = (size_t)(offsets[i + 1] - offsets[i]) - hl[i];
+                if (ng == 0) continue;
                 PlanParams pp = default_plan_params(b->n[i], QS_C64, nullptr);
-                st[i] = build_plan(pp, gates + offsets[i], (size_t)(offsets[i + 1] - offsets[i]), &plans[i]);
+                st[i] = build_plan(pp, gates + offsets[i] + hl[i], ng, &plans[i]);
                 if (st[i]) msg[i] = last_error_cstr();
             }
         });
@@ -252,15 +271,18 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
         }
     // statistics items
     std::vector<uint64_t> s_off, s_cnt;
-    std::vector<float> s_scale;
+    std::vector<float> s_scale, s_fill, s_first;
     std::vector<int> first_item(C + 1);
     for (int i = 0; i < C; ++i) {
         first_item[i] = (int)s_off.size();
         const uint64_t N = 1ULL << b->n[i];
+        const float v = hl[i] ? (float)std::pow(2.0, -0.5 * b->n[i]) : 0.f;
         for (uint64_t a = 0; a < N; a += kStatChunk) {
             s_off.push_back(b->off[i] + a);
             s_cnt.push_back(std::min<uint64_t>(kStatChunk, N - a));
             s_scale.push_back((float)std::ldexp(1.0, b->n[i]));
+            s_fill.push_back(v);
+            s_first.push_back(hl[i] ? v : (a == 0 ? 1.f : 0.f));
         }
     }
     first_item[C] = (int)s_off.size();
@@ -276,7 +298,9 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     size_t o_ss = align(o_sc + s_cnt.size() * 8);
     size_t o_fi = align(o_ss + s_scale.size() * 4);
     size_t o_io = align(o_fi + first_item.size() * 4);
-    size_t total = align(o_io + b->off.size() * 8);
+    size_t o_vf = align(o_io + b->off.size() * 8);
+    size_t o_v1 = align(o_vf + s_fill.size() * 4);
+    size_t total = align(o_v1 + s_first.size() * 4);
     std::vector<unsigned char> host(total, 0);
     std::memcpy(host.data() + o_pass, passes.data(), passes.size() * sizeof(DevPass));
     std::memcpy(host.data() + o_ph, phases.data(), phases.size() * sizeof(DevPhase));
@@ -287,6 +311,8 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     std::memcpy(host.data() + o_ss, s_scale.data(), s_scale.size() * 4);
     std::memcpy(host.data() + o_fi, first_item.data(), first_item.size() * 4);
     std::memcpy(host.data() + o_io, b->off.data(), b->off.size() * 8);
+    std::memcpy(host.data() + o_vf, s_fill.data(), s_fill.size() * 4);
+    std::memcpy(host.data() + o_v1, s_first.data(), s_first.size() * 4);
     batch_release_plan(b);
     QS_CUDA_TRY(cudaMalloc(&b->dev, total));
     QS_CUDA_TRY(cudaMalloc((void **)&b->part, (size_t)nsi * kStatSums * sizeof(double)));
@@ -298,8 +324,9 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     if (qs_status s0 = batch_kernel_setup()) return s0;
     QS_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     qs_status rs = QS_OK;
-    cudaMemsetAsync(b->amps, 0, b->total * sizeof(float2), b->cap_stream);
-    k_batch_basis<<<(C + 127) / 128, 128, 0, b->cap_stream>>>(b->amps, (const uint64_t *)(D + o_io), C);
+    k_batch_init<<<std::min(nsi, 16 * b->num_sms), 256, 0, b->cap_stream>>>(
+        b->amps, (const uint64_t *)(D + o_so), (const uint64_t *)(D + o_sc), (const float *)(D + o_vf),
+        (const float *)(D + o_v1), nsi);
     for (const Launch &L : launches) {
         rs = launch_batch_round(b->cap_stream, b->num_sms, b->amps, D + o_it + L.first * isz, (int)L.count, L.tbits,
                                 (const DevPass *)(D + o_pass), (const DevPhase *)(D + o_ph),

@@ -64,6 +64,19 @@ void gate_matrix(int kind, double theta, Cplx u[4])
     }
 }
 
+size_t leading_h_layer(const qs_gate *g, size_t ng, int n)
+{
+    if (ng < (size_t)n) return 0;
+    uint64_t seen = 0;
+    for (int i = 0; i < n; ++i) {
+        if (g[i].kind != QS_H) return 0;
+        const uint64_t b = 1ULL << g[i].q0;
+        if (seen & b) return 0;
+        seen |= b;
+    }
+    return (size_t)n;
+}
+
 qs_status validate_gates(int n, const qs_gate *g, size_t ng)
 {
     if (ng && !g) return set_error(QS_ERR_INVALID_ARG, "gates is NULL but ngates = %zu", ng);
@@ -770,8 +783,12 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     pp.k = kTcBits;
     pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
     pp.esz = dt == QS_C128 ? 16 : 8;
-    // a deeper lookahead pays where a pass costs the most
-    if (n >= 32) pp.look_steps = pp.look_top = 64;
+    // a deeper lookahead pays where a pass costs the most (host planning of
+    // the next circuit overlaps the current evolution)
+    if (n >= 32)
+        pp.look_steps = pp.look_top = 64;
+    else if (n >= 28)
+        pp.look_steps = pp.look_top = 16;
     pp.r = std::min(pp.r, pp.t);
     return pp;
 }

@@ -44,6 +44,10 @@ bool gate_is_diagonal(int kind);
 // matrix applied to the target when the control bit is set.
 void gate_matrix(int kind, double theta, Cplx u[4]);
 qs_status validate_gates(int n, const qs_gate *g, size_t ng);
+// n when the gate list opens with H on every qubit (n gates, each qubit
+// once), else 0: on |0...0> that layer is the uniform superposition
+// (Sec. pt, cycle 0), written as one fill instead of a pass.
+size_t leading_h_layer(const qs_gate *g, size_t ng, int n);
 
 // ---------------------------------------------------------------------------
 // Fused-pass plan (built on the host, executed by the fused kernels)
@@ -208,6 +212,20 @@ struct qs_state {
     bool is_zero = false;
     mutable bool zero_pending = false;
     mutable bool escaped = false;
+    // asynchronous host read-out (qs_probabilities_async): the probabilities
+    // are formed in ro_buf on `stream`, then copied to page-locked host memory
+    // on ro_stream; ro_done marks the end of the last copy (the buffer is free)
+    mutable void *ro_buf = nullptr;
+    mutable size_t ro_bytes = 0;
+    mutable cudaStream_t ro_stream = nullptr;
+    mutable cudaEvent_t ro_ready = nullptr, ro_done = nullptr;
+    // page-locked host memory mapped into the device: kernels write small
+    // results (hbox) and host-side sample arrays (stage) there directly, so
+    // no copy-engine transfer is needed and nothing queues behind an
+    // asynchronous read-out still copying
+    void *hbox = nullptr, *hbox_dev = nullptr;
+    mutable void *stage = nullptr, *stage_dev = nullptr;
+    mutable size_t stage_bytes = 0;
 };
 
 namespace qs {
@@ -233,6 +251,15 @@ qs_status adjoint_run(qs_state *s, const qs_gate *g, size_t ng, const uint64_t *
                       uint64_t m, double *grad);
 
 size_t dtype_bytes(qs_dtype dt);
+
+constexpr size_t kHostBoxBytes = 4096;
+// Copies `bytes` (a multiple of 8, at most kHostBoxBytes) of device memory
+// to `host` through the state's mapped host box: a one-block kernel on the
+// state's stream, then a stream synchronisation.
+qs_status read_back(const qs_state *s, void *host, const void *dev, size_t bytes);
+// Page-locked, device-mapped staging of at least `bytes` (grown on demand):
+// host and device addresses of the same memory.
+qs_status stage_view(const qs_state *s, size_t bytes, void **host, void **dev);
 
 // batched ensemble helpers
 constexpr int kStatSums = 12;

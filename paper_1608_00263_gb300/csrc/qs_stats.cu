@@ -233,6 +233,47 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nblocks, int
     }
 }
 
+__global__ void k_read_back(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+qs_status read_back(const qs_state *s, void *host, const void *dev, size_t bytes)
+{
+    if (bytes % 8 || bytes > kHostBoxBytes)
+        return set_error(QS_ERR_INVALID_ARG, "read-back of %zu bytes", bytes);
+    k_read_back<<<1, 64, 0, s->stream>>>((const unsigned long long *)dev, (unsigned long long *)s->hbox_dev,
+                                         (int)(bytes / 8));
+    QS_LAUNCH_CHECK();
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    std::memcpy(host, s->hbox, bytes);
+    return QS_OK;
+}
+
+qs_status stage_view(const qs_state *s, size_t bytes, void **host, void **dev)
+{
+    if (s->stage_bytes < bytes) {
+        if (s->stage) cudaFreeHost(s->stage);
+        s->stage = s->stage_dev = nullptr;
+        s->stage_bytes = 0;
+        const size_t cap = std::max(bytes, (size_t)1 << 20);
+        void *h = nullptr, *d = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, cap, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&d, h, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (h) cudaFreeHost(h);
+            return set_error(QS_ERR_OOM, "host staging of %zu bytes: %s", cap, cudaGetErrorString(e));
+        }
+        s->stage = h;
+        s->stage_dev = d;
+        s->stage_bytes = cap;
+    }
+    *host = s->stage;
+    *dev = s->stage_dev;
+    return QS_OK;
+}
+
 qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *entropy,
                         double *uniform_ce, double *norm)
 {
@@ -256,8 +297,7 @@ qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *en
     k_sum_partials<<<1, 32, 0, s->stream>>>(part, grid, kStatAcc, fin);
     QS_LAUNCH_CHECK();
     double h[kStatAcc];
-    QS_CUDA_TRY(cudaMemcpyAsync(h, fin, sizeof h, cudaMemcpyDeviceToHost, s->stream));
-    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (qs_status st = read_back(s, h, fin, sizeof h)) return st;
     // Statistics of the normalised distribution p / S, S = sum p: the
     // arithmetic of the evolution leaves |S - 1| at the rounding level
     // (systematic for FP32: rounded phase constants have modulus below 1),
@@ -606,11 +646,9 @@ qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *de
     k_scan_totals<<<1, kScanThreads, 0, s->stream>>>(btot, (int)nblk);
     k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, s->stream>>>(csum, nchunks, btot);
     double total = 0;
-    cudaError_t e = cudaMemcpyAsync(&total, csum + nchunks - 1, sizeof(double),
-                                    cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) {
-        st = set_error(QS_ERR_CUDA, "sampler scan failed: %s", cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
+    if (qs_status rb = read_back(s, &total, csum + nchunks - 1, sizeof(double))) {
+        st = rb;
     } else if (!(total > 0) || !std::isfinite(total)) {
         st = set_error(QS_ERR_INVALID_ARG, "state has zero or non-finite norm (%g)", total);
     } else if (k > 0) {
@@ -945,9 +983,8 @@ qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples, uint
     QS_LAUNCH_CHECK();
     double sum = 0;
     unsigned long long nbad = 0;
-    QS_CUDA_TRY(cudaMemcpyAsync(&sum, part + grid, sizeof sum, cudaMemcpyDeviceToHost, s->stream));
-    QS_CUDA_TRY(cudaMemcpyAsync(&nbad, bad, sizeof nbad, cudaMemcpyDeviceToHost, s->stream));
-    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (qs_status st = read_back(s, &sum, part + grid, sizeof sum)) return st;
+    if (qs_status st = read_back(s, &nbad, bad, sizeof nbad)) return st;
     if (nbad) return set_error(QS_ERR_INVALID_ARG, "%llu sample indices >= 2^n", nbad);
     *ce = sum / (double)m;
     return QS_OK;

@@ -59,6 +59,32 @@ def test_small_ensemble_matches_oracle():
         qs.qs_batch_destroy(b)
 
 
+def test_batch_initial_states_with_and_without_hadamard_layer():
+    """Instances opening with H on every qubit start from the uniform state
+    (Sec. pt, cycle 0) and plan the rest; the others start from |0...0>:
+    a list that is only the layer, a layer missing one qubit, a layer after a
+    T gate, a layer with a repeated qubit, and the empty list."""
+    n = 12
+    g = qs.qs_circuit_generate(3, 4, 10, 3)
+    assert np.all(g["kind"][:n] == qs.QS_H)
+    t0 = g[n:n + 1].copy()
+    t0["kind"], t0["q0"], t0["theta"] = qs.QS_T, 5, 0.0
+    dup = g.copy()
+    dup["q0"][1] = dup["q0"][0]
+    lists = [g, g[:n], g[1:], np.concatenate([t0, g]), dup, g[:0]]
+    b = qs.qs_batch_create([n] * len(lists))
+    try:
+        for rep in range(2):                                       # capture, then replay
+            qs.qs_batch_apply(b, lists)
+            for i, gl in enumerate(lists):
+                ref = O.simulate(n, gl)
+                psi = device_state(b, i, n)
+                err = np.linalg.norm(psi.astype(complex) - ref) / np.linalg.norm(ref)
+                assert err < 1e-5, (rep, i, err)
+    finally:
+        qs.qs_batch_destroy(b)
+
+
 def test_ensemble_4096():
     import torch
     torch.cuda.empty_cache()

@@ -238,6 +238,49 @@ def test_probabilities(state20):
     assert np.array_equal(pinned32.numpy(), host32)
 
 
+def test_probabilities_async_overlaps_next_circuit():
+    """Asynchronous read-out to page-locked host memory: each buffer holds the
+    probabilities of the state at its call, although the next circuit runs
+    while the copy is in flight; a synchronous read-out into the same buffer
+    lands after an earlier asynchronous one."""
+    import torch
+    n = 20
+    g1, g2 = qs.qs_circuit_generate(4, 5, 25, 1), qs.qs_circuit_generate(4, 5, 25, 2)
+    p1, p2 = O.probabilities(O.simulate(n, g1)), O.probabilities(O.simulate(n, g2))
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        a = torch.full((1 << n,), -1.0, dtype=torch.float64).pin_memory()
+        b = torch.full((1 << n,), -1.0, dtype=torch.float32).pin_memory()
+        qs.qs_apply_circuit(h, g1)
+        qs.qs_probabilities_async(h, a, fp64=True)
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g2)
+        qs.qs_probabilities_async(h, b, fp64=False)
+        qs.qs_state_sync(h)
+        assert np.sum(np.abs(a.numpy() - p1)) < 2e-5
+        assert np.sum(np.abs(b.numpy() - p2)) < 2e-5
+        ref32 = np.empty(1 << n, dtype=np.float32)
+        qs.qs_probabilities(h, ref32, fp64=False)
+        assert np.array_equal(b.numpy(), ref32)
+        # device and pageable outputs behave as qs_probabilities
+        d = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        qs.qs_probabilities_async(h, d, fp64=True)
+        pg = np.empty(1 << n, dtype=np.float64)
+        qs.qs_probabilities_async(h, pg, fp64=True)
+        qs.qs_state_sync(h)
+        assert np.array_equal(d.cpu().numpy(), pg)
+        assert np.allclose(pg, ref32, rtol=2.0 ** -22, atol=0)
+        # async (state of g2) then, after g1, sync into the same buffer
+        qs.qs_probabilities_async(h, a, fp64=True)
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g1)
+        qs.qs_probabilities(h, a, fp64=True)
+        qs.qs_state_sync(h)
+        assert np.sum(np.abs(a.numpy() - p1)) < 2e-5
+    finally:
+        qs.qs_state_destroy(h)
+
+
 def test_pt_moments(state20):
     dtype, h, ref, p = state20
     r = qs.qs_pt_moments(h, 10)
