@@ -417,14 +417,18 @@ struct PGate {
 };
 
 // Returns the indices (in order) of gates applicable with the local set
-// `local` (bitmask over qubits), among gates not yet done.
-// The scan stops once every qubit of `allq` is blocked: no later gate can
-// then apply.
+// `local` (bitmask over qubits), among gates not yet done.  A gate left
+// pending blocks its qubits for the later gates that do not commute with it:
+// a non-diagonal gate for every later gate on its qubit, a diagonal gate only
+// for later non-diagonal gates (diagonal gates commute with each other).
+// The scan stops once every qubit of `allq` is blocked for all gates: no
+// later gate can then apply.
 static void collect(const std::vector<PGate> &g, const std::vector<int> &cand,
                     const std::vector<char> &done, uint64_t local,
                     std::vector<int> *out, int *count, uint64_t allq = ~0ULL)
 {
-    uint64_t blocked = 0;
+    uint64_t blocked = 0;      // a non-diagonal gate is pending on the qubit
+    uint64_t blocked_nd = 0;   // a diagonal gate is pending on the qubit
     int cnt = 0;
     if (out) out->clear();
     for (int i : cand) {
@@ -432,10 +436,12 @@ static void collect(const std::vector<PGate> &g, const std::vector<int> &cand,
         if (blocked == allq) break;
         const PGate &x = g[i];
         uint64_t qm = (1ULL << x.q0) | (x.two ? (1ULL << x.q1) : 0);
-        bool ok = !(qm & blocked) && (x.diag || (qm & ~local) == 0);
+        bool ok = !(qm & blocked) && (x.diag || ((qm & ~local) == 0 && !(qm & blocked_nd)));
         if (ok) {
             ++cnt;
             if (out) out->push_back(i);
+        } else if (x.diag) {
+            blocked_nd |= qm;
         } else {
             blocked |= qm;
         }
@@ -455,24 +461,40 @@ static void first_pending(const std::vector<PGate> &g, const std::vector<int> &c
     }
 }
 
+// Pending diagonal gates per qubit.
+static void diag_pending(const std::vector<PGate> &g, const std::vector<int> &cand,
+                         const std::vector<char> &done, int n, std::vector<int> *cnt)
+{
+    cnt->assign(n, 0);
+    for (int i : cand) {
+        if (done[i] || !g[i].diag) continue;
+        ++(*cnt)[g[i].q0];
+        if (g[i].two) ++(*cnt)[g[i].q1];
+    }
+}
+
 // Greedy choice of `want` qubits added to `base` from `pool`, maximising the
 // number of applicable gates; ties go to the qubit whose next non-diagonal
-// gate is earliest.
+// gate is earliest, then to the qubit with the fewest pending diagonal gates
+// (a register phase applies those to whole threads when their qubits are
+// not register bits).
 static uint64_t choose_local(const std::vector<PGate> &g, const std::vector<int> &cand,
                              const std::vector<char> &done, int n, uint64_t base,
                              uint64_t pool, int want, uint64_t allq = ~0ULL)
 {
-    std::vector<int> first;
+    std::vector<int> first, ndiag;
     first_pending(g, cand, done, n, &first);
+    diag_pending(g, cand, done, n, &ndiag);
     uint64_t local = base;
     for (int step = 0; step < want; ++step) {
-        int best_q = -1, best_cnt = -1, best_first = 1 << 30;
+        int best_q = -1, best_cnt = -1, best_first = 1 << 30, best_diag = 1 << 30;
         for (int q = 0; q < n; ++q) {
             if (!((pool >> q) & 1) || ((local >> q) & 1)) continue;
             int cnt;
             collect(g, cand, done, local | (1ULL << q), nullptr, &cnt, allq);
-            if (cnt > best_cnt || (cnt == best_cnt && first[q] < best_first)) {
-                best_q = q; best_cnt = cnt; best_first = first[q];
+            if (cnt > best_cnt || (cnt == best_cnt && (first[q] < best_first ||
+                                                       (first[q] == best_first && ndiag[q] < best_diag)))) {
+                best_q = q; best_cnt = cnt; best_first = first[q]; best_diag = ndiag[q];
             }
         }
         if (best_q < 0) break;
@@ -485,9 +507,10 @@ static uint64_t choose_local(const std::vector<PGate> &g, const std::vector<int>
 // additions, the `look_top` candidates with the most applicable gates are
 // each completed greedily to the full tile and scored by the gates the
 // completed tile applies; the remaining additions are greedy.  Fewer passes
-// than the plain greedy choice on the paper's circuits: 4 % at 30 qubits
-// (2 steps, 6 candidates, a few milliseconds), 14 % at 34 qubits (every
-// step and candidate, ~0.2 s of host time against ~2 s of evolution).
+// than the plain greedy choice on the paper's circuits: 10 % at 30 qubits
+// (8 steps, 8 candidates, ~40 ms of host time against ~80 ms of evolution),
+// 14 % at 34 qubits (every step and candidate, ~0.2 s against ~1.4 s).
+// Host planning of the next circuit overlaps the current evolution.
 static uint64_t choose_tile(const std::vector<PGate> &g, const std::vector<int> &cand,
                             const std::vector<char> &done, int n, uint64_t base, uint64_t pool,
                             int want, uint64_t allq, int look_steps, int look_top)
@@ -788,7 +811,7 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     if (n >= 32)
         pp.look_steps = pp.look_top = 64;
     else if (n >= 28)
-        pp.look_steps = pp.look_top = 16;
+        pp.look_steps = pp.look_top = 8;
     pp.r = std::min(pp.r, pp.t);
     return pp;
 }
