@@ -149,10 +149,11 @@ class ClockSampler:
 
 def kernel_launches_per_step(passes):
     # fused passes + uniform fill (the leading Hadamard layer on the reset
-    # state) + probabilities (1) + statistics (2 + read-back) + sampler (chunk
-    # sums, 3 scan kernels, read-back, search = 6) + cross entropy (kernel,
-    # final sum, 2 read-backs = 4)
-    return passes + 1 + 1 + 3 + 6 + 4
+    # state) + fused read-out (probabilities, statistics partials and chunk
+    # sums: 1) + statistics (final sum, read-back = 2) + sampler (3 scan
+    # kernels, read-back, search = 5) + cross entropy (kernel, final sum,
+    # 2 read-backs = 4)
+    return passes + 1 + 1 + 2 + 5 + 4
 
 
 def leading_h_layer(qs, g, n):
@@ -271,41 +272,50 @@ def run_ours(args, rank, world, local):
     traffic = load_traffic(args.mode, n)
 
     # ---- e2e: same steps through the public API with host buffers ----
-    # Every step's probabilities reach page-locked host memory (two buffers,
-    # alternating): the copy engine moves step i's while step i+1's circuit
-    # evolves; the timed region ends when the last copy has landed.
     probs_host = [torch.empty(1 << n, dtype=probs.dtype, pin_memory=True) for _ in range(2)]
     samples_host = np.empty(m, dtype=np.uint64)
-    h2d = d2h = 0
-    torch.cuda.synchronize()
-    gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, base_seed + 10_000, dead)
-    qs.qs_prepare_circuit(h, gates, mode=mode)
-    t0 = None
-    for i in range(args.warmup + args.steps):
-        if i == args.warmup:
-            # untimed warm-up steps (read-out buffers allocated) end here
-            qs.qs_state_sync(h)
-            torch.cuda.synchronize()
-            h2d = d2h = 0
-            t0 = time.perf_counter()
-        seed = base_seed + 10_000 + i
-        qs.qs_state_reset(h)
-        qs.qs_apply_circuit(h, gates, mode=mode)
-        # the next circuit is generated and planned while this one evolves
-        nxt = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed + 1, dead)
-        qs.qs_prepare_circuit(h, nxt, mode=mode)
-        qs.qs_probabilities_async(h, probs_host[i % 2], fp64=W["fp64_probs"])
-        qs.qs_pt_moments(h, 10)
-        qs.qs_sample(h, m, 1000 + seed, out=samples_host)
-        qs.qs_cross_entropy(h, samples_host)
-        h2d += gates.nbytes + samples_host.nbytes
-        d2h += probs_host[0].numel() * probs_host[0].element_size() + samples_host.nbytes + 8 * 14
-        gates = nxt
-    qs.qs_state_sync(h)
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0
-    e2e_ms = job_max_ms(e2e_ms, dist, "cuda")
-    e2e_value = job_value(depth * args.steps, world, e2e_ms)
+
+    def e2e_run(asynchronous, seed0):
+        """W untimed + K timed steps through the public API with host buffers:
+        the gate list in, the probabilities and the samples out each step.
+        Synchronous: the read-out kernel writes the page-locked buffer
+        directly.  Asynchronous: qs_probabilities_async, the copy engine moves
+        step i's probabilities (two buffers, alternating) while step i+1's
+        circuit evolves; the timed region ends when the last copy has landed."""
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed0, dead)
+        qs.qs_prepare_circuit(h, gates, mode=mode)
+        t0 = None
+        for i in range(args.warmup + args.steps):
+            if i == args.warmup:
+                qs.qs_state_sync(h)
+                torch.cuda.synchronize()
+                h2d = d2h = 0
+                t0 = time.perf_counter()
+            seed = seed0 + i
+            qs.qs_state_reset(h)
+            qs.qs_apply_circuit(h, gates, mode=mode)
+            # the next circuit is generated and planned while this one evolves
+            nxt = qs.qs_circuit_generate(W["rows"], W["cols"], depth, seed + 1, dead)
+            qs.qs_prepare_circuit(h, nxt, mode=mode)
+            if asynchronous:
+                qs.qs_probabilities_async(h, probs_host[i % 2], fp64=W["fp64_probs"])
+            else:
+                qs.qs_probabilities(h, probs_host[0], fp64=W["fp64_probs"])
+            qs.qs_pt_moments(h, 10)
+            qs.qs_sample(h, m, 1000 + seed, out=samples_host)
+            qs.qs_cross_entropy(h, samples_host)
+            h2d += gates.nbytes + samples_host.nbytes
+            d2h += probs_host[0].numel() * probs_host[0].element_size() + samples_host.nbytes + 8 * 14
+            gates = nxt
+        qs.qs_state_sync(h)
+        torch.cuda.synchronize()
+        ms = job_max_ms((time.perf_counter() - t0) * 1000.0, dist, "cuda")
+        return job_value(depth * args.steps, world, ms), h2d, d2h
+
+    e2e_value, h2d, d2h = e2e_run(False, base_seed + 10_000)
+    e2e_async_value, _, _ = e2e_run(True, base_seed + 20_000)
 
     # ---- one-off comparison of the forms (apply only, untimed region) ----
     compare = {}
@@ -383,7 +393,8 @@ def run_ours(args, rank, world, local):
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                      "bytes_per_launch": pass_bytes, "avg_launch_ms": round(avg_pass_ms, 4)},
         "e2e": {"value": round(e2e_value, 3), "unit": "cycles/s",
-                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
+                "async_readout_value": round(e2e_async_value, 3)},
         "gpu_launches": sum(kernel_launches_per_step(p) for p in passes_seen),
         "clocks": clk,
         "last_step": {k: round(v, 6) for k, v in results["last"].items()},

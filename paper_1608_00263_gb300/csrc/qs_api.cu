@@ -40,6 +40,7 @@ qs_status materialize(const qs_state *s)
 {
     if (!s->zero_pending) return QS_OK;
     s->zero_pending = false;
+    ++s->version;
     return launch_init_zero(const_cast<qs_state *>(s));
 }
 
@@ -117,6 +118,7 @@ void free_state(qs_state *s)
     if (s->ws_f64) cudaFree(s->ws_f64);
     if (s->ws_u64) cudaFree(s->ws_u64);
     if (s->hbox) cudaFreeHost(s->hbox);
+    if (s->rc_buf) cudaFree(s->rc_buf);
     if (s->stage) cudaFreeHost(s->stage);
     for (DevicePlanSlot &c : s->plan_cache.slot) {
         if (c.dev) cudaFree(c.dev);
@@ -200,6 +202,7 @@ extern "C" qs_status qs_state_reset(qs_state *s)
     if (qs_status st = check_state(s)) return st;
     DeviceGuard g(s->device);
     s->is_zero = true;
+    ++s->version;
     if (s->escaped) {
         s->zero_pending = false;
         return launch_init_zero(s);
@@ -292,6 +295,7 @@ extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t 
         return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
     if (ngates == 0) return QS_OK;
     DeviceGuard g(s->device);
+    ++s->version;
     // Sec. pt, cycle 0: on |0...0> a leading layer of Hadamards on every
     // qubit gives the uniform superposition, written in one pass
     if (s->is_zero && !s->escaped) {
@@ -528,6 +532,7 @@ extern "C" qs_status qs_state_copy_in(qs_state *s, const void *host_amps)
     const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
     s->zero_pending = false;
     s->is_zero = false;
+    ++s->version;
     QS_CUDA_TRY(cudaMemcpyAsync(s->amps, host_amps, bytes, cudaMemcpyDefault, s->stream));
     QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return QS_OK;
@@ -561,6 +566,7 @@ extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size
     double ce = 0;
     qs_status st = cross_entropy_run(s, dx, m, &ce);   // also range-checks the samples
     if (!st) st = adjoint_run(s, gates, ngates, dx, m, grad);
+    ++s->version;   // the reverse sweep leaves the state un-applied
     if (buf) cudaFreeAsync(buf, s->stream);
     cudaStreamSynchronize(s->stream);
     if (!st && loss) *loss = ce;

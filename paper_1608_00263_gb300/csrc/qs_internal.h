@@ -226,6 +226,15 @@ struct qs_state {
     void *hbox = nullptr, *hbox_dev = nullptr;
     mutable void *stage = nullptr, *stage_dev = nullptr;
     mutable size_t stage_bytes = 0;
+    // read-out cache (complex64): statistics partials and sampler chunk sums
+    // formed by the fused read-out pass, valid while `version` (bumped by
+    // every change of the amplitudes) equals rc_version and the caller cannot
+    // reach the memory
+    mutable uint64_t version = 0;
+    mutable double *rc_buf = nullptr;
+    mutable size_t rc_doubles = 0;
+    mutable uint64_t rc_version = ~0ULL;
+    mutable int rc_flags = 0;
 };
 
 namespace qs {
@@ -257,6 +266,17 @@ constexpr size_t kHostBoxBytes = 4096;
 // to `host` through the state's mapped host box: a one-block kernel on the
 // state's stream, then a stream synchronisation.
 qs_status read_back(const qs_state *s, void *host, const void *dev, size_t bytes);
+
+// Fused read-out of a complex64 state (one read): p = |psi|^2 into `out`
+// (out_kind 1: FP32, 2: FP64, 0: none; device-accessible, 16-byte aligned),
+// the statistics partials and the sampler's chunk sums into the read-out
+// cache, which it marks valid for the current state.
+constexpr int kReadoutStats = 1, kReadoutChunks = 2, kReadoutScanned = 4;
+qs_status readout_c64(const qs_state *s, void *out, int out_kind);
+bool readout_cached(const qs_state *s, int flag);
+int readout_grid(const qs_state *s);
+double *readout_part(const qs_state *s);
+double *readout_csum(const qs_state *s);
 // Page-locked, device-mapped staging of at least `bytes` (grown on demand):
 // host and device addresses of the same memory.
 qs_status stage_view(const qs_state *s, size_t bytes, void **host, void **dev);

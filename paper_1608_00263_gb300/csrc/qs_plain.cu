@@ -131,6 +131,7 @@ __global__ void k_set_basis0(typename V2T<R>::T *a)
 
 qs_status launch_init_zero(qs_state *s)
 {
+    ++s->version;
     const size_t bytes = (size_t(1) << s->n) * dtype_bytes(s->dt);
     QS_CUDA_TRY(cudaMemsetAsync(s->amps, 0, bytes, s->stream));
     if (s->dt == QS_C64)
@@ -159,6 +160,7 @@ __global__ void k_fill_uniform(float4 *a, uint64_t units, R v)
 
 qs_status launch_init_uniform(qs_state *s)
 {
+    ++s->version;
     const uint64_t N = 1ULL << s->n;
     const double v = std::pow(2.0, -0.5 * s->n);
     const int th = 256;

@@ -92,6 +92,8 @@ qs_status launch_probabilities(const qs_state *s, void *out, int fp64, uint64_t 
                                uint64_t count)
 {
     const int th = 256;
+    if (s->dt == QS_C64 && first == 0 && count == (1ULL << s->n) && !((uintptr_t)out & 15))
+        return readout_c64(s, out, fp64 ? 2 : 1);
     if (s->dt == QS_C64) {
         const bool pairs = !(first & 1) && !(count & 1) && !((uintptr_t)out & (fp64 ? 15 : 7));
         if (pairs) {
@@ -160,53 +162,20 @@ __device__ __forceinline__ void stat_terms(T y, T (&c)[kStatAcc])
     }
 }
 
-// complex64: FP32 per element and per 128-element partial, FP64 across.
-// Each step issues eight 16-byte loads before using them (enough bytes in
-// flight per SM to keep HBM busy).  Elements with y^10 beyond the FP32
-// range (y > 2^12, vanishingly rare) go straight to the FP64 accumulators.
-__device__ __forceinline__ void stat_pair(const float4 v, float scaleN, float (&c)[kStatAcc],
-                                          double (&acc)[kStatAcc])
+// The same for two probabilities already formed in FP32 (the second one
+// only if `two`).  Beyond the FP32 range of y^10 the terms are formed from
+// the FP32 probability in FP64.
+__device__ __forceinline__ void stat_pair_p(float p0, float p1, bool two, float scaleN, float (&c)[kStatAcc],
+                                            double (&acc)[kStatAcc])
 {
-    const float y0 = (v.x * v.x + v.y * v.y) * scaleN;
-    const float y1 = (v.z * v.z + v.w * v.w) * scaleN;
+    const float y0 = p0 * scaleN, y1 = two ? p1 * scaleN : 0.f;
     if (y0 > 4096.f || y1 > 4096.f) {
-        const double d0 = ((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN;
-        const double d1 = ((double)v.z * v.z + (double)v.w * v.w) * (double)scaleN;
-        stat_terms<double>(d0, acc);
-        stat_terms<double>(d1, acc);
+        stat_terms<double>((double)p0 * (double)scaleN, acc);
+        if (two) stat_terms<double>((double)p1 * (double)scaleN, acc);
     } else {
         stat_terms<float>(y0, c);
-        stat_terms<float>(y1, c);
+        if (two) stat_terms<float>(y1, c);
     }
-}
-
-__global__ void __launch_bounds__(kStatThreads)
-k_stats_c64(const float4 *__restrict__ a4, uint64_t nquads, float scaleN, double *__restrict__ part)
-{
-    double acc[kStatAcc];
-#pragma unroll
-    for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    while (w < nquads) {
-        float c[kStatAcc];
-#pragma unroll
-        for (int k = 0; k < kStatAcc; ++k) c[k] = 0.f;
-        for (int it = 0; it < 8 && w < nquads; ++it, w += 8 * stride) {
-            float4 v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint64_t wu = w + (uint64_t)u * stride;
-                v[u] = wu < nquads ? a4[wu] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (w + (uint64_t)u * stride < nquads) stat_pair(v[u], scaleN, c, acc);
-        }
-#pragma unroll
-        for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)c[k];
-    }
-    block_sum_store<kStatAcc>(acc, part + (size_t)blockIdx.x * kStatAcc);
 }
 
 __global__ void __launch_bounds__(kStatThreads)
@@ -280,19 +249,19 @@ qs_status stats_moments(const qs_state *s, int kmax, double *moments, double *en
     const uint64_t N = 1ULL << s->n;
     int grid;
     double *part = s->ws_f64;
-    if (s->dt == QS_C64 && N >= 2) {
-        grid = grid_for(N / 2, kStatThreads, s->num_sms, 8);
-        k_stats_c64<<<grid, kStatThreads, 0, s->stream>>>((const float4 *)s->amps, N / 2,
-                                                           (float)std::ldexp(1.0, s->n), part);
-    } else if (s->dt == QS_C64) {
-        // a single complex64 amplitude: view it as a one-element FP64 problem
-        return set_error(QS_ERR_UNSUPPORTED, "statistics need n >= 1");
+    if (s->dt == QS_C64) {
+        // the read-out cache holds the partials of the current state, or a
+        // fused read-out pass forms them (with the sampler's chunk sums)
+        if (!readout_cached(s, kReadoutStats))
+            if (qs_status st = readout_c64(s, nullptr, 0)) return st;
+        part = readout_part(s);
+        grid = readout_grid(s);
     } else {
         grid = grid_for(N, kStatThreads, s->num_sms, 4);
         k_stats_c128<<<grid, kStatThreads, 0, s->stream>>>((const double2 *)s->amps, N,
                                                             std::ldexp(1.0, s->n), part);
+        QS_LAUNCH_CHECK();
     }
-    QS_LAUNCH_CHECK();
     double *fin = part + (size_t)grid * kStatAcc;
     k_sum_partials<<<1, 32, 0, s->stream>>>(part, grid, kStatAcc, fin);
     QS_LAUNCH_CHECK();
@@ -422,7 +391,8 @@ __device__ __forceinline__ void lane_probs(const typename V2T<R>::T *a, uint64_t
         uint64_t idx = base + i;
         if (idx < N) {
             auto v = a[idx];
-            p[i] = v.x * v.x + v.y * v.y;
+            if constexpr (sizeof(R) == 4) p[i] = prob32(v);
+            else p[i] = v.x * v.x + v.y * v.y;
         } else {
             p[i] = (R)0;
         }
@@ -626,8 +596,185 @@ __global__ void k_sample_search(const typename V2T<R>::T *__restrict__ a, uint64
     }
 }
 
+// ---------------------------------------------------------------------------
+// fused read-out of a complex64 state
+//
+// One warp per 256-amplitude chunk (lane l: amplitudes 8l .. 8l+7, four
+// 16-byte loads), one read of the state for three results: p = |psi|^2 (FP32,
+// or widened exactly to FP64; optional), the chunk sums of the sampler (the
+// lane totals and FP32 warp scan of lane_probs / chunk_scan, so the search
+// kernel's in-chunk prefixes agree with them) and the statistics partials of
+// each block (per-lane FP32 over eight chunks, then FP64, fixed order).  The
+// statistics and chunk sums are the same whether or not p is written.
+// ---------------------------------------------------------------------------
+template <int OUT>   // 0: no p, 1: FP32 p, 2: FP64 p
+__global__ void __launch_bounds__(kStatThreads, 3)
+k_readout_c64(const float2 *__restrict__ a, uint64_t N, uint64_t nchunks, float scaleN, void *__restrict__ out,
+              double *__restrict__ csum, double *__restrict__ part)
+{
+    __shared__ __align__(16) float stage_all[kStatThreads / 32][kChunk];
+    float *stage = stage_all[threadIdx.x >> 5];
+    double acc[kStatAcc];
+#pragma unroll
+    for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    while (c < nchunks) {
+        float cf[kStatAcc];
+#pragma unroll
+        for (int k = 0; k < kStatAcc; ++k) cf[k] = 0.f;
+        for (int it = 0; it < 8 && c < nchunks; ++it, c += warps) {
+            const uint64_t base = c * kChunk + (uint64_t)lane * 8;
+            float p[8];
+            if ((c + 1) * kChunk <= N) {   // a whole chunk: the same branch for all lanes of the warp
+                const float4 *src = reinterpret_cast<const float4 *>(a + base);
+                float4 v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = src[i];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    p[2 * i] = prob32(make_float2(v[i].x, v[i].y));
+                    p[2 * i + 1] = prob32(make_float2(v[i].z, v[i].w));
+                }
+                if constexpr (OUT != 0) {
+                    // through shared memory, so that each store instruction
+                    // writes 32 consecutive 16-byte units (whole lines, also
+                    // when `out` is page-locked host memory)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) stage[lane * 8 + i] = p[i];
+                    __syncwarp();
+                    const float4 *st4 = reinterpret_cast<const float4 *>(stage);
+                    if constexpr (OUT == 2) {
+                        double2 *o = reinterpret_cast<double2 *>(static_cast<double *>(out) + c * kChunk);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float2 q = reinterpret_cast<const float2 *>(stage)[k * 32 + lane];
+                            o[k * 32 + lane] = make_double2(widen_f32(q.x), widen_f32(q.y));
+                        }
+                    } else {
+                        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + c * kChunk);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) o[k * 32 + lane] = st4[k * 32 + lane];
+                    }
+                    __syncwarp();
+                }
+            } else {
+                // a state of fewer than 256 amplitudes (n < 8): one partial chunk
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    p[i] = base + i < N ? prob32(a[base + i]) : 0.f;
+                    if (base + i < N) {
+                        if constexpr (OUT == 2) static_cast<double *>(out)[base + i] = widen_f32(p[i]);
+                        else if constexpr (OUT == 1) static_cast<float *>(out)[base + i] = p[i];
+                    }
+                }
+            }
+            double incl, excl;
+            chunk_scan(lane_total<float>(p), incl, excl);
+            if (lane == 31) csum[c] = incl;
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                if (base + i < N)
+                    stat_pair_p(p[i], p[i + 1], base + i + 1 < N, scaleN, cf, acc);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)cf[k];
+    }
+    block_sum_store<kStatAcc>(acc, part + (size_t)blockIdx.x * kStatAcc);
+}
+
+int readout_grid(const qs_state *s)
+{
+    const uint64_t nchunks = ((1ULL << s->n) + kChunk - 1) / kChunk;
+    return grid_for(nchunks * 32, kStatThreads, s->num_sms, 3);
+}
+
+// Device buffers of the read-out cache: statistics partials (+ their sum)
+// and chunk sums (+ the scan's block totals).
+static qs_status readout_buffers(const qs_state *s)
+{
+    const uint64_t nchunks = ((1ULL << s->n) + kChunk - 1) / kChunk;
+    const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
+    const size_t want = ((size_t)readout_grid(s) + 1) * kStatAcc + nchunks + nblk + 1;
+    if (s->rc_buf && s->rc_doubles >= want) return QS_OK;
+    if (s->rc_buf) cudaFree(s->rc_buf);
+    s->rc_buf = nullptr;
+    s->rc_doubles = 0;
+    cudaError_t e = cudaMalloc((void **)&s->rc_buf, want * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->rc_buf = nullptr;
+        return set_error(QS_ERR_OOM, "read-out cache of %zu doubles: %s", want, cudaGetErrorString(e));
+    }
+    s->rc_doubles = want;
+    return QS_OK;
+}
+
+double *readout_part(const qs_state *s) { return s->rc_buf; }
+double *readout_csum(const qs_state *s) { return s->rc_buf + ((size_t)readout_grid(s) + 1) * kStatAcc; }
+
+qs_status readout_c64(const qs_state *s, void *out, int out_kind)
+{
+    if (qs_status st = readout_buffers(s)) return st;
+    const uint64_t N = 1ULL << s->n;
+    const uint64_t nchunks = (N + kChunk - 1) / kChunk;
+    const int grid = readout_grid(s);
+    const float scaleN = (float)std::ldexp(1.0, s->n);
+    const float2 *a = (const float2 *)s->amps;
+    if (out_kind == 2)
+        k_readout_c64<2><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, readout_csum(s), readout_part(s));
+    else if (out_kind == 1)
+        k_readout_c64<1><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, readout_csum(s), readout_part(s));
+    else
+        k_readout_c64<0><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, nullptr, readout_csum(s),
+                                                                readout_part(s));
+    QS_LAUNCH_CHECK();
+    s->rc_version = s->version;
+    s->rc_flags = kReadoutStats | kReadoutChunks;
+    return QS_OK;
+}
+
+bool readout_cached(const qs_state *s, int flag)
+{
+    return !s->escaped && s->rc_buf && s->rc_version == s->version && (s->rc_flags & flag);
+}
+
+// complex64: the chunk sums come from the read-out cache (a fused read-out
+// pass when it holds none for the current state) and are scanned in place
+// once; later samples of the same state reuse the scanned offsets.
+static qs_status sampler_run_c64(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *dev_out)
+{
+    const uint64_t N = 1ULL << s->n;
+    const uint64_t nchunks = (N + kChunk - 1) / kChunk;
+    const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
+    if (!readout_cached(s, kReadoutChunks))
+        if (qs_status st = readout_c64(s, nullptr, 0)) return st;
+    double *csum = readout_csum(s), *btot = csum + nchunks;
+    if (!(s->rc_flags & kReadoutScanned)) {
+        k_scan_block_totals<<<(unsigned)nblk, kScanThreads, 0, s->stream>>>(csum, nchunks, btot);
+        k_scan_totals<<<1, kScanThreads, 0, s->stream>>>(btot, (int)nblk);
+        k_scan_apply<<<(unsigned)nblk, kScanThreads, 0, s->stream>>>(csum, nchunks, btot);
+        QS_LAUNCH_CHECK();
+        s->rc_flags |= kReadoutScanned;
+    }
+    double total = 0;
+    if (qs_status rb = read_back(s, &total, csum + nchunks - 1, sizeof(double))) return rb;
+    if (!(total > 0) || !std::isfinite(total))
+        return set_error(QS_ERR_INVALID_ARG, "state has zero or non-finite norm (%g)", total);
+    if (k > 0) {
+        const int th = 256;
+        const int g2 = grid_for((k + 31) / 32 * 32, th, s->num_sms, 16);
+        k_sample_search<float><<<g2, th, 0, s->stream>>>((const float2 *)s->amps, N, nchunks, csum, k, seed, dev_out);
+        QS_LAUNCH_CHECK();
+    }
+    return QS_OK;
+}
+
 qs_status sampler_run(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *dev_out)
 {
+    if (s->dt == QS_C64) return sampler_run_c64(s, k, seed, dev_out);
     const uint64_t N = 1ULL << s->n;
     const uint64_t nchunks = (N + kChunk - 1) / kChunk;
     const uint64_t nblk = (nchunks + kScanSeg - 1) / kScanSeg;
