@@ -178,6 +178,28 @@ def test_plan_semantics_random_gates(emulator, n, t, r, c):
     assert passes >= 1
 
 
+@pytest.mark.parametrize("n,t,r,c,seed", [(10, 6, 4, 2, 0), (12, 7, 5, 3, 1), (9, 5, 3, 0, 2), (13, 8, 5, 5, 3)])
+def test_plan_semantics_diagonal_heavy(emulator, n, t, r, c, seed):
+    """Mostly diagonal gates: a pending diagonal gate holds back only later
+    non-diagonal gates on its qubits, so diagonal gates overtake it inside
+    passes and phases; the plan must still give the circuit's state."""
+    rng = np.random.default_rng(seed)
+    g = np.zeros(400, dtype=qs.GATE_DTYPE)
+    diag = [qs.QS_T, qs.QS_CZ, qs.QS_RZ, qs.QS_CPHASE]
+    dense = [qs.QS_H, qs.QS_X_HALF, qs.QS_Y_HALF, qs.QS_RX, qs.QS_RY]
+    for i in range(g.size):
+        k = int(rng.choice(diag)) if rng.random() < 0.75 else int(rng.choice(dense))
+        g[i]["kind"] = k
+        if k in (qs.QS_CZ, qs.QS_CPHASE):
+            g[i]["q0"], g[i]["q1"] = rng.choice(n, size=2, replace=False)
+        else:
+            g[i]["q0"] = rng.integers(0, n)
+        g[i]["theta"] = rng.uniform(-3, 3)
+    psi, passes = _emulate(emulator, n, g, t, r, c)
+    ref = O.simulate(n, g)
+    assert np.max(np.abs(psi - ref)) < 1e-12
+
+
 @pytest.mark.parametrize("rows,cols,depth,t", [(4, 5, 25, 13), (4, 4, 30, 9), (3, 5, 40, 10)])
 def test_plan_semantics_random_circuits(emulator, rows, cols, depth, t):
     n = rows * cols
