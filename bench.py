@@ -390,7 +390,8 @@ def run_ours(args, rank, world, local):
                                 else "k_fused_pass<float,5,true,true>"),
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
-                     "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
+                     "frac": round(achieved / hbm_peak, 4),
+                     "frac_of_nominal_7900": round(achieved / 7900.0, 4), "traffic": traffic,
                      "bytes_per_launch": pass_bytes, "avg_launch_ms": round(avg_pass_ms, 4)},
         "e2e": {"value": round(e2e_value, 3), "unit": "cycles/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
