@@ -27,6 +27,30 @@ __device__ __forceinline__ uint64_t insert_zero(uint64_t j, int q)
     return ((j >> q) << (q + 1)) | lo;
 }
 
+// Waits for the phase `parity` of the shared-memory mbarrier at `mbar`
+// (shared address) to complete, for at most `limit_ns` nanoseconds of the
+// global timer (and at most `max_iter` polls, should the timer not advance).
+// Returns whether the phase completed; never blocks longer.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint64_t limit_ns,
+                                                  uint32_t max_iter = 1u << 26)
+{
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= limit_ns) return false;
+    }
+    return false;
+}
+
 #define QS_CUDA_TRY(expr)                                                        \
     do {                                                                         \
         cudaError_t e_ = (expr);                                                 \

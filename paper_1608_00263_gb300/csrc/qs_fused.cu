@@ -398,7 +398,7 @@ struct FusedSmem {
 // traffic and MMA wait overlap the other's work.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kTmemCols = 256;              // D: 0..127, block: 128..255 (two CTAs per SM)
-constexpr int kTcWaitLimit = 1 << 22;
+constexpr uint64_t kTcWaitNs = 1000000000ull;   // 1 s: far beyond 24 products of 128 x 128 x 16
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -565,26 +565,14 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
     }
     // ---- bounded wait for the products ----
     {
-        uint32_t done = 0;
         const uint32_t mb = smem_addr(&TS.mbar);
-        for (int it = 0; it < kTcWaitLimit && !done; ++it) {
-            asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                         " selp.u32 %0, 1, 0, p;\n}"
-                         : "=r"(done)
-                         : "r"(mb), "r"(parity));
-        }
-        if (!done) {
+        if (!mbar_wait_bounded(mb, parity, kTcWaitNs)) {
             // give up on this launch: the products may still be in flight,
             // so wait once more (bounded) before the caller releases the
             // tensor memory, and skip the epilogue
             TS.abort = 1;
             atomicExch(err_flag, 1);
-            for (int it = 0; it < kTcWaitLimit && !done; ++it) {
-                asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                             " selp.u32 %0, 1, 0, p;\n}"
-                             : "=r"(done)
-                             : "r"(mb), "r"(parity));
-            }
+            mbar_wait_bounded(mb, parity, kTcWaitNs);
         }
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
