@@ -144,7 +144,8 @@ qs_status qs_state_destroy(qs_state *s);
 
 /* Device pointer of the amplitudes (interleaved re, im).  Once the caller
  * holds the pointer, resets are written at once and the library assumes
- * nothing about the contents (see qs_state_reset). */
+ * nothing about the contents (see qs_state_reset): read-out results are
+ * formed afresh by every call. */
 qs_status qs_state_amplitudes(const qs_state *s, void **device_amps);
 
 /* Sets the state to |0...0>.  For a state whose memory the caller cannot
@@ -184,7 +185,11 @@ qs_status qs_plan_circuit(int n, qs_dtype dt, const qs_gate *gates,
 
 /* Writes p_U(x) = |<x|psi>|^2 for all 2^n x in canonical order into `out`
  * (host or device, caller-owned): doubles if out_is_fp64, else floats.
- * Asynchronous for device `out`; synchronous for host `out`. */
+ * Asynchronous for device `out`; synchronous for host `out`.  For complex64
+ * states the same read of the state also forms the partial sums of
+ * qs_pt_moments and the chunk sums of qs_sample; those calls reuse them
+ * while the amplitudes are unchanged (never for a state whose pointer the
+ * caller holds), with the same results as a fresh pass. */
 qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64);
 
 /* As qs_probabilities, but stream-ordered for every kind of `out` except
