@@ -154,6 +154,13 @@ def test_leading_hadamard_layer_only_from_basis_zero(dtype):
         qs.qs_state_reset(h)
         qs.qs_apply_circuit(h, perm)
         assert rel_l2(qs.qs_state_copy_out(h, n, dtype), O.simulate(n, perm)) < TOL[dtype]
+        # every form starts from the uniform fill (the old contents are not used)
+        modes = [qs.QS_MODE_PLAIN, qs.QS_MODE_FUSED] + ([qs.QS_MODE_FUSED_TC] if dtype == qs.QS_C64 else [])
+        ref = O.simulate(n, g)
+        for md in modes:
+            qs.qs_state_reset(h)
+            qs.qs_apply_circuit(h, g, mode=md)
+            assert rel_l2(qs.qs_state_copy_out(h, n, dtype), ref) < TOL[dtype], md
         qs.qs_state_reset(h)
         qs.qs_apply_circuit(h, g[:n])            # the layer alone: exactly uniform
         psi = qs.qs_state_copy_out(h, n, dtype)
