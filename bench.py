@@ -540,9 +540,12 @@ def grid20_forms(qs, torch):
     for name, dt in (("c64", qs.QS_C64), ("c128", qs.QS_C128)):
         h = qs.qs_state_create(n, dt)
         try:
-            ms_tot, dh_tot = 0.0, 0.0
+            ms_tot, dh_tot, bytes_tot = 0.0, 0.0, 0.0
             for seed in range(10):
                 g = qs.qs_circuit_generate(4, 5, depth, seed)
+                plan = qs.qs_plan_circuit(n, dt, g[leading_h_layer(qs, g, n):])
+                esz = 8 if dt == qs.QS_C64 else 16
+                bytes_tot += plan["bytes"] + esz * (1 << n)              # passes + the uniform fill
                 qs.qs_state_reset(h)
                 qs.qs_prepare_circuit(h, g)
                 torch.cuda.synchronize()
@@ -554,8 +557,11 @@ def grid20_forms(qs, torch):
                 ms_tot += a.elapsed_time(b)
                 x = qs.qs_sample(h, 100000, 1000 + seed)
                 dh_tot += qs.qs_cross_entropy(h, x)[1]
+            # the state stays in L2 between passes: bytes moved per second of
+            # apply, against the HBM copy rate for scale
             out[name] = {"apply_ms_mean": round(ms_tot / 10, 4), "cycles_per_s": round(10 * depth / (ms_tot / 1e3), 1),
-                         "delta_h_mean": round(dh_tot / 10, 4)}
+                         "delta_h_mean": round(dh_tot / 10, 4),
+                         "pass_bytes_gbs": round(bytes_tot / (ms_tot / 1e3) / 1e9, 1)}
         finally:
             qs.qs_state_destroy(h)
     return out
