@@ -379,10 +379,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded random circuits of the paper's grid rules)",
-        "config": {"workload": args.workload, "qubits": n, "depth": depth, "samples": m,
-                   "state": "complex64 %.1f GB" % ((8 << n) / 1e9),
-                   "form": args.mode, "l2": "inputs larger than L2 (state %.1f GB)" % ((8 << n) / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(args, n, world),
         "apply_cycles_per_s": round(depth * args.steps / (apply_total / 1000.0), 3),
         "passes_per_circuit": passes_total / args.steps,
         "fill_ms_per_circuit": round(fill_ms / args.steps, 4),
@@ -686,6 +683,18 @@ def cpu_baseline(W, dead, n, cycles=(1, 2)):
                          n)}
 
 
+def workload_config(args, n, world):
+    """The `config` object of both arms' lines: the workload timed."""
+    W = WORKLOADS[args.workload]
+    state = (8 << n) / 1e9
+    size = "%.1f GB" % state if state >= 1 else "%.1f MB" % (state * 1e3)
+    l2 = ("inputs larger than L2 (state %s)" % size if state > 0.129
+          else "state L2-resident (%s), not flushed between steps" % size)
+    return {"workload": args.workload, "qubits": n, "depth": W["depth"], "samples": W["m"],
+            "state": "complex64 " + size, "form": args.mode, "l2": l2,
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -716,7 +725,7 @@ def run_reference(args, rank, world):
            "ms_per_step": round(dt * 1000 / args.steps, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded random circuits of the paper's grid rules)",
-           "config": {"workload": args.workload, "qubits": n, "depth": W["depth"]},
+           "config": workload_config(args, n, world),
            "cpu_baseline": {"value": round(value, 5), "unit": "cycles/s", "cores": os.cpu_count(),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": round(value, 5), "unit": "cycles/s", "h2d_bytes_per_step": 0,
