@@ -221,12 +221,10 @@ qs_status qs_state_sync(const qs_state *s);
 qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out);
 
 /* Allocation-free variant of qs_sample, for callers that must not allocate
- * device memory while they run: code recording a CUDA graph (cudaMalloc is
- * not permitted during stream capture), latency-critical loops that cannot
- * absorb the implicit synchronisation of an allocation, and applications or
- * host frameworks that hand all device memory to their own pool or fix
- * their budget up front.  The paper has no counterpart; it is a deployment
- * convenience.
+ * device memory while they run: applications and host frameworks that hand
+ * all device memory to their own pool or fix their memory budget up front,
+ * so that a library call that allocates would fail or break that budget.
+ * The paper has no counterpart; it is a deployment convenience.
  *   n, dt, device_amps: the state (2^n amplitudes of type dt in device
  *     memory, 16-byte aligned, canonical order), read only;
  *   k, seed: as for qs_sample; device_out: k uint64 slots in device memory.
@@ -235,14 +233,15 @@ qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
  * array of 8 MiB compiled into the library, held by every GPU that loads it
  * until the process exits, so n is limited to 1..28 (larger n returns
  * QS_ERR_INVALID_ARG before any device work).  No call allocates memory.
- * The first call on each device looks up that device's address of the array
- * (make it outside any stream capture); later calls reuse it.  All calls
+ * Every call looks up the current device's address of the array; the first
+ * call on a device also loads the library's device code there.  All calls
  * share the one array: calls whose work overlaps on the GPU (different
  * streams, or host threads) race and must be serialised by the caller; the
  * array keeps the previous call's contents, and every entry a call reads is
  * written by that same call first.  Work is ordered on cuda_stream (NULL =
  * legacy default stream); the call synchronises that stream once to check
- * the norm and returns with the search kernel queued. */
+ * the norm (QS_ERR_INVALID_ARG for a zero or non-finite norm) and returns
+ * with the search kernel queued. */
 qs_status qs_sample_noalloc(int n, qs_dtype dt, const void *device_amps, void *cuda_stream,
                             uint64_t k, uint64_t seed, uint64_t *device_out);
 

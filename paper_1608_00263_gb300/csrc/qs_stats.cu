@@ -21,7 +21,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "qs_device.cuh"
@@ -1153,32 +1152,21 @@ namespace qs {
 constexpr uint64_t kNoAllocMaxChunks = 1ULL << 20;   // 2^28 amplitudes / 256
 constexpr uint64_t kNoAllocMaxBlocks = (kNoAllocMaxChunks + kScanSeg - 1) / kScanSeg;
 constexpr int kNoAllocMaxQubits = 28;
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxChunks + kNoAllocMaxBlocks];
 
-// Device address of g_noalloc_scratch per device, looked up once per device
-// (host code only sees a host-side stand-in under the array's name).
-static std::mutex g_noalloc_mu;
-static double *g_noalloc_addr[kNoAllocMaxDevices];
-
+// Device address of g_noalloc_scratch on the current device (host code only
+// sees a host-side stand-in under the array's name).  Looked up on every
+// call rather than cached: the address belongs to the module loaded in the
+// current context, which a device reset replaces.
 static qs_status noalloc_scratch(double **out)
 {
-    int dev = 0;
-    QS_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return set_error(QS_ERR_UNSUPPORTED, "device %d beyond the %d this entry point tracks", dev,
-                         kNoAllocMaxDevices);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(QS_ERR_CUDA, "cudaGetSymbolAddress for the sampler scratch failed: %s",
-                             cudaGetErrorString(e));
-        g_noalloc_addr[dev] = (double *)p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(QS_ERR_CUDA, "cudaGetSymbolAddress for the sampler scratch failed: %s",
+                         cudaGetErrorString(e));
+    *out = (double *)p;
     return QS_OK;
 }
 

@@ -66,12 +66,11 @@ extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, in
     return emulate_plan_mode(n, g, ng, t, r, c, QS_MODE_FUSED, psi_interleaved, passes_out, nullptr);
 }
 
-extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode,
-                                 double *psi_interleaved, int *passes_out, int *tc_phases_out)
+// Executes a built plan on a double-precision state (the semantics the
+// fused kernels give each op).
+static int emulate_built_plan(const Plan &plan, double *psi_interleaved, int *passes_out,
+                              int *tc_phases_out = nullptr)
 {
-    PlanParams pp{n, t, r, c, mode, kTcBits, mode == QS_MODE_FUSED_TC && t == 13 ? 1 : 0};
-    Plan plan;
-    if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
     cd *psi = reinterpret_cast<cd *>(psi_interleaved);
     for (const DevPass &P : plan.passes) {
         const int T = P.t, ngl = P.n - T;
@@ -135,4 +134,129 @@ extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int 
         *tc_phases_out = k;
     }
     return 0;
+}
+
+extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode,
+                                 double *psi_interleaved, int *passes_out, int *tc_phases_out)
+{
+    PlanParams pp{n, t, r, c, mode, kTcBits, mode == QS_MODE_FUSED_TC && t == 13 ? 1 : 0};
+    Plan plan;
+    if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
+    return emulate_built_plan(plan, psi_interleaved, passes_out, tc_phases_out);
+}
+
+// Symbolic check of a plan built with the library's own default parameters
+// for (n, dtype, mode): every op is mapped back to the gate it applies
+// (kind and qubits, through the phase's register map and the pass's tile
+// map), and the sequence of ops must be a reordering of the gate list that
+// keeps every pair of non-commuting gates (a shared qubit, at least one of
+// them non-diagonal) in circuit order.  Also checks the tile and register
+// maps and each pass's count of deferred 1/sqrt2 factors.  Needs no state,
+// so it runs at any n.  Supports plans whose gates are one op each (H,
+// X^1/2, Y^1/2, T, CZ, RZ, CPHASE) and no tensor-core phases.  Returns 0,
+// or a negative code naming the first violated rule; *passes_out receives
+// the number of passes.
+// check_plan_against: the plan is built from `g_plan` and checked against
+// the circuit order of `g` (the same list for check_plan_order; a different
+// one lets a test show that the check rejects a wrong order).
+extern "C" int check_plan_against(int n, int dtype, int mode, const qs_gate *g_plan, const qs_gate *g,
+                                  size_t ng, int *passes_out)
+{
+    qs_opts o{};
+    o.mode = mode;
+    PlanParams pp = default_plan_params(n, (qs_dtype)dtype, &o);
+    Plan plan;
+    if (build_plan(pp, g_plan, ng, &plan) != QS_OK) return -1;
+    if (passes_out) *passes_out = (int)plan.passes.size();
+    std::vector<char> used(ng, 0);
+    size_t applied = 0;
+    auto qmask_of = [&](const qs_gate &x) {
+        uint64_t m = 1ULL << x.q0;
+        if (gate_is_two_qubit(x.kind)) m |= 1ULL << x.q1;
+        return m;
+    };
+    for (const DevPass &P : plan.passes) {
+        // tile map: P.t distinct qubits in ascending order, the rest in G
+        uint64_t tile = 0, glob = 0;
+        for (int b = 0; b < P.t; ++b) {
+            if (P.L[b] >= n || (b && P.L[b] <= P.L[b - 1])) return -2;
+            tile |= 1ULL << P.L[b];
+        }
+        for (int i = 0; i < n - P.t; ++i) {
+            if (P.G[i] >= n || ((tile >> P.G[i]) & 1) || (i && P.G[i] <= P.G[i - 1])) return -3;
+            glob |= 1ULL << P.G[i];
+        }
+        if ((tile | glob) != ((n == 64) ? ~0ULL : ((1ULL << n) - 1))) return -3;
+        int nondiag = 0;
+        for (int ph = 0; ph < P.nphases; ++ph) {
+            const DevPhase &H = plan.phases[P.phase_begin + ph];
+            if (H.kind != 0) return -4;
+            uint32_t rbits = 0;
+            for (int j = 0; j < P.r; ++j) {
+                if (H.R[j] >= P.t || ((rbits >> H.R[j]) & 1)) return -5;
+                rbits |= 1u << H.R[j];
+            }
+            for (int op_i = H.op_begin; op_i < H.op_end; ++op_i) {
+                const DevOp &op = plan.ops[op_i];
+                int kind = -1;
+                uint64_t qm = 0;
+                if (op.type == OP_H || op.type == OP_XH || op.type == OP_YH) {
+                    if (op.a >= P.r) return -6;
+                    kind = op.type == OP_H ? QS_H : op.type == OP_XH ? QS_X_HALF : QS_Y_HALF;
+                    qm = 1ULL << P.L[H.R[op.a]];
+                    ++nondiag;
+                } else if (op.type == OP_NEG || op.type == OP_PHASE) {
+                    uint64_t rq = 0;
+                    for (int j = 0; j < P.r; ++j)
+                        if ((op.rmask >> j) & 1) rq |= 1ULL << P.L[H.R[j]];
+                    if (op.rmask >> P.r) return -7;
+                    if (rq & op.qmask) return -7;
+                    qm = rq | op.qmask;
+                    const int nq = __builtin_popcountll(qm);
+                    if (op.type == OP_NEG) kind = nq == 2 ? QS_CZ : -1;
+                    else kind = nq == 2 ? QS_CPHASE : -2;   // T or RZ: resolved below
+                } else {
+                    return -8;
+                }
+                // earliest unused gate of this kind on these qubits
+                size_t pick = ng;
+                for (size_t i = 0; i < ng; ++i) {
+                    if (used[i] || qmask_of(g[i]) != qm) continue;
+                    const int k = g[i].kind;
+                    const bool match = kind == -2 ? (k == QS_T || k == QS_RZ) : k == kind;
+                    if (match) { pick = i; break; }
+                }
+                if (pick == ng) return -9;
+                // no earlier pending gate may fail to commute with it
+                const bool dg = gate_is_diagonal(g[pick].kind);
+                for (size_t j = 0; j < pick; ++j) {
+                    if (used[j] || !(qmask_of(g[j]) & qm)) continue;
+                    if (!(dg && gate_is_diagonal(g[j].kind))) return -10;
+                }
+                used[pick] = 1;
+                ++applied;
+            }
+        }
+        if (P.deferred != nondiag) return -11;
+    }
+    return applied == ng ? 0 : -12;
+}
+
+extern "C" int check_plan_order(int n, int dtype, int mode, const qs_gate *g, size_t ng, int *passes_out)
+{
+    return check_plan_against(n, dtype, mode, g, g, ng, passes_out);
+}
+
+// Numerical emulation as emulate_plan, with the tile lookahead chosen by the
+// caller (the library deepens it for large states: 8 additions among 8
+// candidates at 28-31 qubits, every addition and candidate from 32 on).
+extern "C" int emulate_plan_look(int n, const qs_gate *g, size_t ng, int t, int r, int c, int look_steps,
+                                 int look_top, double *psi_interleaved, int *passes_out)
+{
+    PlanParams pp{n, t, r, c, QS_MODE_FUSED, kTcBits, 0};
+    pp.look_steps = look_steps;
+    pp.look_top = look_top;
+    Plan plan;
+    if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
+    return emulate_built_plan(plan, psi_interleaved, passes_out);
 }

@@ -1,0 +1,172 @@
+"""The metric's own workload against the FP64 oracle: 30 qubits on a 5x6 grid,
+depth 40, complex64, seed 0 (Sec. "Convergence to Porter-Thomas" circuit
+rules; the estimation procedure of Sec. "Characterizing quantum supremacy").
+
+The oracle evolves the same gate list in FP64 (16 GB of host memory, about a
+minute and a half on the GPU host's cores) and every form of the CUDA path is
+compared with it:
+
+* state: relative L2 error <= 1e-5 for the fused, tensor-core and plain
+  forms (compared chunk by chunk; no second full copy of the state on the
+  host);
+* entropy and uniform cross entropy within 1e-6 relative, the norm within
+  2e-5, moments 1..10 within 1e-5 relative (the k-th moment amplifies the
+  relative probability error k-fold);
+* 10^6 samples: every sample satisfies the oracle's CDF inversion within
+  the bound that the complex64 state's probability error puts on the CDF;
+  the sample cross entropy within 1e-6 relative of the oracle's on the same
+  sample list.
+
+At 30 qubits the planner runs its deeper tile lookahead (8 additions scored
+among 8 candidates), so this also pins that branch of the planner against
+the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1608_00263_gb300 as qs
+from paper_1608_00263_gb300 import build as qs_build
+
+pytestmark = pytest.mark.gpu
+
+N_QUBITS = 30
+CHUNK = 1 << 26          # amplitudes per comparison chunk
+
+
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return float("inf")
+
+
+@pytest.fixture(scope="module")
+def oracle_state():
+    qs_build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    # psi (16 GB) + p (8 GB) + the CDF (8 GB) on the host
+    if _mem_available_gb() < 40:
+        pytest.skip("the 30-qubit FP64 oracle needs ~40 GB of host memory")
+    g = qs.qs_circuit_generate(5, 6, 40, 0)
+    assert g.tobytes() == O.generate_circuit(5, 6, 40, 0).tobytes()
+    # a dict, so that the last test can drop the 16 GB state once it is done
+    return {"gates": g, "psi": O.simulate(N_QUBITS, g)}
+
+
+def _view(ptr, count):
+    import torch
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
+                                    "version": 3}
+    return torch.as_tensor(_Arr(), device="cuda")
+
+
+def _rel_l2_vs_oracle(h, psi):
+    """||psi_gpu - psi|| / ||psi|| with the oracle's chunks moved to the
+    device (test-side arithmetic in FP64)."""
+    import torch
+    t = _view(qs.qs_state_amplitudes(h), 2 * psi.size)
+    num = den = 0.0
+    for i in range(0, psi.size, CHUNK):
+        ref = torch.from_numpy(psi[i:i + CHUNK].view(np.float64)).cuda()
+        a = t[2 * i:2 * (i + CHUNK)].double()
+        num += float(torch.sum((a - ref) ** 2))
+        den += float(torch.sum(ref ** 2))
+    return math.sqrt(num / den)
+
+
+@pytest.fixture(scope="module")
+def fused_state(oracle_state):
+    g = oracle_state["gates"]
+    h = qs.qs_state_create(N_QUBITS, qs.QS_C64)
+    qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED)
+    yield h
+    qs.qs_state_destroy(h)
+
+
+@pytest.mark.parametrize("mode", [qs.QS_MODE_FUSED_TC, qs.QS_MODE_PLAIN])
+def test_other_forms_vs_oracle(oracle_state, mode):
+    g, psi = oracle_state["gates"], oracle_state["psi"]
+    h = qs.qs_state_create(N_QUBITS, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(h, g, mode=mode)
+        err = _rel_l2_vs_oracle(h, psi)
+    finally:
+        qs.qs_state_destroy(h)
+    assert err < 1e-5, (mode, err)
+
+
+def test_fused_state_statistics_and_samples_vs_oracle(oracle_state, fused_state):
+    import torch
+    psi = oracle_state["psi"]
+    h = fused_state
+    # statistics before the amplitudes are exposed, so they come from the
+    # library's own read-out
+    r = qs.qs_pt_moments(h, 10)
+    m = 1000000
+    seed = 1000
+    x = qs.qs_sample(h, m, seed)
+    ce, dh = qs.qs_cross_entropy(h, x)
+
+    err = _rel_l2_vs_oracle(h, psi)
+    assert err < 1e-5, err
+    # ||p_gpu - p||_1 bounds the CDF difference between the two sides
+    t = _view(qs.qs_state_amplitudes(h), 2 * psi.size)
+    l1 = 0.0
+    for i in range(0, psi.size, CHUNK):
+        ref = torch.from_numpy(psi[i:i + CHUNK].view(np.float64)).cuda().view(-1, 2)
+        a = t[2 * i:2 * (i + CHUNK)].double().view(-1, 2)
+        l1 += float(torch.sum(torch.abs(torch.sum(a * a, 1) - torch.sum(ref * ref, 1))))
+    p = O.probabilities(psi)
+    del psi
+    oracle_state.pop("psi")
+    assert r["norm"] == pytest.approx(O.norm(p), abs=2e-5)
+    H = O.entropy(p)
+    assert r["entropy"] == pytest.approx(H, rel=1e-6)
+    assert r["uniform_ce"] == pytest.approx(O.uniform_ce(p), rel=1e-6)
+    # moments N^{k-1} sum p^k (the oracle's definition; FP64, in chunks)
+    N = float(1 << N_QUBITS)
+    mo = np.zeros(10)
+    for i in range(0, p.size, CHUNK):
+        q = p[i:i + CHUNK] * N
+        tk = np.ones_like(q)
+        for k in range(10):
+            tk *= q
+            mo[k] += float(np.sum(tk))
+    mo /= N
+    for k in range(10):
+        assert r["moments"][k] == pytest.approx(mo[k], rel=1e-5), k
+    # Porter-Thomas regime (Sec. pt): the oracle itself sits at the closed forms
+    assert abs(H - (N_QUBITS * math.log(2) - 1 + O.EULER_GAMMA)) < 4 * 0.75 * 2.0 ** (-N_QUBITS / 2)
+
+    # samples: x_j = min{i : C_i > u_j C_{N-1}} on the oracle's CDF, within
+    # the CDF error bound l1
+    C = np.cumsum(p)
+    total = C[-1]
+    u = np.array([O.sample_uniform(seed, j) for j in range(m)])
+    target = u * total
+    xi = x.astype(np.int64)
+    lo = np.where(xi > 0, C[np.maximum(xi - 1, 0)], 0.0)
+    hi = C[xi]
+    bound = l1 + 1e-9
+    ok = (lo - bound <= target) & (target < hi + bound)
+    assert ok.all(), np.nonzero(~ok)[0][:10]
+    exact = (lo <= target) & (target < hi)
+    # the complex64 state moves only samples whose target lies near a boundary
+    assert np.mean(exact) > 0.95, np.mean(exact)
+    del C
+    ce_o, dh_o = O.cross_entropy(p, x)
+    assert ce == pytest.approx(ce_o, rel=1e-6)
+    assert dh == pytest.approx(dh_o, abs=3e-5)
+    # Eq. ae on ideal samples: Delta H ~ 1 within a few 1/sqrt(m)
+    # (spread of ln(N p) over ideal samples ~0.8, plus the finite-N offset)
+    assert abs(dh_o - 1) < 4 * 0.8 / math.sqrt(m) + 0.002

@@ -230,6 +230,18 @@ def test_probabilities(state20):
     torch.cuda.synchronize()
     pd = out.cpu().numpy()
     assert np.sum(np.abs(pd - p)) < 2 * tol
+    # element by element: the read-out forms |psi|^2 of the state it holds
+    # (complex64: one FP32 FMA of the products, widened exactly to FP64, so
+    # within 2^-22 relative; complex128: FP64 throughout) ...
+    psi = qs.qs_state_copy_out(h, 20, dtype).astype(np.complex128)
+    pg = psi.real ** 2 + psi.imag ** 2
+    rtol = 2.0 ** -22 if dtype == qs.QS_C64 else 1e-15
+    assert np.all(np.abs(pd - pg) <= rtol * pg + 1e-300), np.max(np.abs(pd - pg) / pg)
+    # ... and each probability differs from the oracle's only by what that
+    # amplitude's own error allows: |p - p_ref| <= (2 |psi_ref| + |d|) |d|
+    d = np.abs(psi - ref)
+    allow = rtol * pg + (2 * np.abs(ref) + d) * d * (1 + 1e-9) + 1e-300
+    assert np.all(np.abs(pd - p) <= allow)
     host = np.empty(1 << 20, dtype=np.float64)
     qs.qs_probabilities(h, host, fp64=True)
     assert np.array_equal(host, pd)

@@ -137,6 +137,16 @@ def emulator():
     lib.emulate_plan_mode.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.check_plan_order.restype = ctypes.c_int
+    lib.check_plan_order.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]
+    lib.check_plan_against.restype = ctypes.c_int
+    lib.check_plan_against.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]
+    lib.emulate_plan_look.restype = ctypes.c_int
+    lib.emulate_plan_look.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
     lib.emulate_plan.restype = ctypes.c_int
     lib.emulate_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -237,3 +247,57 @@ def test_tc_plan_semantics(emulator, rows, cols, depth, seed):
     err = np.linalg.norm(psi - ref) / np.linalg.norm(ref)
     assert tcp.value > 0
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("rows,cols,corners,depth,seed", [
+    (4, 7, False, 40, 0), (5, 6, False, 40, 0), (5, 6, False, 40, 1), (5, 6, False, 40, 2),
+    (6, 6, True, 40, 0)])
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_full_size_plans_keep_circuit_order(emulator, rows, cols, corners, depth, seed, dtype):
+    """The plans the library builds for 28-, 30- and 34-qubit circuits (with
+    the deeper tile lookahead those sizes use) apply every gate once, keep
+    every pair of non-commuting gates in circuit order, and carry consistent
+    tile / register maps and deferred-factor counts: a symbolic check that
+    needs no state."""
+    dead = O.grid_dead_mask(rows, cols, [(0, 0), (rows - 1, cols - 1)] if corners else [])
+    n = rows * cols - int(dead.sum())
+    g = np.ascontiguousarray(qs.qs_circuit_generate(rows, cols, depth, seed, dead), dtype=qs.GATE_DTYPE)
+    passes = ctypes.c_int(0)
+    rc = emulator.check_plan_order(n, dtype, qs.QS_MODE_FUSED, g.ctypes.data, g.size, ctypes.byref(passes))
+    assert rc == 0, rc
+    assert passes.value == qs.qs_plan_circuit(n, dtype, g)["passes"]
+
+
+def test_plan_order_check_catches_a_swapped_pair(emulator):
+    """The symbolic check itself: the plan of a circuit in which an X^1/2 or
+    Y^1/2 gate was moved before the CZ on its qubit that precedes it is not
+    a valid plan of the original circuit."""
+    g = np.ascontiguousarray(qs.qs_circuit_generate(3, 4, 12, 0), dtype=qs.GATE_DTYPE)
+    passes = ctypes.c_int(0)
+    assert emulator.check_plan_order(12, qs.QS_C64, qs.QS_MODE_FUSED, g.ctypes.data, g.size,
+                                     ctypes.byref(passes)) == 0
+    i = next(k for k in range(1, g.size) if int(g[k]["kind"]) in (qs.QS_X_HALF, qs.QS_Y_HALF)
+             and any(int(g[j]["kind"]) == qs.QS_CZ and g[k]["q0"] in (g[j]["q0"], g[j]["q1"])
+                     for j in range(k)))
+    j = max(j for j in range(i) if int(g[j]["kind"]) == qs.QS_CZ and g[i]["q0"] in (g[j]["q0"], g[j]["q1"]))
+    sw = g.copy()
+    sw[[i, j]] = sw[[j, i]]
+    rc = emulator.check_plan_against(12, qs.QS_C64, qs.QS_MODE_FUSED, sw.ctypes.data, g.ctypes.data,
+                                     g.size, ctypes.byref(passes))
+    assert rc == -10, rc
+
+
+@pytest.mark.parametrize("look", [(8, 8), (64, 64)])
+@pytest.mark.parametrize("rows,cols,depth,t,seed", [(4, 5, 25, 13, 0), (4, 4, 40, 10, 1), (3, 6, 30, 11, 2)])
+def test_plan_semantics_deep_lookahead(emulator, look, rows, cols, depth, t, seed):
+    """The tile lookahead of large states (8 additions among 8 candidates at
+    28-31 qubits, every addition and candidate from 32 on), run on states
+    small enough to emulate numerically: the plan reproduces the oracle."""
+    n = rows * cols
+    g = np.ascontiguousarray(qs.qs_circuit_generate(rows, cols, depth, seed), dtype=qs.GATE_DTYPE)
+    psi = O.zero_state(n)
+    passes = ctypes.c_int(0)
+    assert emulator.emulate_plan_look(n, g.ctypes.data, g.size, t, 5, 5, look[0], look[1],
+                                      psi.ctypes.data, ctypes.byref(passes)) == 0
+    ref = O.simulate(n, g)
+    assert np.max(np.abs(psi - ref)) < 1e-12

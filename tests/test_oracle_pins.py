@@ -400,3 +400,44 @@ def test_sampled_log_probability_histogram_eq_pal():
     emp = np.arange(1, z.size + 1) / z.size
     ks = np.max(np.abs(emp - F))
     assert ks < 0.012
+
+
+def test_shifted_amplitudes_equal_shifted_circuits():
+    """The adjoint tests form a shifted circuit's amplitudes from two FP64
+    states (R_P(theta + d) = R_P(theta) R_P(d), CPHASE(phi + d) = CPHASE(phi)
+    (1 + (e^{id} - 1) Pi_11)); that must equal evolving the shifted circuit
+    from scratch, for every parameter kind and several shifts."""
+    from adjoint_reference import PARAM, _shifted_amplitudes, parameterised_circuit
+    n = 10
+    nominal, noisy, idx = parameterised_circuit(2, 5, 12, 4, 13)
+    xi = np.arange(1 << n, dtype=np.int64)
+    psi_final = O.simulate(n, noisy)
+    kinds_seen = set()
+    picks = [int(k) for kind in PARAM for k in idx[noisy["kind"][idx] == kind][:3]]
+    for k in picks:
+        kinds_seen.add(int(noisy[k]["kind"]))
+        amp = _shifted_amplitudes(n, noisy, k, xi, O.simulate(n, noisy[:k]), psi_final)
+        for d in (np.pi / 2, -np.pi / 2, 0.3):
+            gs = noisy.copy()
+            gs[k]["theta"] += d
+            assert np.max(np.abs(amp(d) - O.simulate(n, gs))) < 1e-12
+    assert kinds_seen == set(PARAM)
+
+
+def test_shift_and_fd_gradients_agree_with_plain_shifted_circuits():
+    """The one-suffix-per-parameter gradients equal the parameter shift taken
+    by evolving the two shifted circuits from scratch, and central
+    differences agree with both (12 qubits, every parameter kind)."""
+    from adjoint_reference import (oracle_fd_grad, oracle_shift_and_fd, oracle_shift_grad,
+                                   parameterised_circuit)
+    n = 12
+    nominal, noisy, idx = parameterised_circuit(3, 4, 16, 3, 7)
+    x = O.sample(O.probabilities(O.simulate(n, nominal)), 5000, 8)
+    subset = idx[::9]
+    ps, fd = oracle_shift_and_fd(n, noisy, x, subset)
+    direct = np.array([oracle_shift_grad(n, noisy, x, int(k)) for k in subset])
+    fd_direct = np.array([oracle_fd_grad(n, noisy, x, int(k)) for k in subset[:6]])
+    scale = np.max(np.abs(direct))
+    assert np.max(np.abs(ps - direct)) < 1e-12 * scale
+    assert np.max(np.abs(fd[:6] - fd_direct)) < 1e-8 * scale
+    assert np.max(np.abs(fd - ps)) < 1e-6 * scale
