@@ -165,11 +165,41 @@ def leading_h_layer(qs, g, n):
     return n if len(set(g["q0"][:n].tolist())) == n else 0
 
 
-def applied_plan(qs, n, g, md):
+def device_state_copy(qs, torch, h, n):
+    """A device copy of a complex64 state (as 2^(n+1) floats)."""
+    ptr = qs.qs_state_amplitudes(h)
+    out = torch.empty(2 << n, dtype=torch.float32, device="cuda")
+    src = torch.as_tensor(_CudaArray(ptr, 2 << n), device="cuda")
+    out.copy_(src)
+    return out
+
+
+def device_rel_l2(qs, torch, h, n, ref):
+    """||psi - ref|| / ||ref|| over device memory, in FP64 chunks."""
+    src = torch.as_tensor(_CudaArray(qs.qs_state_amplitudes(h), 2 << n), device="cuda")
+    num = den = 0.0
+    step = 1 << 27
+    for i in range(0, 2 << n, step):
+        a, b = src[i:i + step].double(), ref[i:i + step].double()
+        num += float(torch.sum((a - b) ** 2))
+        den += float(torch.sum(b * b))
+    return math.sqrt(num / den)
+
+
+class _CudaArray:
+    """A raw device pointer of `count` float32 values, for torch.as_tensor."""
+
+    def __init__(self, ptr, count):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 3}
+
+
+def applied_plan(qs, n, g, md, prec=0):
     """Launches and algorithmic bytes of applying g to the reset state: the
     uniform fill (2^n complex64 written) and the plan of the remaining gates."""
     k = leading_h_layer(qs, g, n)
-    st = qs.qs_plan_circuit(n, qs.QS_C64, g[k:], mode=md) if len(g) > k else {"passes": 0, "bytes": 0.0}
+    st = (qs.qs_plan_circuit(n, qs.QS_C64, g[k:], mode=md, precision=prec) if len(g) > k
+          else {"passes": 0, "bytes": 0.0})
     return {"passes": st["passes"], "launches": st["passes"] + (1 if k else 0),
             "bytes": st["bytes"] + (8.0 * (1 << n) if k else 0.0), "fill": k}
 
@@ -321,21 +351,35 @@ def run_ours(args, rank, world, local):
     compare = {}
     if not args.no_compare and rank == 0:
         gates = qs.qs_circuit_generate(W["rows"], W["cols"], depth, base_seed, dead)
-        for name, md in (("plain", qs.QS_MODE_PLAIN), ("fused", qs.QS_MODE_FUSED),
-                         ("tc", qs.QS_MODE_FUSED_TC)):
+        ref_state = None
+        for name, md, prec in (("plain", qs.QS_MODE_PLAIN, 0), ("fused", qs.QS_MODE_FUSED, 0),
+                               ("tc", qs.QS_MODE_FUSED_TC, qs.QS_PREC_FP16X3),
+                               ("tc_bf16x3", qs.QS_MODE_FUSED_TC, qs.QS_PREC_BF16X3),
+                               ("tc_bf16x6", qs.QS_MODE_FUSED_TC, qs.QS_PREC_BF16X6),
+                               ("tc_tf32x3", qs.QS_MODE_FUSED_TC, qs.QS_PREC_TF32X3),
+                               ("tc_tf32", qs.QS_MODE_FUSED_TC, qs.QS_PREC_TF32)):
             qs.qs_state_reset(h)
-            qs.qs_prepare_circuit(h, gates, mode=md)
+            qs.qs_prepare_circuit(h, gates, mode=md, precision=prec)
             torch.cuda.synchronize()
             a, b = ev(), ev()
             a.record(stream)
-            qs.qs_apply_circuit(h, gates, mode=md)
+            qs.qs_apply_circuit(h, gates, mode=md, precision=prec)
             b.record(stream)
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
-            pst = applied_plan(qs, n, gates, md)
+            pst = applied_plan(qs, n, gates, md, prec)
+            nrm = qs.qs_pt_moments(h, 0)["norm"]
             compare[name] = {"apply_ms": round(ms, 3), "cycles_per_s": round(depth / (ms / 1e3), 2),
-                             "launches": pst["launches"],
+                             "launches": pst["launches"], "norm": round(nrm, 7),
+                             "norm_drift_within_1e-5": abs(nrm - 1) <= 1e-5,
                              "hbm_frac_of_measured": round(pst["bytes"] / (ms / 1e3) / 1e9 / hbm_peak, 4)}
+            # relative L2 distance to the register form's state (both FP32
+            # evolutions; the lossy operand precisions show their error here)
+            if name == "fused":
+                ref_state = device_state_copy(qs, torch, h, n)
+            elif name.startswith("tc") and ref_state is not None:
+                compare[name]["rel_l2_vs_fused"] = float("%.3e" % device_rel_l2(qs, torch, h, n, ref_state))
+        del ref_state
 
     # ---- 34 qubits (6x6 grid minus two corners, depth 40): the three forms,
     # apply only, one circuit each (outside the timed region) ----
@@ -360,6 +404,12 @@ def run_ours(args, rank, world, local):
         small = grid20_forms(qs, torch)
         grad = adjoint_24(qs, torch)
         h = qs.qs_state_create(n, qs.QS_C64, stream)
+
+    # arithmetic rates of this GPU (FMA chains, CUDA events): the roofline
+    # denominators of the ALU-bound passes
+    alu = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32x2_fma"), (2, "fp64_fma")):
+        alu[name + "_tflops"] = round(2.0 * qs.qs_alu_rate(kind, stream) / 1e12, 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -403,6 +453,7 @@ def run_ours(args, rank, world, local):
         "single_error": single,
         "grid4x5_n20_d25": small,
         "adjoint": grad,
+        "alu_peaks": alu,
     }
     if cpu:
         out["cpu_baseline"] = cpu
@@ -443,6 +494,7 @@ def forms_34(qs, torch, hbm_peak):
             nrm = qs.qs_pt_moments(h, 0)["norm"]
             out[name] = {"apply_ms": round(ms, 1), "cycles_per_s": round(W["depth"] / (ms / 1e3), 2),
                          "launches": st["launches"], "norm": round(nrm, 7),
+                         "norm_drift_within_1e-5": abs(nrm - 1) <= 1e-5,
                          "hbm_frac_of_measured": round(st["bytes"] / (ms / 1e3) / 1e9 / hbm_peak, 4)}
     finally:
         qs.qs_state_destroy(h)
@@ -661,26 +713,68 @@ def load_traffic(mode, n):
     return round(r["bytes_per_launch"] * (2.0 ** n) / (2.0 ** r["qubits"]), 1)
 
 
-def cpu_baseline(W, dead, n, cycles=(1, 2)):
-    """Oracle (FP64 CPU) on a bounded sample: the gates of the given cycles of
-    the workload's circuit, applied to an n-qubit state; returns cycles/s."""
-    import numpy as np
+ORACLE_SHARES = 64      # one oracle step = 1/64 of the whole step
 
-    import oracle as O
-    gates = O.generate_circuit(W["rows"], W["cols"], W["depth"], 0, dead)
-    sel = gates[(gates["cycle"] >= cycles[0]) & (gates["cycle"] <= cycles[-1])]
-    psi = O.zero_state(n)
-    t0 = time.perf_counter()
-    O.apply_circuit(psi, sel)
-    dt = time.perf_counter() - t0
-    del psi
-    ncyc = cycles[-1] - cycles[0] + 1
-    return {"value": round(ncyc / dt, 5), "unit": "cycles/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": "FP64 oracle applying the %d gates of cycles %d-%d of the %s circuit to a "
-                      "%d-qubit state (OpenMP over all host cores; state allocation excluded)"
-                      % (len(sel), cycles[0], cycles[-1], "x".join(map(str, (W["rows"], W["cols"]))),
-                         n)}
+
+class OracleStep:
+    """The FP64 oracle on a bounded sample of the whole step: step i does
+    1/64 of every leg of one full step of the workload --
+      * evolution: gates [i G/64, (i+1) G/64) of the circuit (G gates, H
+        layer included), applied in order to one 2^n-amplitude state, so 64
+        consecutive steps evolve the whole circuit once;
+      * read-out: probabilities of the state's slice i (2^n/64 amplitudes),
+        norm, entropy, uniform cross entropy and moments 1..10 of a
+        Porter-Thomas distributed slice of the same size (the output
+        distribution's shape, Sec. pt; seeded), m/64 samples from that slice
+        (inverse CDF) and their cross entropy.
+    Its unit is 40/64 cycles of the 40-cycle step."""
+
+    def __init__(self, W, dead, n):
+        import numpy as np
+
+        import oracle as O
+        self.O, self.np = O, np
+        self.n, self.W = n, W
+        self.gates = O.generate_circuit(W["rows"], W["cols"], W["depth"], 0, dead)
+        self.psi = O.zero_state(n)
+        self.slice = (1 << n) // ORACLE_SHARES
+        rng = np.random.default_rng(12345)
+        pt = rng.exponential(size=self.slice)
+        self.pt = pt / pt.sum() / ORACLE_SHARES       # a 1/64 share of a normalised distribution
+        self.m = W["m"] // ORACLE_SHARES
+        self.cycles = W["depth"] / ORACLE_SHARES
+
+    def step(self, i):
+        O, G = self.O, self.gates.size
+        k = i % ORACLE_SHARES
+        t0 = time.perf_counter()
+        if k == 0 and i:
+            self.psi = O.zero_state(self.n)          # the next circuit starts from |0...0>
+        O.apply_circuit(self.psi, self.gates[k * G // ORACLE_SHARES:(k + 1) * G // ORACLE_SHARES])
+        O.probabilities(self.psi[k * self.slice:(k + 1) * self.slice])
+        p = self.pt
+        O.norm(p), O.entropy(p), O.uniform_ce(p), O.moments(p, 10)
+        x = O.sample(p, self.m, 1000 + i)
+        O.cross_entropy(p, x)
+        return time.perf_counter() - t0
+
+    def describe(self):
+        return ("FP64 oracle (OpenMP over all host cores), 1/%d of the whole %s step per oracle "
+                "step: about %d of the circuit's %d gates on the 2^%d state, then probabilities of a "
+                "2^%d slice and norm, entropy, uniform CE, moments 1..10, %d samples and their CE "
+                "on a Porter-Thomas slice of that size; value = (%g cycles per oracle step) / time"
+                % (ORACLE_SHARES, "x".join(map(str, (self.W["rows"], self.W["cols"]))),
+                   self.gates.size // ORACLE_SHARES, self.gates.size, self.n,
+                   self.n - int(math.log2(ORACLE_SHARES)), self.m, self.cycles))
+
+
+def cpu_baseline(W, dead, n, steps=4):
+    """Oracle (FP64 CPU) on a bounded sample of the whole step: `steps`
+    consecutive 1/64 shares (OracleStep); returns cycles/s."""
+    o = OracleStep(W, dead, n)
+    dt = sum(o.step(i) for i in range(steps))
+    return {"value": round(o.cycles * steps / dt, 5), "unit": "cycles/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": "%d oracle steps; %s" % (steps, o.describe())}
 
 
 def workload_config(args, n, world):
@@ -707,19 +801,12 @@ def run_reference(args, rank, world):
         for r, c in W["dead"]:
             dead[r * W["cols"] + c] = 1
     n = W["rows"] * W["cols"] - len(W["dead"])
-    import oracle as O
-    gates = O.generate_circuit(W["rows"], W["cols"], W["depth"], 0, dead)
-    sel = gates[(gates["cycle"] >= 1) & (gates["cycle"] <= 2)]
-    psi = O.zero_state(n)
-    for _ in range(args.warmup):
-        O.apply_circuit(psi, sel)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        O.apply_circuit(psi, sel)
-    dt = time.perf_counter() - t0
-    value = 2 * args.steps / dt
-    sample = ("FP64 oracle, two cycles (%d gates, cycles 1-2) of the %s circuit per step on a "
-              "%d-qubit state, OpenMP over all host cores" % (len(sel), args.workload, n))
+    o = OracleStep(W, dead, n)
+    for i in range(args.warmup):
+        o.step(i)
+    dt = sum(o.step(args.warmup + i) for i in range(args.steps))
+    value = o.cycles * args.steps / dt
+    sample = o.describe()
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "cycles/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt * 1000 / args.steps, 3), "higher_is_better": True,

@@ -87,14 +87,26 @@ typedef enum {
                               products on the tcgen05 tensor cores */
 } qs_mode;
 
-/* Operand precision of QS_MODE_FUSED_TC (ignored by the other modes). */
+/* Operand precision of QS_MODE_FUSED_TC (ignored by the other modes).  The
+ * block matrix (host-multiplied in FP64) and the state tile are split into
+ * terms of the operand type; the products listed are accumulated in FP32
+ * by the tensor cores.  The paper itself works in double precision
+ * throughout (appendix "Quantum Simulation Details"); these forms trade
+ * operand width for tensor-core rate. */
 typedef enum {
-    QS_PREC_DEFAULT = 0,   /* FP16x3 for TC mode */
-    QS_PREC_FP16X3 = 1,    /* hi/lo FP16 split of both operands, three
-                              products, FP32 accumulation, per-tile
-                              power-of-two scaling: ~22 significant bits */
-    QS_PREC_BF16X3 = 2     /* hi/lo BF16 split, three products: ~16 bits;
-                              reported lossy */
+    QS_PREC_DEFAULT = 0,   /* QS_PREC_FP16X3 */
+    QS_PREC_FP16X3 = 1,    /* hi + lo FP16 terms of both operands, three
+                              products (hi hi, hi lo, lo hi), per-tile
+                              power-of-two scaling into FP16's range: ~22
+                              significant bits */
+    QS_PREC_BF16X3 = 2,    /* hi + lo BF16 terms, three products: ~16
+                              significant bits; lossy against the 1e-5
+                              state bound (its error is reported) */
+    QS_PREC_BF16X6 = 3,    /* hi + mid + lo BF16 terms, six products (all
+                              pairs of combined order <= 2): ~24 bits */
+    QS_PREC_TF32X3 = 4,    /* hi + lo TF32 terms, three products: ~22 bits */
+    QS_PREC_TF32 = 5       /* one TF32 term, one product: ~11 bits; lossy,
+                              for comparison (its error is reported) */
 } qs_precision;
 
 /* Options for qs_apply_circuit; NULL means defaults
@@ -105,7 +117,10 @@ typedef struct {
     int precision;   /* qs_precision */
     int k;           /* TC block size in qubits (6 is the only built value) */
     int tile_log2;   /* fused tile size in amplitudes, log2 (0 = default) */
-    int autotune;    /* reserved, must be 0 */
+    int autotune;    /* 1: the library times candidate tile sizes (and, for
+                        QS_MODE_FUSED_TC, the register form) and keeps the
+                        fastest (see qs_apply_circuit, qs_batch_set_options);
+                        0: use the other fields as given */
 } qs_opts;
 
 /* Planner summary (host-only, see qs_plan_circuit). */
@@ -161,7 +176,15 @@ qs_status qs_state_reset(qs_state *s);
  * |psi> <- G_{ngates-1} ... G_0 |psi>  (Eq. sqgunitaryoperation for each
  * single-qubit gate; controlled form for CZ / CPHASE).  Every gate is
  * validated first (kind < 9, qubits < n, q0 != q1 for two-qubit kinds); on
- * error nothing is launched.  `opts` may be NULL. */
+ * error nothing is launched.  `opts` may be NULL.
+ * opts->autotune = 1 (fused modes, tile_log2 = 0): the first call for a
+ * given (device, n, dtype, mode, precision) times this gate list on a
+ * scratch copy of the state (allocated stream-ordered for the duration of
+ * the call) with every candidate tile size (9..13 qubits, 12 for
+ * complex128, at most n) and, when QS_MODE_FUSED_TC was asked for, the
+ * tensor-core form; the fastest is cached for the rest of the process and
+ * used by this and later calls.  States of more than 26 qubits use the
+ * defaults (13-qubit tiles, the fastest measured from 20 qubits on). */
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
                            const qs_opts *opts);
 
@@ -408,6 +431,29 @@ qs_status qs_batch_apply(qs_batch *b, const qs_gate *gates, const uint64_t *offs
 /* Device pointer of instance i's amplitudes (canonical order). */
 qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps);
 
+/* Options of later runs of the batch (the paper has no counterpart; a
+ * throughput knob of the ensemble engine): opts->mode must be
+ * QS_MODE_FUSED (the batched pass has no tensor-core form:
+ * QS_ERR_UNSUPPORTED for QS_MODE_FUSED_TC); opts->tile_log2 in 5..13 fixes
+ * the tile size of every instance (0 = the planner's default, 13 qubits or
+ * n if smaller); opts->autotune = 1 lets the library choose the tile size
+ * per instance size n instead: on the next run it times the lockstep rounds
+ * of the batch's own instances of each size n with every candidate tile
+ * size (9..13 qubits, at most n) on their own state memory (CUDA events;
+ * one untimed and one timed run per candidate), keeps the fastest, and
+ * caches the choice per (device, n) for the rest of the process, so later
+ * batches with instances of a size already seen skip the timing.  NULL
+ * restores the defaults.  The next run replans.  Host only. */
+qs_status qs_batch_set_options(qs_batch *b, const qs_opts *opts);
+
+/* After a run: tile_log2[i] (count entries, may be NULL) receives the tile
+ * size of instance i's passes (0 when its list is only the Hadamard layer),
+ * *run_bytes (may be NULL) the algorithmic HBM bytes of one run: 16 bytes
+ * per amplitude per pass, plus the initial-state write and the statistics
+ * read (8 bytes per amplitude each).  QS_ERR_INVALID_ARG before the first
+ * run.  Host only. */
+qs_status qs_batch_plan_info(const qs_batch *b, int *tile_log2, double *run_bytes);
+
 qs_status qs_batch_destroy(qs_batch *b);
 
 /* Copies the amplitudes to / from a host buffer of 2^n amplitudes in
@@ -436,6 +482,16 @@ qs_status qs_state_copy_in(qs_state *s, const void *host_amps);
 qs_status qs_circuit_generate(int rows, int cols, const uint8_t *dead,
                               int depth, uint64_t seed, qs_gate *out,
                               size_t *ngates);
+
+/* Measurement support (no counterpart in the paper): the rate of fused
+ * multiply-adds this GPU sustains, the denominator of the roofline of
+ * arithmetic-bound kernels.  kind 0: scalar FP32, 1: packed FP32x2 (two
+ * FMAs per instruction lane), 2: FP64.  Runs a few milliseconds of
+ * independent FMA chains on every SM (64 warps each) on cuda_stream (NULL =
+ * legacy default stream), timed with CUDA events; *fma_per_s receives FMAs
+ * per second (flops / 2).  Synchronous; allocates a small output buffer
+ * stream-ordered.  QS_ERR_INVALID_ARG for another kind. */
+qs_status qs_alu_rate(int kind, void *cuda_stream, double *fma_per_s);
 
 #ifdef __cplusplus
 }

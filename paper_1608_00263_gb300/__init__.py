@@ -14,12 +14,14 @@ import numpy as np
 from . import _native as N
 from ._native import (GATE_DTYPE, QSError, QS_C64, QS_C128, QS_H, QS_X_HALF, QS_Y_HALF, QS_T,
                       QS_CZ, QS_RX, QS_RY, QS_RZ, QS_CPHASE, QS_MODE_PLAIN, QS_MODE_FUSED,
-                      QS_MODE_FUSED_TC, QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3)
+                      QS_MODE_FUSED_TC, QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3,
+                      QS_PREC_BF16X6, QS_PREC_TF32X3, QS_PREC_TF32)
 
 __all__ = [
     "GATE_DTYPE", "QSError", "QS_C64", "QS_C128", "QS_H", "QS_X_HALF", "QS_Y_HALF", "QS_T",
     "QS_CZ", "QS_RX", "QS_RY", "QS_RZ", "QS_CPHASE", "QS_MODE_PLAIN", "QS_MODE_FUSED",
     "QS_MODE_FUSED_TC", "QS_PREC_DEFAULT", "QS_PREC_FP16X3", "QS_PREC_BF16X3",
+    "QS_PREC_BF16X6", "QS_PREC_TF32X3", "QS_PREC_TF32",
     "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
@@ -29,7 +31,7 @@ __all__ = [
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
     "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit", "qs_batch_apply",
-    "library_path",
+    "qs_alu_rate", "qs_batch_set_options", "qs_batch_plan_info", "library_path",
 ]
 
 
@@ -62,8 +64,8 @@ def _stream(stream):
     return stream.cuda_stream
 
 
-def _opts(mode, precision, k, tile_log2):
-    return N.qs_opts(mode, precision, k, tile_log2, 0)
+def _opts(mode, precision, k, tile_log2, autotune=0):
+    return N.qs_opts(mode, precision, k, tile_log2, autotune)
 
 
 def _gates(gates):
@@ -107,9 +109,10 @@ def qs_state_reset(h):
     N.check(N.lib().qs_state_reset(h))
 
 
-def qs_apply_circuit(h, gates, mode=QS_MODE_FUSED, precision=QS_PREC_DEFAULT, k=0, tile_log2=0):
+def qs_apply_circuit(h, gates, mode=QS_MODE_FUSED, precision=QS_PREC_DEFAULT, k=0, tile_log2=0,
+                     autotune=0):
     g = _gates(gates)
-    o = _opts(mode, precision, k, tile_log2)
+    o = _opts(mode, precision, k, tile_log2, autotune)
     N.check(N.lib().qs_apply_circuit(h, g.ctypes.data if g.size else None, g.size, ctypes.byref(o)))
 
 
@@ -354,3 +357,27 @@ def qs_cycle_statistics(h, gates, kmax=10, mode=QS_MODE_FUSED):
     N.check(N.lib().qs_cycle_statistics(h, gp, g.size, ctypes.byref(o), kmax, out.ctypes.data, cnt.value,
                                         ctypes.byref(cnt)))
     return out
+
+
+def qs_alu_rate(kind, stream=None):
+    """Fused multiply-adds per second this GPU sustains (kind 0: FP32, 1:
+    packed FP32x2, 2: FP64); see include/qs.h."""
+    r = ctypes.c_double()
+    N.check(N.lib().qs_alu_rate(kind, _stream(stream), ctypes.byref(r)))
+    return r.value
+
+
+def qs_batch_set_options(b, tile_log2=0, autotune=0, mode=QS_MODE_FUSED):
+    """Tile size (fixed, or autotuned per instance size) of later runs; see
+    include/qs.h."""
+    o = _opts(mode, QS_PREC_DEFAULT, 0, tile_log2, autotune)
+    N.check(N.lib().qs_batch_set_options(b, ctypes.byref(o)))
+
+
+def qs_batch_plan_info(b):
+    """(tile sizes per instance, algorithmic bytes of one run) of the last
+    prepared run."""
+    t = np.zeros(_batch_sizes[b], dtype=np.int32)
+    by = ctypes.c_double()
+    N.check(N.lib().qs_batch_plan_info(b, t.ctypes.data, ctypes.byref(by)))
+    return t, by.value

@@ -17,7 +17,8 @@ QS_OK, QS_ERR_INVALID_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_UNSUP
 QS_C64, QS_C128 = 0, 1
 (QS_H, QS_X_HALF, QS_Y_HALF, QS_T, QS_CZ, QS_RX, QS_RY, QS_RZ, QS_CPHASE) = range(9)
 QS_MODE_PLAIN, QS_MODE_FUSED, QS_MODE_FUSED_TC = 0, 1, 2
-QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3 = 0, 1, 2
+(QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3, QS_PREC_BF16X6, QS_PREC_TF32X3,
+ QS_PREC_TF32) = range(6)
 
 GATE_DTYPE = np.dtype([("kind", np.uint8), ("q0", np.uint8), ("q1", np.uint8),
                        ("pad", np.uint8), ("cycle", np.uint32), ("theta", np.float64)])
@@ -89,6 +90,9 @@ SIGNATURES = {
     "qs_state_copy_in": (ctypes.c_int, [P, P]),
     "qs_circuit_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, U64, P,
                                            ctypes.POINTER(ctypes.c_size_t)]),
+    "qs_alu_rate": (ctypes.c_int, [ctypes.c_int, P, PD]),
+    "qs_batch_set_options": (ctypes.c_int, [P, ctypes.POINTER(qs_opts)]),
+    "qs_batch_plan_info": (ctypes.c_int, [P, P, PD]),
 }
 
 _lib = None

@@ -3,6 +3,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "qs_device.cuh"
@@ -278,21 +281,113 @@ static qs_status slot_in_use(qs_state *s, DevicePlanSlot *c)
     return QS_OK;
 }
 
+// ---- autotune (qs_opts.autotune = 1) ----
+// Fused forms chosen per (device, n, dtype, requested mode, precision) by
+// timing candidate tile sizes -- and, for QS_MODE_FUSED_TC, the register
+// form at the default tile -- on a scratch copy of the state; cached for the
+// rest of the process.  States above kAutotuneMaxQubits keep the defaults
+// (13-qubit tiles, the fastest measured from 20 qubits on).
+constexpr int kAutotuneMaxQubits = 26;
+static std::mutex g_autotune_mu;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_autotune;   // -> (mode, tile)
+
+static qs_status autotune_opts(qs_state *s, const qs_gate *gates, size_t ngates, const qs_opts *o, qs_opts *out)
+{
+    *out = *o;
+    out->autotune = 0;
+    out->tile_log2 = 0;
+    if (o->mode == QS_MODE_PLAIN || s->n > kAutotuneMaxQubits) return QS_OK;
+    const auto key = std::make_tuple(s->device, s->n, (int)s->dt, o->mode, o->precision);
+    {
+        std::lock_guard<std::mutex> lock(g_autotune_mu);
+        auto it = g_autotune.find(key);
+        if (it != g_autotune.end()) {
+            out->mode = it->second.first;
+            out->tile_log2 = it->second.second;
+            return QS_OK;
+        }
+    }
+    const int rb = s->dt == QS_C128 ? 4 : 5;
+    std::vector<std::pair<int, int>> cand;            // (mode, tile)
+    const int tmax = std::min(s->n, s->dt == QS_C128 ? 12 : 13);
+    for (int t = std::max(rb, std::min(9, s->n)); t <= tmax; ++t) cand.push_back({QS_MODE_FUSED, t});
+    if (o->mode == QS_MODE_FUSED_TC && s->dt == QS_C64 && s->n >= 13) cand.push_back({QS_MODE_FUSED_TC, 13});
+    if (cand.size() <= 1) return QS_OK;
+    // scratch copy of the state, evolved by every candidate in turn
+    const size_t bytes = ((size_t)1 << s->n) * dtype_bytes(s->dt);
+    void *scratch = nullptr;
+    QS_CUDA_TRY(cudaMallocAsync(&scratch, bytes, s->stream));
+    qs_state *t = nullptr;
+    qs_status rc = materialize(s);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(scratch, s->amps, bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) rc = set_error(QS_ERR_CUDA, "autotune copy: %s", cudaGetErrorString(e));
+    }
+    if (!rc) rc = qs_state_attach(s->n, s->dt, scratch, s->stream, &t);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = set_error(QS_ERR_CUDA, "autotune events");
+    std::pair<int, int> best{0, 0};
+    float best_ms = 3.4e38f;
+    for (size_t c = 0; !rc && c < cand.size(); ++c) {
+        qs_opts co = *o;
+        co.autotune = 0;
+        co.mode = cand[c].first;
+        co.tile_log2 = cand[c].first == QS_MODE_FUSED ? cand[c].second : 0;
+        float ms = 0;
+        if ((rc = qs_apply_circuit(t, gates, ngates, &co))) break;     // untimed: plans, uploads
+        cudaEventRecord(e0, s->stream);
+        if ((rc = qs_apply_circuit(t, gates, ngates, &co))) break;
+        cudaEventRecord(e1, s->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = set_error(QS_ERR_CUDA, "autotune timing");
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (t) qs_state_destroy(t);
+    cudaFreeAsync(scratch, s->stream);
+    if (rc) return rc;
+    clear_error();
+    out->mode = best.first;
+    out->tile_log2 = best.first == QS_MODE_FUSED ? best.second : 0;
+    std::lock_guard<std::mutex> lock(g_autotune_mu);
+    g_autotune[key] = best;
+    return QS_OK;
+}
+
 extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
                                       const qs_opts *opts)
 {
     clear_error();
     if (qs_status st = check_state(s)) return st;
     if (qs_status st = validate_gates(s->n, gates, ngates)) return st;
-    if (opts && opts->autotune != 0) return set_error(QS_ERR_UNSUPPORTED, "autotune is not built");
+    if (opts && opts->autotune != 0 && opts->autotune != 1)
+        return set_error(QS_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    qs_opts tuned;
+    if (opts && opts->autotune == 1 && ngates) {
+        if (opts->tile_log2) return set_error(QS_ERR_INVALID_ARG, "autotune chooses the tile size: tile_log2 must be 0");
+        if (opts->mode == QS_MODE_FUSED_TC && (opts->precision < QS_PREC_DEFAULT || opts->precision > QS_PREC_TF32))
+            return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d is not a qs_precision", opts->precision);
+        if (opts->mode != QS_MODE_PLAIN && opts->mode != QS_MODE_FUSED && opts->mode != QS_MODE_FUSED_TC)
+            return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", opts->mode);
+        DeviceGuard g(s->device);
+        if (qs_status st = autotune_opts(s, gates, ngates, opts, &tuned)) return st;
+        opts = &tuned;
+    }
     const int mode = opts ? opts->mode : QS_MODE_FUSED;
     if (mode != QS_MODE_PLAIN && mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
         return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
     const int rb = s->dt == QS_C128 ? 4 : 5;
     if (mode == QS_MODE_FUSED && opts && opts->tile_log2 && (opts->tile_log2 < rb || opts->tile_log2 > rb + 8))
         return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside %d..%d", opts->tile_log2, rb, rb + 8);
-    if (mode == QS_MODE_FUSED_TC && opts && opts->precision != QS_PREC_DEFAULT && opts->precision != QS_PREC_FP16X3)
-        return set_error(QS_ERR_UNSUPPORTED, "tensor-core precision %d is not built", opts->precision);
+    if (mode == QS_MODE_FUSED_TC && opts && (opts->precision < QS_PREC_DEFAULT || opts->precision > QS_PREC_TF32))
+        return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d is not a qs_precision", opts->precision);
     if (ngates == 0) return QS_OK;
     DeviceGuard g(s->device);
     ++s->version;
@@ -333,6 +428,8 @@ extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_
     if (ngates == 0 || mode == QS_MODE_PLAIN || s->n < rb) return QS_OK;
     if (mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
         return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (mode == QS_MODE_FUSED_TC && opts && (opts->precision < QS_PREC_DEFAULT || opts->precision > QS_PREC_TF32))
+        return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d is not a qs_precision", opts->precision);
     DeviceGuard g(s->device);
     // a leading Hadamard layer is written as the uniform state when the
     // circuit starts from |0...0> (the usual reset + apply): plan the rest

@@ -13,7 +13,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "qs_device.cuh"
@@ -71,6 +74,14 @@ struct qs_batch {
     cudaGraphExec_t exec = nullptr;
     int kmax_last = 0;
     std::vector<double> host_sums;
+    double round_bytes = 0;           // algorithmic bytes of the prepared rounds
+    // options (qs_batch_set_options): a fixed tile size for every instance
+    // (0 = the planner's default), or the autotuned size of each n
+    int tile_log2 = 0;
+    int autotune = 0;
+    std::map<int, int> tile_for_n;    // tile bits chosen per instance size (autotune)
+    std::map<int, double> tune_ms;     // the winner's time per size class
+    std::vector<int> tile_used;        // tile bits of each instance's plan (0: no pass)
 };
 
 static void batch_release_plan(qs_batch *b)
@@ -83,6 +94,216 @@ static void batch_release_plan(qs_batch *b)
     b->dev = nullptr;
     b->part = b->sums = nullptr;
     b->ready = false;
+}
+
+// Tile sizes chosen by the autotuner, per (device, qubits): a process-wide
+// cache, so later batches with instances of the same size skip the timing.
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tuned_tile;
+
+// Plans for instances `idx` with tile size tbits[i] (0 = default), on host
+// threads.  plans[i] is left empty for instances not listed or whose list
+// is only the Hadamard layer.
+static qs_status plan_instances(const qs_batch *b, const qs_gate *gates, const uint64_t *offsets,
+                                const std::vector<size_t> &hl, const std::vector<int> &idx,
+                                const std::vector<int> &tbits, std::vector<Plan> *plans)
+{
+    plans->assign(b->count, Plan());
+    std::vector<qs_status> st(idx.size(), QS_OK);
+    std::vector<std::string> msg(idx.size());
+    const unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (unsigned w = 0; w < nth; ++w)
+        pool.emplace_back([&, w]() {
+            for (size_t k = w; k < idx.size(); k += nth) {
+                const int i = idx[k];
+                const size_t ng = (size_t)(offsets[i + 1] - offsets[i]) - hl[i];
+                if (ng == 0) continue;
+                qs_opts o{};
+                o.mode = QS_MODE_FUSED;
+                o.tile_log2 = tbits[i];
+                PlanParams pp = default_plan_params(b->n[i], QS_C64, &o);
+                st[k] = build_plan(pp, gates + offsets[i] + hl[i], ng, &(*plans)[i]);
+                if (st[k]) msg[k] = last_error_cstr();
+            }
+        });
+    for (auto &t : pool) t.join();
+    for (size_t k = 0; k < idx.size(); ++k)
+        if (st[k]) return set_error(st[k], "instance %d: %s", idx[k], msg[k].c_str());
+    return QS_OK;
+}
+
+// Lockstep rounds of the listed instances: the concatenated plans and the
+// work items (instance, pass, <= kItemTiles tiles) of every (round, tile
+// size), laid out for one device buffer.
+struct RoundLaunch {
+    int round, tbits;
+    size_t first, count;
+};
+struct Rounds {
+    std::vector<DevPass> passes;
+    std::vector<DevPhase> phases;
+    std::vector<DevOp> ops;
+    std::vector<unsigned char> items;
+    std::vector<RoundLaunch> launches;
+    double bytes = 0;                // algorithmic bytes (16 per amplitude per pass)
+};
+
+static void build_rounds(const qs_batch *b, const std::vector<Plan> &plans, const std::vector<int> &idx,
+                         Rounds *R)
+{
+    *R = Rounds();
+    std::vector<int> first_pass(b->count, 0);
+    int max_passes = 0;
+    for (int i : idx) {
+        first_pass[i] = (int)R->passes.size();
+        const int pb = (int)R->phases.size(), ob = (int)R->ops.size();
+        for (DevPass p : plans[i].passes) {
+            p.phase_begin += pb;
+            R->passes.push_back(p);
+        }
+        for (DevPhase h : plans[i].phases) {
+            h.op_begin += ob;
+            h.op_end += ob;
+            R->phases.push_back(h);
+        }
+        R->ops.insert(R->ops.end(), plans[i].ops.begin(), plans[i].ops.end());
+        max_passes = std::max(max_passes, (int)plans[i].passes.size());
+        R->bytes += (double)plans[i].passes.size() * 16.0 * std::ldexp(1.0, b->n[i]);
+    }
+    const size_t isz = batch_item_bytes();
+    for (int r = 0; r < max_passes; ++r)
+        for (int tb = 5; tb <= 13; ++tb) {
+            RoundLaunch L{r, tb, R->items.size() / isz, 0};
+            for (int i : idx) {
+                if (r >= (int)plans[i].passes.size()) continue;
+                const DevPass &p = plans[i].passes[r];
+                if (p.t != tb) continue;
+                const uint64_t ntiles = 1ULL << (b->n[i] - p.t);
+                for (uint64_t t0 = 0; t0 < ntiles; t0 += kItemTiles) {
+                    const uint64_t t1 = std::min<uint64_t>(ntiles, t0 + kItemTiles);
+                    R->items.resize(R->items.size() + isz);
+                    batch_item_fill(R->items.data() + R->items.size() - isz, b->off[i],
+                                    (uint32_t)(first_pass[i] + r), (uint32_t)t0, (uint32_t)t1);
+                    ++L.count;
+                }
+            }
+            if (L.count) R->launches.push_back(L);
+        }
+}
+
+// Section offsets of a Rounds layout in a device buffer: passes | phases |
+// ops | items, each 256-byte aligned.
+struct RoundOffsets {
+    size_t pass, phase, op, item, total;
+};
+static RoundOffsets round_offsets(const Rounds &R)
+{
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    RoundOffsets o;
+    o.pass = 0;
+    o.phase = align(o.pass + R.passes.size() * sizeof(DevPass));
+    o.op = align(o.phase + R.phases.size() * sizeof(DevPhase));
+    o.item = align(o.op + R.ops.size() * sizeof(DevOp));
+    o.total = align(o.item + R.items.size());
+    return o;
+}
+
+static void round_pack(const Rounds &R, const RoundOffsets &o, unsigned char *host)
+{
+    std::memcpy(host + o.pass, R.passes.data(), R.passes.size() * sizeof(DevPass));
+    std::memcpy(host + o.phase, R.phases.data(), R.phases.size() * sizeof(DevPhase));
+    std::memcpy(host + o.op, R.ops.data(), R.ops.size() * sizeof(DevOp));
+    if (!R.items.empty()) std::memcpy(host + o.item, R.items.data(), R.items.size());
+}
+
+static qs_status launch_rounds(const qs_batch *b, cudaStream_t st, const Rounds &R, const RoundOffsets &o,
+                               const unsigned char *D)
+{
+    const size_t isz = batch_item_bytes();
+    for (const RoundLaunch &L : R.launches)
+        if (qs_status rs = launch_batch_round(st, b->num_sms, b->amps, D + o.item + L.first * isz, (int)L.count,
+                                              L.tbits, (const DevPass *)(D + o.pass),
+                                              (const DevPhase *)(D + o.phase), (const DevOp *)(D + o.op)))
+            return rs;
+    return QS_OK;
+}
+
+// Autotuner: for every instance size n not yet in the cache, time the
+// lockstep rounds of the batch's own instances of that size (their real
+// circuits, on their own state memory, which the run resets afterwards)
+// with each candidate tile size -- 9..13 qubits, capped at n -- and keep
+// the fastest.  One untimed and one timed run (CUDA events) per candidate.
+static qs_status batch_autotune(qs_batch *b, const qs_gate *gates, const uint64_t *offsets,
+                                const std::vector<size_t> &hl)
+{
+    std::map<int, std::vector<int>> by_n;
+    for (int i = 0; i < b->count; ++i) by_n[b->n[i]].push_back(i);
+    if (qs_status s0 = batch_kernel_setup()) return s0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QS_CUDA_TRY(cudaEventCreate(&e0));
+    QS_CUDA_TRY(cudaEventCreate(&e1));
+    qs_status rc = QS_OK;
+    for (auto &kv : by_n) {
+        const int n = kv.first;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned_tile.find({b->device, n});
+            if (it != g_tuned_tile.end()) {
+                b->tile_for_n[n] = it->second;
+                continue;
+            }
+        }
+        int best_t = 0;
+        double best_ms = 1e300;
+        for (int t = std::min(9, n); t <= std::min(13, n); ++t) {
+            std::vector<int> tb(b->count, t);
+            std::vector<Plan> plans;
+            if ((rc = plan_instances(b, gates, offsets, hl, kv.second, tb, &plans))) break;
+            Rounds R;
+            build_rounds(b, plans, kv.second, &R);
+            if (R.launches.empty()) break;          // only Hadamard layers: nothing to time
+            const RoundOffsets o = round_offsets(R);
+            std::vector<unsigned char> host(o.total, 0);
+            round_pack(R, o, host.data());
+            void *dev = nullptr;
+            cudaError_t e = cudaMalloc(&dev, o.total);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                rc = set_error(QS_ERR_OOM, "autotune plan buffer: %s", cudaGetErrorString(e));
+                break;
+            }
+            e = cudaMemcpy(dev, host.data(), o.total, cudaMemcpyHostToDevice);
+            float ms = 0;
+            if (e == cudaSuccess) rc = launch_rounds(b, b->cap_stream, R, o, (const unsigned char *)dev);
+            if (e == cudaSuccess && !rc) {
+                cudaEventRecord(e0, b->cap_stream);
+                rc = launch_rounds(b, b->cap_stream, R, o, (const unsigned char *)dev);
+                cudaEventRecord(e1, b->cap_stream);
+                if (!rc) e = cudaEventSynchronize(e1);
+                if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            cudaError_t ef = cudaStreamSynchronize(b->cap_stream);
+            cudaFree(dev);
+            if (e == cudaSuccess) e = ef;
+            if (!rc && e != cudaSuccess) rc = set_error(QS_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
+            if (rc) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_t = t;
+            }
+        }
+        if (rc) break;
+        if (best_t) {
+            b->tile_for_n[n] = best_t;
+            b->tune_ms[n] = best_ms;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tuned_tile[{b->device, n}] = best_t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 extern "C" qs_status qs_batch_create(int count, const int *nqubits, void *cuda_stream, qs_batch **out)
@@ -117,6 +338,40 @@ extern "C" qs_status qs_batch_create(int count, const int *nqubits, void *cuda_s
         return set_error(QS_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     }
     *out = b;
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_set_options(qs_batch *b, const qs_opts *opts)
+{
+    clear_error();
+    if (!b) return set_error(QS_ERR_INVALID_ARG, "batch is NULL");
+    const int mode = opts ? opts->mode : QS_MODE_FUSED;
+    if (mode == QS_MODE_FUSED_TC)
+        return set_error(QS_ERR_UNSUPPORTED, "the batched pass has no tensor-core form");
+    if (mode != QS_MODE_FUSED) return set_error(QS_ERR_INVALID_ARG, "batch mode must be QS_MODE_FUSED");
+    const int t = opts ? opts->tile_log2 : 0, at = opts ? opts->autotune : 0;
+    if (t != 0 && (t < 5 || t > 13)) return set_error(QS_ERR_INVALID_ARG, "tile_log2 %d outside 5..13", t);
+    if (at != 0 && at != 1) return set_error(QS_ERR_INVALID_ARG, "autotune must be 0 or 1");
+    if (at && t) return set_error(QS_ERR_INVALID_ARG, "autotune chooses the tile size: tile_log2 must be 0");
+    b->tile_log2 = t;
+    b->autotune = at;
+    b->tile_for_n.clear();
+    b->tune_ms.clear();
+    b->ready = false;                 // the next run replans
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_plan_info(const qs_batch *b, int *tile_log2, double *run_bytes)
+{
+    clear_error();
+    if (!b) return set_error(QS_ERR_INVALID_ARG, "batch is NULL");
+    if (!b->ready) return set_error(QS_ERR_INVALID_ARG, "no run has been prepared yet");
+    if (tile_log2)
+        for (int i = 0; i < b->count; ++i) tile_log2[i] = b->tile_used[i];
+    if (run_bytes) {
+        // rounds, the initial states (one write) and the statistics (one read)
+        *run_bytes = b->round_bytes + 16.0 * (double)b->total;
+    }
     return QS_OK;
 }
 
@@ -201,74 +456,26 @@ extern "C" qs_status qs_batch_mean_probabilities(qs_batch *b, double *out)
 static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)
 {
     const int C = b->count;
-    std::vector<Plan> plans(C);
-    std::vector<qs_status> st(C, QS_OK);
-    std::vector<std::string> msg(C);
     // an instance whose circuit opens with a Hadamard layer starts from the
     // uniform state (written by k_batch_init) and plans the rest
     std::vector<size_t> hl(C);
     for (int i = 0; i < C; ++i)
         hl[i] = leading_h_layer(gates + offsets[i], (size_t)(offsets[i + 1] - offsets[i]), b->n[i]);
-    const unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> pool;
-    for (unsigned w = 0; w < nth; ++w)
-        pool.emplace_back([&, w]() {
-            for (int i = (int)w; i < C; i += (int)nth) {
-                const size_t ng = (size_t)(offsets[i + 1] - offsets[i]) - hl[i];
-                if (ng == 0) continue;
-                PlanParams pp = default_plan_params(b->n[i], QS_C64, nullptr);
-                st[i] = build_plan(pp, gates + offsets[i] + hl[i], ng, &plans[i]);
-                if (st[i]) msg[i] = last_error_cstr();
-            }
-        });
-    for (auto &t : pool) t.join();
-    for (int i = 0; i < C; ++i)
-        if (st[i]) return set_error(st[i], "instance %d: %s", i, msg[i].c_str());
-
-    // concatenate plans (rebase phase and op indices)
-    std::vector<DevPass> passes;
-    std::vector<DevPhase> phases;
-    std::vector<DevOp> ops;
-    std::vector<int> first_pass(C);
-    int max_passes = 0;
+    if (b->autotune)
+        if (qs_status s0 = batch_autotune(b, gates, offsets, hl)) return s0;
+    std::vector<int> all(C), tbits(C, b->tile_log2);
     for (int i = 0; i < C; ++i) {
-        first_pass[i] = (int)passes.size();
-        const int pb = (int)phases.size(), ob = (int)ops.size();
-        for (DevPass p : plans[i].passes) {
-            p.phase_begin += pb;
-            passes.push_back(p);
-        }
-        for (DevPhase h : plans[i].phases) {
-            h.op_begin += ob;
-            h.op_end += ob;
-            phases.push_back(h);
-        }
-        ops.insert(ops.end(), plans[i].ops.begin(), plans[i].ops.end());
-        max_passes = std::max(max_passes, (int)plans[i].passes.size());
+        all[i] = i;
+        if (b->autotune && b->tile_for_n.count(b->n[i])) tbits[i] = b->tile_for_n[b->n[i]];
     }
-    // work items per (round, tile bits)
-    struct Launch { int round, tbits; size_t first, count; };
-    std::vector<Launch> launches;
-    std::vector<unsigned char> items;
-    const size_t isz = batch_item_bytes();
-    for (int r = 0; r < max_passes; ++r)
-        for (int tb = 5; tb <= 13; ++tb) {
-            Launch L{r, tb, items.size() / isz, 0};
-            for (int i = 0; i < C; ++i) {
-                if (r >= (int)plans[i].passes.size()) continue;
-                const DevPass &p = plans[i].passes[r];
-                if (p.t != tb) continue;
-                const uint64_t ntiles = 1ULL << (b->n[i] - p.t);
-                for (uint64_t t0 = 0; t0 < ntiles; t0 += kItemTiles) {
-                    const uint64_t t1 = std::min<uint64_t>(ntiles, t0 + kItemTiles);
-                    items.resize(items.size() + isz);
-                    batch_item_fill(items.data() + items.size() - isz, b->off[i], (uint32_t)(first_pass[i] + r),
-                                    (uint32_t)t0, (uint32_t)t1);
-                    ++L.count;
-                }
-            }
-            if (L.count) launches.push_back(L);
-        }
+    std::vector<Plan> plans;
+    if (qs_status s0 = plan_instances(b, gates, offsets, hl, all, tbits, &plans)) return s0;
+    Rounds R;
+    build_rounds(b, plans, all, &R);
+    b->round_bytes = R.bytes;
+    b->tile_used.assign(C, 0);
+    for (int i = 0; i < C; ++i)
+        if (!plans[i].passes.empty()) b->tile_used[i] = plans[i].passes[0].t;
     // statistics items
     std::vector<uint64_t> s_off, s_cnt;
     std::vector<float> s_scale, s_fill, s_first;
@@ -288,12 +495,11 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     first_item[C] = (int)s_off.size();
     const int nsi = (int)s_off.size();
 
-    // one device buffer: passes | phases | ops | items | s_off | s_cnt | s_scale | first_item | inst_off
+    // one device buffer: rounds (passes | phases | ops | items) | s_off |
+    // s_cnt | s_scale | first_item | inst_off | fill | first
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t o_pass = 0, o_ph = align(o_pass + passes.size() * sizeof(DevPass));
-    size_t o_op = align(o_ph + phases.size() * sizeof(DevPhase));
-    size_t o_it = align(o_op + ops.size() * sizeof(DevOp));
-    size_t o_so = align(o_it + items.size());
+    const RoundOffsets ro = round_offsets(R);
+    size_t o_so = ro.total;
     size_t o_sc = align(o_so + s_off.size() * 8);
     size_t o_ss = align(o_sc + s_cnt.size() * 8);
     size_t o_fi = align(o_ss + s_scale.size() * 4);
@@ -302,10 +508,7 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     size_t o_v1 = align(o_vf + s_fill.size() * 4);
     size_t total = align(o_v1 + s_first.size() * 4);
     std::vector<unsigned char> host(total, 0);
-    std::memcpy(host.data() + o_pass, passes.data(), passes.size() * sizeof(DevPass));
-    std::memcpy(host.data() + o_ph, phases.data(), phases.size() * sizeof(DevPhase));
-    std::memcpy(host.data() + o_op, ops.data(), ops.size() * sizeof(DevOp));
-    if (!items.empty()) std::memcpy(host.data() + o_it, items.data(), items.size());
+    round_pack(R, ro, host.data());
     std::memcpy(host.data() + o_so, s_off.data(), s_off.size() * 8);
     std::memcpy(host.data() + o_sc, s_cnt.data(), s_cnt.size() * 8);
     std::memcpy(host.data() + o_ss, s_scale.data(), s_scale.size() * 4);
@@ -327,12 +530,7 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     k_batch_init<<<std::min(nsi, 16 * b->num_sms), 256, 0, b->cap_stream>>>(
         b->amps, (const uint64_t *)(D + o_so), (const uint64_t *)(D + o_sc), (const float *)(D + o_vf),
         (const float *)(D + o_v1), nsi);
-    for (const Launch &L : launches) {
-        rs = launch_batch_round(b->cap_stream, b->num_sms, b->amps, D + o_it + L.first * isz, (int)L.count, L.tbits,
-                                (const DevPass *)(D + o_pass), (const DevPhase *)(D + o_ph),
-                                (const DevOp *)(D + o_op));
-        if (rs) break;
-    }
+    rs = launch_rounds(b, b->cap_stream, R, ro, D);
     if (!rs)
         rs = launch_batch_stats(b->cap_stream, b->num_sms, b->amps, (const uint64_t *)(D + o_so),
                                 (const uint64_t *)(D + o_sc), (const float *)(D + o_ss), nsi,

@@ -23,6 +23,7 @@
 //   * Shared memory uses a 16-byte-granular XOR swizzle (linear over GF(2),
 //     so slot addresses are XORs of per-bit offsets) to spread the strided
 //     phase accesses over the banks.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstring>
@@ -321,6 +322,88 @@ __device__ __forceinline__ void exec_op(uint32_t code, V *a, uint64_t idx_th, ui
 #undef sel
 }
 
+// ---- Clifford+T interpreter: one dense byte code per op ----
+// The passes of the paper's circuits (H, X^1/2, Y^1/2, T, CZ) stage each op
+// as one byte from a dense range, so the interpreter's dispatch is one byte
+// load and one indexed branch; the one-op-per-case layout keeps the slots
+// in fixed registers as in exec_op.
+enum : uint32_t {
+    C_H = 0, C_XH = 5, C_YH = 10,     // + register bit
+    C_T = 15,                         // + register bit: T phase on the slots with the bit set
+    C_CZ = 20,                        // + index of the register-bit pair (cz_pair_index)
+    C_CZO = 30,                       // + register bit: sign on the slots with the bit set where
+                                      //   the op's selection outside the register set holds
+    C_Z = 35,                         // + register bit: unconditional sign
+    C_COUNT = 40
+};
+
+// Pairs (j, k), j < k < 5, numbered (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) ...
+__host__ __device__ __forceinline__ int cz_pair_index(int j, int k)
+{
+    return j * 4 - (j * (j + 1)) / 2 + (k - 1);
+}
+
+template <int RB, typename V, typename R, typename OpT>
+__device__ __forceinline__ void exec_ct(uint32_t code, V *a, uint64_t idx_th, const OpT *op)
+{
+    constexpr int NS = 1 << RB;
+    const R c = (R)0.70710678118654752440;
+    switch (code) {
+#define QS_J(J)                                                                          \
+    case C_H + J: reg_h<NS, (J < RB ? J : 0)>(a); break;                                 \
+    case C_XH + J: reg_xh<NS, (J < RB ? J : 0)>(a); break;                               \
+    case C_YH + J: reg_yh<NS, (J < RB ? J : 0)>(a); break;                               \
+    case C_T + J: reg_phase<NS, (1 << (J < RB ? J : 0))>(a, c, c, true); break;          \
+    case C_CZO + J: {                                                                    \
+        const uint64_t qm = op->qmask;                                                   \
+        reg_sign<NS, (1 << (J < RB ? J : 0))>(a, ((idx_th & qm) == qm) ? (R)-1 : (R)1);  \
+        break;                                                                           \
+    }                                                                                    \
+    case C_Z + J: reg_sign<NS, (1 << (J < RB ? J : 0))>(a, (R)-1); break;
+    QS_J(0) QS_J(1) QS_J(2) QS_J(3) QS_J(4)
+#undef QS_J
+#define QS_P(J, K) \
+    case C_CZ + (J * 4 - (J * (J + 1)) / 2 + (K - 1)): reg_sign<NS, ((1 << J) | (1 << K)) & (NS - 1)>(a, (R)-1); break;
+    QS_P(0, 1) QS_P(0, 2) QS_P(0, 3) QS_P(0, 4) QS_P(1, 2) QS_P(1, 3) QS_P(1, 4) QS_P(2, 3) QS_P(2, 4) QS_P(3, 4)
+#undef QS_P
+    default: break;
+    }
+}
+
+// Byte code of a staged op in the Clifford+T interpreter, or -1 when the op
+// needs the full interpreter (parameterised gates, general phases, a T
+// phase selected outside the register set).  Thread-uniform diagonal ops
+// (no register bits) run in the phase tail and get no code.
+__host__ __device__ inline int ct_code(const DevOp &d)
+{
+    // lowest / highest set bit and count of the 8-bit register mask
+    int lo = -1, hi = -1, bits = 0;
+    for (int b = 0; b < 8; ++b)
+        if ((d.rmask >> b) & 1) {
+            if (lo < 0) lo = b;
+            hi = b;
+            ++bits;
+        }
+    switch (d.type) {
+    case OP_H: return C_H + d.a;
+    case OP_XH: return C_XH + d.a;
+    case OP_YH: return C_YH + d.a;
+    case OP_PHASE: {
+        if (d.rmask == 0) return C_COUNT;          // tail
+        const bool tphase = d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
+        if (!tphase || bits != 1 || d.qmask) return -1;
+        return C_T + hi;
+    }
+    case OP_NEG: {
+        if (d.rmask == 0) return C_COUNT;          // tail
+        if (bits == 1) return (d.qmask ? C_CZO : C_Z) + hi;
+        if (bits == 2 && !d.qmask) return C_CZ + cz_pair_index(lo, hi);
+        return -1;
+    }
+    default: return -1;
+    }
+}
+
 // Deposits the low bits of x into the positions listed in pos[0..cnt).
 __device__ __forceinline__ uint64_t deposit(uint64_t x, const uint8_t *pos, int cnt)
 {
@@ -372,6 +455,7 @@ struct FusedSmem {
     SPhase ph[kMaxPhasesPerPass];
     SOp<R> ops[kMaxOpsPerPass];
     R phase[kMaxOpsPerPass][2];
+    uint8_t code8[kMaxOpsPerPass + 4];      // Clifford+T interpreter (FULL = false)
     SThread th[kMaxPhasesPerPass][kThreadsMax];
     uint64_t it_off[(1 << RB)];
 };
@@ -382,35 +466,74 @@ struct FusedSmem {
 // The 64 x 64 block unitary acts on the 6 block qubits of the tile for each
 // of the 128 columns (values of the other 7 tile qubits).  Realified:
 // D (128 x 128) = A (128 x 128) * B (128 x 128) with B[k][col] = re (k < 64)
-// or im (k >= 64) of the tile amplitude (block index k mod 64, col), scaled
-// by 2^14 / 2^ceil(d/2), d = deferred 1/sqrt2 factors pending in the tile:
-// |value| <= 2^(d/2) ||psi||, ||psi|| ~ 1, so scaled values stay below the
-// FP16 maximum (the scale is a power of two: exact).  Rows of A and D
-// interleave the real and imaginary parts of the 64 output block rows, so
-// neighbouring lanes of the epilogue store the two halves of one amplitude.
-// FP16 hi + lo splits of A and B, three products (hi hi, hi lo,
-// lo hi) and FP32 accumulation give ~22 significant bits.  A lives in
-// tensor memory (loaded once per CTA), B in shared memory (canonical
-// K-major layout without swizzle: 8 x 16-byte core matrices, 128 bytes
-// apart along K, 2048 bytes apart along the 128 columns), D in tensor memory.
-// Each CTA holds 256 tensor-memory columns (D, one block) and B takes the
-// tile's own shared buffer, so two CTAs share an SM and one CTA's tile
-// traffic and MMA wait overlap the other's work.
+// or im (k >= 64) of the tile amplitude (block index k mod 64, col).  Rows
+// of A and D interleave the real and imaginary parts of the 64 output block
+// rows, so neighbouring lanes of the epilogue store the two halves of one
+// amplitude.  A and B are split into the terms of the operand precision
+// (tc_prec: FP16 / BF16 / TF32, one to three terms) and the products of the
+// terms whose combined order is below the term count are accumulated in
+// FP32 in tensor memory: hi hi, hi lo, lo hi for two terms; all six pairs of
+// order <= 2 for three.  FP16 values are first scaled by 2^14 / 2^ceil(d/2),
+// d = deferred 1/sqrt2 factors pending in the tile: |value| <= 2^(d/2)
+// ||psi||, so scaled values stay below the FP16 maximum (a power of two:
+// exact); BF16 and TF32 carry FP32's exponent range and need no scale.
+// A lives in tensor memory (loaded once per CTA), B in shared memory
+// (canonical K-major layout without swizzle: 8 rows x 16-byte core
+// matrices, 128 bytes apart along K, 16 cores apart along the 128 columns),
+// D in tensor memory.  When A's terms fit 128 columns (FP16x3, BF16x3,
+// TF32) a CTA holds 256 columns and B takes the tile's own shared buffer,
+// so two CTAs share an SM and one CTA's tile traffic and MMA wait overlap
+// the other's work; BF16x6 and TF32x3 hold 512 columns and B continues past
+// the tile, one CTA per SM.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kTmemCols = 256;              // D: 0..127, block: 128..255 (two CTAs per SM)
-constexpr uint64_t kTcWaitNs = 1000000000ull;   // 1 s: far beyond 24 products of 128 x 128 x 16
+constexpr uint64_t kTcWaitNs = 1000000000ull;   // 1 s: far beyond 96 products of 128 x 128 x 16
+
+// Compile-time layout of a precision (TCP = qs_precision value, 1..5).
+template <int TCP>
+struct TcCfg {
+    static constexpr TcPrec P = tc_prec(TCP);
+    static constexpr int kTerms = P.terms;
+    static constexpr int kElem = P.elem_bytes;
+    static constexpr int kAColsPerTerm = 128 * kElem / 4;         // tensor-memory columns
+    static constexpr uint32_t kTmemCols = (128 + kTerms * kAColsPerTerm) <= 256 ? 256u : 512u;
+    static constexpr int kCtasPerSm = kTmemCols == 256 ? 2 : 1;
+    static constexpr int kBTermBytes = 128 * 128 * kElem;          // one term of B
+    // B's terms start in the tile's own buffer (its amplitudes are in
+    // registers while the terms are written) and continue into the dynamic
+    // shared memory that follows the tile when they exceed its 64 KB
+    static constexpr int kBExtraBytes = kTerms * kBTermBytes > 65536 ? kTerms * kBTermBytes - 65536 : 0;
+    static constexpr int kKSteps = 128 / (32 / kElem);             // MMAs along K per product
+    static constexpr uint32_t kSbo = 128u * (128 * kElem / 16);     // bytes between 8-column groups
+    static constexpr int kProducts = kTerms == 3 ? 6 : (kTerms == 2 ? 3 : 1);
+    // instruction descriptor: D FP32, A and B of the same format, K-major,
+    // N = 128, M = 128
+    static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)P.fmt << 7) | ((uint32_t)P.fmt << 10) |
+                                       ((128u >> 3) << 17) | ((128u >> 4) << 24);
+};
+
+// Dynamic shared memory of the tensor-core form: the tile, the part of B's
+// terms beyond the tile's 64 KB, and the slack that aligns the tile to 1024
+// bytes.
+__host__ __device__ constexpr size_t tc_dyn_smem(int tcp)
+{
+    return 65536 +
+           (tc_prec(tcp).terms * 128 * 128 * tc_prec(tcp).elem_bytes > 65536
+                ? (size_t)tc_prec(tcp).terms * 128 * 128 * tc_prec(tcp).elem_bytes - 65536
+                : 0) +
+           1024;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t sbo)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;     // leading (K) byte offset
-    d |= (uint64_t)((2048u >> 4) & 0x3FFF) << 32;    // stride (column) byte offset
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;      // stride (column) byte offset
     d |= (uint64_t)1 << 46;                          // descriptor version
     return d;
 }
@@ -441,14 +564,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r)
 }
 
 // Allocates tensor memory, loads this pass's block matrices (warps 0-3: one
-// row per thread) and initialises the completion barrier.
+// row per thread, every term) and initialises the completion barrier.
+template <int TCP>
 __device__ __forceinline__ void tc_setup(TcSmem &TS, const DevPhase *phases, int nph,
                                          const uint32_t *tc_words)
 {
+    using C = TcCfg<TCP>;
+    constexpr int kRowWords = C::kTerms * C::kAColsPerTerm;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&TS.tmem_base)),
-                     "r"(kTmemCols));
+                     "r"(C::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -464,12 +590,13 @@ __device__ __forceinline__ void tc_setup(TcSmem &TS, const DevPhase *phases, int
         int slot = 0;
         for (int ph = 0; ph < nph; ++ph) {
             if (phases[ph].kind != 1) continue;
-            const uint32_t *w = tc_words + (size_t)phases[ph].tc_block * kTcWordsPerBlock + (size_t)m * 128;
-            for (int c = 0; c < 4; ++c) {
+            const uint32_t *w = tc_words + (size_t)phases[ph].tc_block * tc_words_per_block(TCP) +
+                                (size_t)m * kRowWords;
+            for (int c = 0; c < kRowWords / 32; ++c) {
                 uint32_t r[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) r[j] = __ldg(w + c * 32 + j);
-                tmem_st32(tbase + ((uint32_t)(warp * 32) << 16) + 128 + 128 * slot + 32 * c, r);
+                tmem_st32(tbase + ((uint32_t)(warp * 32) << 16) + 128 + kRowWords * slot + 32 * c, r);
             }
             ++slot;
         }
@@ -480,27 +607,74 @@ __device__ __forceinline__ void tc_setup(TcSmem &TS, const DevPhase *phases, int
     asm volatile("tcgen05.fence::after_thread_sync;");
 }
 
+template <int TCP>
 __device__ __forceinline__ void tc_teardown(TcSmem &TS)
 {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(TS.tmem_base), "r"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(TS.tmem_base),
+                     "r"(TcCfg<TCP>::kTmemCols));
     }
 }
 
-// One block phase on the shared tile (all 256 threads).  The FP16 operands
-// take the tile's own buffer: every thread first moves its 32 amplitudes
-// (4 units of 8 block rows of one column) to registers, then writes their
-// hi / lo halves in the MMA layout; after the products complete, the
-// accumulator is scattered back into the tile.
-__device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, float2 *tile,
-                                         uint32_t parity, int *err_flag)
+// Term t of a split: the operand type's rounding of what terms 0..t-1 leave.
+// 16-bit formats work on pairs of values (one 32-bit word, lower value in
+// the low half); TF32 on single values (the low 13 bits of the word zero).
+template <int FMT>
+__device__ __forceinline__ uint32_t split_pair(float &r0, float &r1)
 {
-    const float sc = ldexpf(1.f, scale_exp), inv_sc = ldexpf(1.f, -scale_exp);
+    uint32_t w;
+    float2 v;
+    if (FMT == 0) {
+        const __half2 h = __floats2half2_rn(r0, r1);
+        w = *reinterpret_cast<const uint32_t *>(&h);
+        v = __half22float2(h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r0, r1);
+        w = *reinterpret_cast<const uint32_t *>(&h);
+        v = __bfloat1622float2(h);
+    }
+    r0 -= v.x;
+    r1 -= v.y;
+    return w;
+}
+
+__device__ __forceinline__ uint32_t split_tf32(float &r)
+{
+    uint32_t w;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w) : "f"(r));
+    r -= __uint_as_float(w);
+    return w;
+}
+
+template <int TCP>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t acc)
+{
+    if constexpr (TcCfg<TCP>::P.fmt == 2)
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                     "r"(a), "l"(bdesc), "r"(TcCfg<TCP>::kIdesc), "r"(acc));
+    else
+        asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                     "r"(a), "l"(bdesc), "r"(TcCfg<TCP>::kIdesc), "r"(acc));
+}
+
+// One block phase on the shared tile (all 256 threads).  Every thread first
+// moves its 32 amplitudes (4 units of 8 block rows of one column) to
+// registers, then writes their terms in the MMA layout (into the tile's own
+// buffer and, past its 64 KB, the shared memory after it); after the
+// products complete, the accumulator is scattered back into the tile.
+template <int TCP>
+__device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, float2 *tile,
+                                         unsigned char *bbuf, uint32_t parity, int *err_flag)
+{
+    using C = TcCfg<TCP>;
+    const float sc = C::P.scaled ? ldexpf(1.f, scale_exp) : 1.f;
+    const float inv_sc = C::P.scaled ? ldexpf(1.f, -scale_exp) : 1.f;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    unsigned char *bhi = reinterpret_cast<unsigned char *>(tile), *blo = bhi + 32768;
     const uint32_t *blk = TS.blk_off[slot], *col = TS.col_off[slot];
     float2 xv[4][8];
 #pragma unroll
@@ -511,32 +685,49 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
         for (int j = 0; j < 8; ++j) xv[i][j] = tile[base ^ blk[j]];
     }
     __syncthreads();
-    // ---- registers (FP32) -> B hi / lo (FP16, canonical layout) ----
+    // ---- registers (FP32) -> B terms (canonical K-major layout) ----
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int u = tid + 256 * i;
         const int nu = u & 127, bg = u >> 7;
-        uint32_t hre[4], him[4], lre[4], lim[4];
+        float rr[8], ri[8];
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-            float2 x0 = xv[i][j], x1 = xv[i][j + 1];
-            x0.x *= sc; x0.y *= sc; x1.x *= sc; x1.y *= sc;
-            const __half2 hr = __floats2half2_rn(x0.x, x1.x);
-            const __half2 hm = __floats2half2_rn(x0.y, x1.y);
-            const float2 hrf = __half22float2(hr), hmf = __half22float2(hm);
-            const __half2 lr = __floats2half2_rn(x0.x - hrf.x, x1.x - hrf.y);
-            const __half2 lm = __floats2half2_rn(x0.y - hmf.x, x1.y - hmf.y);
-            hre[j / 2] = *reinterpret_cast<const uint32_t *>(&hr);
-            him[j / 2] = *reinterpret_cast<const uint32_t *>(&hm);
-            lre[j / 2] = *reinterpret_cast<const uint32_t *>(&lr);
-            lim[j / 2] = *reinterpret_cast<const uint32_t *>(&lm);
+        for (int j = 0; j < 8; ++j) { rr[j] = xv[i][j].x * sc; ri[j] = xv[i][j].y * sc; }
+        if constexpr (C::kElem == 2) {
+            // 8 block rows = one 16-byte core row of K; imaginary K + 64
+            const uint32_t off_re = (uint32_t)(((nu >> 3) * 16 + bg) * 128 + (nu & 7) * 16);
+            const uint32_t off_im = off_re + 8 * 128;
+#pragma unroll
+            for (int t = 0; t < C::kTerms; ++t) {
+                uint32_t wr[4], wi[4];
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    wr[j / 2] = split_pair<C::P.fmt>(rr[j], rr[j + 1]);
+                    wi[j / 2] = split_pair<C::P.fmt>(ri[j], ri[j + 1]);
+                }
+                unsigned char *bt = bbuf + t * C::kBTermBytes;
+                *reinterpret_cast<uint4 *>(bt + off_re) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+                *reinterpret_cast<uint4 *>(bt + off_im) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            }
+        } else {
+            // TF32: 8 block rows = two 16-byte core rows of K (4 values each)
+            const uint32_t off_re = (uint32_t)((nu >> 3) * C::kSbo + (2 * bg) * 128 + (nu & 7) * 16);
+            const uint32_t off_im = off_re + 16 * 128;
+#pragma unroll
+            for (int t = 0; t < C::kTerms; ++t) {
+                uint32_t wr[8], wi[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    wr[j] = split_tf32(rr[j]);
+                    wi[j] = split_tf32(ri[j]);
+                }
+                unsigned char *bt = bbuf + t * C::kBTermBytes;
+                *reinterpret_cast<uint4 *>(bt + off_re) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+                *reinterpret_cast<uint4 *>(bt + off_re + 128) = make_uint4(wr[4], wr[5], wr[6], wr[7]);
+                *reinterpret_cast<uint4 *>(bt + off_im) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+                *reinterpret_cast<uint4 *>(bt + off_im + 128) = make_uint4(wi[4], wi[5], wi[6], wi[7]);
+            }
         }
-        const uint32_t off_re = (uint32_t)(((nu >> 3) * 16 + bg) * 128 + (nu & 7) * 16);
-        const uint32_t off_im = off_re + 8 * 128;
-        *reinterpret_cast<uint4 *>(bhi + off_re) = make_uint4(hre[0], hre[1], hre[2], hre[3]);
-        *reinterpret_cast<uint4 *>(bhi + off_im) = make_uint4(him[0], him[1], him[2], him[3]);
-        *reinterpret_cast<uint4 *>(blo + off_re) = make_uint4(lre[0], lre[1], lre[2], lre[3]);
-        *reinterpret_cast<uint4 *>(blo + off_im) = make_uint4(lim[0], lim[1], lim[2], lim[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -544,21 +735,20 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
     const uint32_t tbase = TS.tmem_base;
     if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // M = 128, N = 128, F16 x F16 -> F32, both operands K-major
-        const uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-        const uint32_t a_hi = tbase + 128 + 128 * slot, a_lo = a_hi + 64;
-        const uint32_t sh = smem_addr(bhi), sl = smem_addr(blo);
+        // products (A term, B term), smallest first within each K step
+        constexpr int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+        constexpr int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
+        const uint32_t a0 = tbase + 128 + (uint32_t)(C::kTerms * C::kAColsPerTerm * slot);
+        const uint32_t sb = smem_addr(bbuf);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint64_t dh = tc_desc(sh + 256 * k), dl = tc_desc(sl + 256 * k);
-            const uint32_t acc = k > 0;
-            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tbase),
-                         "r"(a_hi + 8 * k), "l"(dh), "r"(idesc), "r"(acc));
-            asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(tbase),
-                         "r"(a_hi + 8 * k), "l"(dl), "r"(idesc));
-            asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, 1;" ::"r"(tbase),
-                         "r"(a_lo + 8 * k), "l"(dh), "r"(idesc));
+        for (int k = 0; k < C::kKSteps; ++k) {
+#pragma unroll
+            for (int q = 0; q < C::kProducts; ++q) {
+                const int ta = C::kProducts == 6 ? pa[q] : (C::kProducts == 3 ? pa3[q] : 0);
+                const int tb = C::kProducts == 6 ? pb[q] : (C::kProducts == 3 ? pb3[q] : 0);
+                const uint64_t bd = tc_desc(sb + tb * C::kBTermBytes + 256 * k, C::kSbo);
+                tc_mma<TCP>(tbase, a0 + ta * C::kAColsPerTerm + 8 * k, bd, (k > 0 || q > 0) ? 1u : 0u);
+            }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_addr(&TS.mbar)));
@@ -592,7 +782,8 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-                tf[2 * (rowoff ^ col[c0 + j]) + comp] = __uint_as_float(r[j]) * inv_sc;
+                tf[2 * (rowoff ^ col[c0 + j]) + comp] = C::P.scaled ? __uint_as_float(r[j]) * inv_sc
+                                                                    : __uint_as_float(r[j]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -600,12 +791,13 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
 }
 
 // One launch = one pass over the state.  blockDim.x = 2^(t - RB).
-// TC = true: tensor-core variant (complex64, t = 13), one CTA per SM; its
-// dynamic shared memory holds the tile and the two FP16 operand buffers.
+// TCP > 0: tensor-core variant of operand precision TCP (complex64, t = 13);
+// its dynamic shared memory holds the tile (and a separate B buffer when
+// the precision's B terms exceed the tile's 64 KB).
 // Runs tiles [t_begin, t_end) of one pass on `amps`: stages the pass's
 // phases and ops into shared memory, then loads, transforms and stores each
 // tile.  Shared by the single-state kernel and the batched kernel.
-template <typename R, int RB, bool TC, bool FULL>
+template <typename R, int RB, int TCP, bool FULL>
 __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__ amps,
                                                 const DevPass *__restrict__ pass_g,
                                                 const DevPhase *__restrict__ phases_g,
@@ -662,7 +854,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         S.th[ph][tid].qoff = q;
     }
     int ntc = 0;
-    if (TC) {
+    if (TCP) {
         for (int ph = 0; ph < nph; ++ph) {
             const DevPhase &D = phases_g[S.P.phase_begin + ph];
             if (D.kind != 1) continue;
@@ -686,7 +878,8 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             ++ntc;
         }
         if (tid == 0) TS.abort = 0;
-        if (ntc) tc_setup(TS, phases_g + S.P.phase_begin, nph, tc_words);
+        if constexpr (TCP > 0)
+            if (ntc) tc_setup<TCP>(TS, phases_g + S.P.phase_begin, nph, tc_words);
     }
     {
         const int o0 = phases_g[S.P.phase_begin].op_begin;
@@ -711,6 +904,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             }
             so.aux = (uint32_t)(o - o0);
             so.qmask = d.qmask;
+            if (!FULL) S.code8[o - o0] = (uint8_t)ct_code(d);
             S.phase[o - o0][0] = (R)d.m[0];
             S.phase[o - o0][1] = (R)d.m[1];
             S.ops[o - o0] = so;
@@ -743,7 +937,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                                S.P.L[kRunBits - 1] == kRunBits - 1;
     const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
     for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
-        if (TC && TS.abort) break;
+        if (TCP && TS.abort) break;
         // out-of-tile and thread bits are disjoint from it_off: OR = add
         const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
@@ -765,9 +959,11 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         }
 
         for (int ph = 0; ph < nph; ++ph) {
-            if constexpr (TC) {
+            if constexpr (TCP > 0) {
                 if (S.ph[ph].kind == 1) {
-                    tc_phase(TS, S.ph[ph].slot, S.ph[ph].scale_exp, tile, tc_parity, err_flag);
+                    unsigned char *bbuf = reinterpret_cast<unsigned char *>(tile);
+                    tc_phase<TCP>(TS, S.ph[ph].slot, S.ph[ph].scale_exp, reinterpret_cast<float2 *>(tile), bbuf,
+                                  tc_parity, err_flag);
                     tc_parity ^= 1u;
                     if (TS.abort) break;
                     continue;
@@ -788,9 +984,19 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             R fr = (R)1, fi = (R)0;             // thread-uniform pending factor
             const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end, ub = S.ph[ph].uniform_begin;
             const bool fpend = ub < oe;
-            for (int o = ob; o < ub; ++o) {
-                const SOp<R> op = S.ops[o];
-                exec_op<RB, FULL>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
+            if constexpr (FULL) {
+                for (int o = ob; o < ub; ++o) {
+                    const SOp<R> op = S.ops[o];
+                    exec_op<RB, FULL>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
+                }
+            } else {
+                // the next op's code is loaded while the current op runs
+                uint32_t cn = S.code8[ob];
+                for (int o = ob; o < ub; ++o) {
+                    const uint32_t cc = cn;
+                    cn = S.code8[o + 1];
+                    exec_ct<RB, V, R>(cc, a, idx_th, &S.ops[o]);
+                }
             }
             // tail: diagonal ops selected outside the register set multiply
             // the thread's pending factor (no interpreter dispatch)
@@ -857,12 +1063,21 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         }
         __syncthreads();
     }
-    if (TC && ntc) tc_teardown(TS);
+    if constexpr (TCP > 0)
+        if (ntc) tc_teardown<TCP>(TS);
     __syncthreads();
 }
 
-template <typename R, int RB, bool TC, bool FULL>
-__global__ void __launch_bounds__(kThreadsMax, 2)
+// CTAs per SM of a pass: two, or one for tensor-core precisions whose
+// block terms need 512 tensor-memory columns.
+__host__ __device__ constexpr int pass_ctas_per_sm(int tcp)
+{
+    return tcp == 0 ? 2
+                    : (128 + tc_prec(tcp).terms * (128 * tc_prec(tcp).elem_bytes / 4) <= 256 ? 2 : 1);
+}
+
+template <typename R, int RB, int TCP, bool FULL>
+__global__ void __launch_bounds__(kThreadsMax, pass_ctas_per_sm(TCP))
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
              uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
@@ -873,29 +1088,28 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     // the tensor-core form starts the tile (its MMA operand buffer) on a
     // 1024-byte boundary of the shared window; the launch adds the slack
     unsigned char *smem_raw = smem_dyn;
-    if (TC) smem_raw += (1024u - (smem_addr(smem_dyn) & 1023u)) & 1023u;
+    if (TCP) smem_raw += (1024u - (smem_addr(smem_dyn) & 1023u)) & 1023u;
     // contiguous range of tiles per CTA
     const uint64_t per = ntiles / gridDim.x, extra = ntiles % gridDim.x;
     const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
     const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
-    fused_pass_body<R, RB, TC, FULL>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
-                                     smem_raw);
+    fused_pass_body<R, RB, TCP, FULL>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
+                                      smem_raw);
 }
 
-// True when pass `hp` stages a shear, a general phase on register bits or a
-// T-valued phase on two register bits (the interpreter cases that only the
-// FULL kernel carries).  Mirrors the device staging: a phase op with m0 = m1
-// = 1/sqrt2 is staged as a T phase.
+// True when pass `hp` stages an op that the Clifford+T interpreter has no
+// byte code for (shears, general phases, T phases selected outside the
+// register set): such passes run the full interpreter.  Mirrors the device
+// staging (ct_code on the same ops).
 static bool pass_needs_full(const Plan &plan, const DevPass &hp)
 {
-    const int o0 = plan.phases[hp.phase_begin].op_begin;
-    const int o1 = plan.phases[hp.phase_begin + hp.nphases - 1].op_end;
-    for (int o = o0; o < o1; ++o) {
-        const DevOp &d = plan.ops[o];
-        if (d.type == OP_SHX || d.type == OP_SHY) return true;
-        if (d.type == OP_PHASE && d.rmask) {
-            const bool tphase = d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
-            if (!tphase || (d.rmask & (d.rmask - 1))) return true;
+    for (int ph = 0; ph < hp.nphases; ++ph) {
+        const DevPhase &D = plan.phases[hp.phase_begin + ph];
+        bool tail = false;     // thread-uniform diagonal ops must close the phase
+        for (int o = D.op_begin; o < D.op_end; ++o) {
+            const int c = ct_code(plan.ops[o]);
+            if (c < 0 || (tail && c != (int)C_COUNT)) return true;
+            tail = c == (int)C_COUNT;
         }
     }
     return false;
@@ -922,7 +1136,7 @@ k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict_
     __shared__ TcSmem TS;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
-        fused_pass_body<R, RB, false, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
+        fused_pass_body<R, RB, 0, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
                                       w.tile_end, nullptr, nullptr, S, TS, smem_raw);
     }
 }
@@ -952,10 +1166,18 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                     return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need 13-bit tiles");
                 if (!any_tc) QS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
                 any_tc = true;
-                auto kern = k_fused_pass<R, RB, true, true>;
-                const size_t smem = (size_t(1) << hp.t) * sizeof(V) + 1024;
+                decltype(&k_fused_pass<R, RB, 1, true>) kern;
+                switch (plan.precision) {
+                case QS_PREC_BF16X3: kern = k_fused_pass<R, RB, QS_PREC_BF16X3, true>; break;
+                case QS_PREC_BF16X6: kern = k_fused_pass<R, RB, QS_PREC_BF16X6, true>; break;
+                case QS_PREC_TF32X3: kern = k_fused_pass<R, RB, QS_PREC_TF32X3, true>; break;
+                case QS_PREC_TF32: kern = k_fused_pass<R, RB, QS_PREC_TF32, true>; break;
+                case QS_PREC_FP16X3: kern = k_fused_pass<R, RB, QS_PREC_FP16X3, true>; break;
+                default: return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d", plan.precision);
+                }
+                const size_t smem = tc_dyn_smem(plan.precision);
                 QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                const uint64_t cap = (uint64_t)s->num_sms * 2;
+                const uint64_t cap = (uint64_t)s->num_sms * pass_ctas_per_sm(plan.precision);
                 const int grid = (int)(ntiles < cap ? ntiles : cap);
                 kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, dwords,
                                                          err);
@@ -963,7 +1185,7 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                 return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need complex64");
             }
         } else {
-            auto kern = pass_needs_full(plan, hp) ? k_fused_pass<R, RB, false, true> : k_fused_pass<R, RB, false, false>;
+            auto kern = pass_needs_full(plan, hp) ? k_fused_pass<R, RB, 0, true> : k_fused_pass<R, RB, 0, false>;
             const size_t smem = (size_t(1) << hp.t) * sizeof(V);
             QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const uint64_t cap = (uint64_t)s->num_sms * 2;

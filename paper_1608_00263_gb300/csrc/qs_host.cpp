@@ -763,17 +763,62 @@ double f16_bits_to_f64(uint16_t h)
     return s ? -v : v;
 }
 
+// Rounds x to `frac` fraction bits, round to nearest even (no range limit:
+// the 8-bit exponent of BF16 and TF32 covers every value a block holds).
+static double round_frac_bits(double x, int frac)
+{
+    if (x == 0 || !std::isfinite(x)) return x;
+    int e;
+    std::frexp(x, &e);                        // |x| = f 2^e, f in [0.5, 1)
+    const double q = std::ldexp(1.0, e - 1 - frac);   // spacing at |x|
+    return std::nearbyint(x / q) * q;         // nearbyint: ties to even
+}
+
+uint16_t f64_to_bf16_bits(double x)
+{
+    const float f = (float)round_frac_bits(x, 7);   // exact in FP32
+    uint32_t w;
+    std::memcpy(&w, &f, 4);
+    return (uint16_t)(w >> 16);
+}
+
+double bf16_bits_to_f64(uint16_t h)
+{
+    const uint32_t w = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &w, 4);
+    return f;
+}
+
+uint32_t f64_to_tf32_bits(double x)
+{
+    const float f = (float)round_frac_bits(x, 10);  // exact in FP32, low 13 bits zero
+    uint32_t w;
+    std::memcpy(&w, &f, 4);
+    return w;
+}
+
+double tf32_bits_to_f64(uint32_t w)
+{
+    float f;
+    std::memcpy(&f, &w, 4);
+    return f;
+}
+
 namespace {
 
-// Realified block A = [[Re U, -Im U], [Im U, Re U]] split into FP16 hi + lo
-// and packed for tensor memory (see kTcWordsPerBlock).
-static void pack_block(const std::vector<Cplx> &U, std::vector<uint32_t> *words)
+// Realified block A = [[Re U, -Im U], [Im U, Re U]] split into the terms of
+// `precision` (term t = the operand type's rounding of what terms 0..t-1
+// leave) and packed for tensor memory (see tc_words_per_block).
+static void pack_block(const std::vector<Cplx> &U, int precision, std::vector<uint32_t> *words)
 {
+    const TcPrec tp = tc_prec(precision);
     const int D = 1 << kTcBits, MK = 2 * D;
+    const int wpt = MK * tp.elem_bytes / 4;          // words per term per row
     const size_t base = words->size();
-    words->resize(base + kTcWordsPerBlock);
+    words->resize(base + (size_t)tc_words_per_block(precision));
     for (int m = 0; m < MK; ++m) {
-        uint16_t hi[2 * 64], lo[2 * 64];
+        uint32_t *row = words->data() + base + (size_t)m * tp.terms * wpt;
         for (int k = 0; k < MK; ++k) {
             // output rows interleave re / im of block row m / 2; input
             // columns are the re block then the im block
@@ -781,12 +826,20 @@ static void pack_block(const std::vector<Cplx> &U, std::vector<uint32_t> *words)
             double a;
             if (!(m & 1)) a = k < D ? u.re : -u.im;
             else a = k < D ? u.im : u.re;
-            hi[k] = f64_to_f16_bits(a);
-            lo[k] = f64_to_f16_bits(a - f16_bits_to_f64(hi[k]));
-        }
-        for (int w = 0; w < MK / 2; ++w) {
-            (*words)[base + (size_t)m * MK + w] = hi[2 * w] | ((uint32_t)hi[2 * w + 1] << 16);
-            (*words)[base + (size_t)m * MK + MK / 2 + w] = lo[2 * w] | ((uint32_t)lo[2 * w + 1] << 16);
+            for (int t = 0; t < tp.terms; ++t) {
+                uint32_t *w = row + t * wpt;
+                double v;
+                if (tp.fmt == 2) {
+                    w[k] = f64_to_tf32_bits(a);
+                    v = tf32_bits_to_f64(w[k]);
+                } else {
+                    const uint16_t h = tp.fmt == 1 ? f64_to_bf16_bits(a) : f64_to_f16_bits(a);
+                    v = tp.fmt == 1 ? bf16_bits_to_f64(h) : f16_bits_to_f64(h);
+                    if (k & 1) w[k / 2] |= (uint32_t)h << 16;
+                    else w[k / 2] = h;
+                }
+                a -= v;
+            }
         }
     }
 }
@@ -805,6 +858,7 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t);
     pp.k = kTcBits;
     pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
+    pp.precision = (o && o->precision != QS_PREC_DEFAULT) ? o->precision : QS_PREC_FP16X3;
     pp.esz = dt == QS_C128 ? 16 : 8;
     // a deeper lookahead pays where a pass costs the most (host planning of
     // the next circuit overlaps the current evolution)
@@ -840,6 +894,7 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
     Plan &P = *out;
     P = Plan();
     P.n = n; P.t = pp.t; P.r = pp.r; P.c = pp.c; P.mode = pp.mode;
+    P.precision = pp.precision;
     P.gates = (int)ng;
 
     std::vector<char> done(ng, 0);
@@ -896,12 +951,12 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
                         if ((blk >> q) & 1) { bq[j] = q; ph.R[j++] = (uint8_t)tile_bit_of[q]; }
                     order_tc_block(bq, ph.R);
                     ph.kind = 1;
-                    ph.tc_block = (int)(P.tc_words.size() / kTcWordsPerBlock);
+                    ph.tc_block = (int)(P.tc_words.size() / tc_words_per_block(pp.precision));
                     ph.defer_before = deferred;
                     ph.op_begin = ph.op_end = (int)P.ops.size();
                     std::vector<Cplx> U;
                     block_unitary(g, tc_gates, bq, &U);
-                    pack_block(U, &P.tc_words);
+                    pack_block(U, pp.precision, &P.tc_words);
                     for (int gi : tc_gates) { pdone[gi] = 1; --prem; }
                     P.phases.push_back(ph);
                     ++dp.nphases;
@@ -1065,6 +1120,8 @@ extern "C" qs_status qs_plan_circuit(int n, qs_dtype dt, const qs_gate *gates,
     }
     if (mode != QS_MODE_FUSED && mode != QS_MODE_FUSED_TC)
         return set_error(QS_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (mode == QS_MODE_FUSED_TC && opts && (opts->precision < QS_PREC_DEFAULT || opts->precision > QS_PREC_TF32))
+        return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d is not a qs_precision", opts->precision);
     PlanParams pp = default_plan_params(n, dt, opts);
     Plan plan;
     st = build_plan(pp, gates, ngates, &plan);

@@ -19,6 +19,12 @@ struct CUevent_st;
 typedef CUevent_st *cudaEvent_t;
 #endif
 
+#ifdef __CUDACC__
+#define QS_TC_HD __host__ __device__
+#else
+#define QS_TC_HD
+#endif
+
 namespace qs {
 
 constexpr int kMaxQubits = 34;
@@ -99,12 +105,36 @@ struct DevPhase {       // 40 bytes
 // realified to A (128 x 128): row 2i is (Re U_i, -Im U_i) and row 2i+1 is
 // (Im U_i, Re U_i) over the K columns (re block, then im block), i.e. the
 // rows of [[Re U, -Im U], [Im U, Re U]] with real and imaginary output rows
-// interleaved; split into FP16 hi + lo, stored row-major as 32-bit words of
-// two consecutive K elements (lower K in the low half): 128 rows x (64 hi
-// words, 64 lo words).
+// interleaved; split into the terms of the operand precision and stored
+// row-major as 32-bit words: per row, the words of term 0, then term 1, ...
+// (16-bit formats: two consecutive K elements per word, lower K in the low
+// half; TF32: one element per word).
 constexpr int kTcBits = 6;
-constexpr int kTcWordsPerBlock = 128 * 128;
-constexpr int kMaxTcPerPass = 1;        // TMEM per CTA: accumulator + 1 block (hi, lo); 2 CTAs per SM
+constexpr int kMaxTcPerPass = 1;        // TMEM per CTA: accumulator + 1 block's terms
+
+// Operand format of a tensor-core precision (qs_precision): element type
+// (0 FP16, 1 BF16, 2 TF32, the instruction descriptor's encoding), number
+// of terms of each operand, and whether tiles are scaled into FP16's range.
+struct TcPrec {
+    int fmt;
+    int terms;
+    int elem_bytes;
+    bool scaled;
+};
+QS_TC_HD constexpr TcPrec tc_prec(int precision)
+{
+    return precision == QS_PREC_BF16X3   ? TcPrec{1, 2, 2, false}
+           : precision == QS_PREC_BF16X6 ? TcPrec{1, 3, 2, false}
+           : precision == QS_PREC_TF32X3 ? TcPrec{2, 2, 4, false}
+           : precision == QS_PREC_TF32   ? TcPrec{2, 1, 4, false}
+                                         : TcPrec{0, 2, 2, true};
+}
+// 32-bit words of one block matrix: 128 rows x terms x 128 K elements.
+QS_TC_HD constexpr int tc_words_per_block(int precision)
+{
+    return 128 * tc_prec(precision).terms * (128 * tc_prec(precision).elem_bytes / 4);
+}
+constexpr int kTcWordsPerBlock = 128 * 128;   // FP16x3 (the default precision)
 
 struct DevPass {
     int32_t t;              // tile bits
@@ -127,7 +157,8 @@ struct Plan {
     std::vector<DevPass> passes;
     std::vector<DevPhase> phases;
     std::vector<DevOp> ops;
-    std::vector<uint32_t> tc_words;  // TC mode: packed FP16 block matrices
+    std::vector<uint32_t> tc_words;  // TC mode: packed block matrices (see tc_prec)
+    int precision = QS_PREC_FP16X3;  // TC mode: operand precision of tc_words
     int gates = 0;
 };
 
@@ -140,6 +171,7 @@ struct PlanParams {
     int k;           // TC block bits
     int tc_ok;       // tensor-core phases allowed (complex64, 13-bit tiles)
     int esz = 8;     // bytes per amplitude (8 complex64, 16 complex128)
+    int precision = QS_PREC_FP16X3;   // TC operand precision (qs_precision, not DEFAULT)
     int look_steps = 2;   // tile choice: additions scored by greedy completion
     int look_top = 6;     // ... among this many best-scoring candidates
 };
@@ -163,6 +195,13 @@ QS_HD inline uint32_t tile_swizzle(uint32_t e, uint32_t CE)
 qs_status build_plan(const PlanParams &pp, const qs_gate *g, size_t ng, Plan *out);
 uint16_t f64_to_f16_bits(double x);
 double f16_bits_to_f64(uint16_t h);
+// bfloat16 (8 exponent bits, 7 fraction bits) and TF32 (8 exponent bits, 10
+// fraction bits, kept in a 32-bit word with the low 13 bits zero) from a
+// double, round to nearest even.
+uint16_t f64_to_bf16_bits(double x);
+double bf16_bits_to_f64(uint16_t h);
+uint32_t f64_to_tf32_bits(double x);
+double tf32_bits_to_f64(uint32_t w);
 PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o);
 double plan_bytes(const Plan &p, qs_dtype dt);
 

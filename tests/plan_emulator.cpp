@@ -17,6 +17,8 @@ using cd = std::complex<double>;
 using namespace qs;
 
 extern "C" uint16_t emul_f16(double x) { return f64_to_f16_bits(x); }
+extern "C" uint16_t emul_bf16(double x) { return f64_to_bf16_bits(x); }
+extern "C" uint32_t emul_tf32(double x) { return f64_to_tf32_bits(x); }
 extern "C" double emul_f16_back(uint16_t h) { return f16_bits_to_f64(h); }
 
 // Tensor-core phase: apply the stored block matrix (hi + lo, decoded) to
@@ -24,14 +26,24 @@ extern "C" double emul_f16_back(uint16_t h) { return f16_bits_to_f64(h); }
 // realified vectors [re; im]; output rows interleave re and im.
 static void apply_tc(const Plan &plan, const DevPass &P, const DevPhase &H, std::vector<cd> &tile)
 {
-    const uint32_t *w = plan.tc_words.data() + (size_t)H.tc_block * kTcWordsPerBlock;
-    double A[128][128];
+    const TcPrec tp = tc_prec(plan.precision);
+    const int wpt = 128 * tp.elem_bytes / 4;        // words per term per row
+    const uint32_t *w = plan.tc_words.data() + (size_t)H.tc_block * tc_words_per_block(plan.precision);
+    static double A[128][128];
     for (int m = 0; m < 128; ++m)
         for (int k = 0; k < 128; ++k) {
-            const uint32_t hw = w[m * 128 + k / 2], lw = w[m * 128 + 64 + k / 2];
-            const uint16_t hb = (k & 1) ? (uint16_t)(hw >> 16) : (uint16_t)(hw & 0xffff);
-            const uint16_t lb = (k & 1) ? (uint16_t)(lw >> 16) : (uint16_t)(lw & 0xffff);
-            A[m][k] = f16_bits_to_f64(hb) + f16_bits_to_f64(lb);
+            double a = 0;
+            for (int t = 0; t < tp.terms; ++t) {
+                const uint32_t *row = w + (size_t)m * tp.terms * wpt + t * wpt;
+                if (tp.fmt == 2) {
+                    a += tf32_bits_to_f64(row[k]);
+                } else {
+                    const uint32_t word = row[k / 2];
+                    const uint16_t b = (k & 1) ? (uint16_t)(word >> 16) : (uint16_t)(word & 0xffff);
+                    a += tp.fmt == 1 ? bf16_bits_to_f64(b) : f16_bits_to_f64(b);
+                }
+            }
+            A[m][k] = a;
         }
     uint64_t bmask = 0;
     for (int j = 0; j < kTcBits; ++j) bmask |= 1ULL << H.R[j];
@@ -134,6 +146,16 @@ static int emulate_built_plan(const Plan &plan, double *psi_interleaved, int *pa
         *tc_phases_out = k;
     }
     return 0;
+}
+
+extern "C" int emulate_plan_prec(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode, int precision,
+                                 double *psi_interleaved, int *passes_out, int *tc_phases_out)
+{
+    PlanParams pp{n, t, r, c, mode, kTcBits, mode == QS_MODE_FUSED_TC && t == 13 ? 1 : 0};
+    pp.precision = precision;
+    Plan plan;
+    if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
+    return emulate_built_plan(plan, psi_interleaved, passes_out, tc_phases_out);
 }
 
 extern "C" int emulate_plan_mode(int n, const qs_gate *g, size_t ng, int t, int r, int c, int mode,

@@ -13,9 +13,10 @@ compared with it:
   2e-5, moments 1..10 within 1e-5 relative (the k-th moment amplifies the
   relative probability error k-fold);
 * 10^6 samples: every sample satisfies the oracle's CDF inversion within
-  the bound that the complex64 state's probability error puts on the CDF;
-  the sample cross entropy within 1e-6 relative of the oracle's on the same
-  sample list.
+  the bound that the complex64 state's probability error puts on the CDF,
+  and the inversion of the GPU state's own FP64 CDF within the sampler's
+  FP32 in-chunk rounding (at least 99 % exactly); the sample cross entropy
+  within 1e-6 relative of the oracle's on the same sample list.
 
 At 30 qubits the planner runs its deeper tile lookahead (8 additions scored
 among 8 candidates), so this also pins that branch of the planner against
@@ -93,16 +94,23 @@ def fused_state(oracle_state):
     qs.qs_state_destroy(h)
 
 
-@pytest.mark.parametrize("mode", [qs.QS_MODE_FUSED_TC, qs.QS_MODE_PLAIN])
-def test_other_forms_vs_oracle(oracle_state, mode):
+@pytest.mark.parametrize("mode,prec,tol", [
+    (qs.QS_MODE_PLAIN, 0, 1e-5), (qs.QS_MODE_FUSED_TC, qs.QS_PREC_FP16X3, 1e-5),
+    (qs.QS_MODE_FUSED_TC, qs.QS_PREC_BF16X6, 1e-5), (qs.QS_MODE_FUSED_TC, qs.QS_PREC_TF32X3, 1e-5),
+    (qs.QS_MODE_FUSED_TC, qs.QS_PREC_BF16X3, None), (qs.QS_MODE_FUSED_TC, qs.QS_PREC_TF32, None)])
+def test_other_forms_vs_oracle(oracle_state, mode, prec, tol):
+    """Plain per-gate form and the tensor-core form in every operand
+    precision; the lossy ones (BF16x3, TF32) are reported and bounded only
+    loosely."""
     g, psi = oracle_state["gates"], oracle_state["psi"]
     h = qs.qs_state_create(N_QUBITS, qs.QS_C64)
     try:
-        qs.qs_apply_circuit(h, g, mode=mode)
+        qs.qs_apply_circuit(h, g, mode=mode, precision=prec)
         err = _rel_l2_vs_oracle(h, psi)
     finally:
         qs.qs_state_destroy(h)
-    assert err < 1e-5, (mode, err)
+    print("mode %d precision %d: relative L2 error %.3e" % (mode, prec, err))
+    assert err < (tol if tol else 5e-2), (mode, prec, err)
 
 
 def test_fused_state_statistics_and_samples_vs_oracle(oracle_state, fused_state):
@@ -160,10 +168,33 @@ def test_fused_state_statistics_and_samples_vs_oracle(oracle_state, fused_state)
     bound = l1 + 1e-9
     ok = (lo - bound <= target) & (target < hi + bound)
     assert ok.all(), np.nonzero(~ok)[0][:10]
+    del C, lo, hi
+    # against the CDF of the GPU state's own probabilities (FP64 sums of
+    # |psi_gpu|^2) the inversion is exact but for targets within the FP32
+    # in-chunk prefix rounding of a boundary; against the oracle's CDF the
+    # state's 1e-6-level error moves the CDF by far more than one p ~ 2^-30,
+    # so only the l1 bound above applies there
+    pg = np.empty(p.size)
+    for i in range(0, p.size, CHUNK):
+        a = t[2 * i:2 * (i + CHUNK)].double().view(-1, 2)
+        pg[i:i + CHUNK] = torch.sum(a * a, 1).cpu().numpy()
+    Cg = np.cumsum(pg)
+    del pg
+    target = u * Cg[-1]
+    lo = np.where(xi > 0, Cg[np.maximum(xi - 1, 0)], 0.0)
+    hi = Cg[xi]
     exact = (lo <= target) & (target < hi)
-    # the complex64 state moves only samples whose target lies near a boundary
-    assert np.mean(exact) > 0.95, np.mean(exact)
-    del C
+    assert np.mean(exact) > 0.99, np.mean(exact)
+    # the sampler's CDF carries the FP32 rounding of |psi|^2 and of the
+    # in-chunk prefixes (FP64 chunk offsets): almost every target lies within
+    # one average probability 2^-30 of the FP64 CDF's interval, and all lie
+    # within the worst case of 256 FP32 roundings per unit of mass
+    one_p = Cg[-1] * 2.0 ** -N_QUBITS
+    near = (lo - one_p <= target) & (target < hi + one_p)
+    assert np.mean(near) > 0.999, np.mean(near)
+    worst = 256 * 2.0 ** -24 * np.maximum(hi, one_p)
+    assert ((lo - worst <= target) & (target < hi + worst)).all()
+    del Cg, lo, hi
     ce_o, dh_o = O.cross_entropy(p, x)
     assert ce == pytest.approx(ce_o, rel=1e-6)
     assert dh == pytest.approx(dh_o, abs=3e-5)

@@ -502,6 +502,42 @@ def test_tc_form_random_gates():
     assert rel_l2(psi, ref) < 1e-5
 
 
+PRECISIONS = [(qs.QS_PREC_FP16X3, 1e-5), (qs.QS_PREC_BF16X6, 1e-5), (qs.QS_PREC_TF32X3, 1e-5),
+              (qs.QS_PREC_BF16X3, None), (qs.QS_PREC_TF32, None)]
+
+
+@pytest.mark.parametrize("prec,tol", PRECISIONS)
+@pytest.mark.parametrize("rows,cols,depth,seed", [(4, 5, 25, 1), (4, 6, 30, 5)])
+def test_tc_precisions_vs_oracle(prec, tol, rows, cols, depth, seed):
+    """Every operand precision of the tensor-core form against the FP64
+    oracle: FP16x3, BF16x6 and TF32x3 within the 1e-5 state bound; BF16x3
+    (~16 bits) and plain TF32 (~11 bits) are lossy, and their error is only
+    reported (and bounded loosely, so that a broken form still fails)."""
+    n = rows * cols
+    g = qs.qs_circuit_generate(rows, cols, depth, seed)
+    st = qs.qs_plan_circuit(n, qs.QS_C64, g, mode=qs.QS_MODE_FUSED_TC, precision=prec)
+    ref = O.simulate(n, g)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED_TC, precision=prec)
+        err = rel_l2(qs.qs_state_copy_out(h, n), ref)
+    finally:
+        qs.qs_state_destroy(h)
+    print("tc precision %d, %d qubits: relative L2 error %.3e (%d passes)" % (prec, n, err, st["passes"]))
+    assert err < (tol if tol else 5e-2), err
+
+
+def test_tc_precision_out_of_range_is_rejected():
+    g = qs.qs_circuit_generate(3, 5, 10, 0)
+    h = qs.qs_state_create(15, qs.QS_C64)
+    try:
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED_TC, precision=6)
+        assert e.value.status == _native.QS_ERR_INVALID_ARG
+    finally:
+        qs.qs_state_destroy(h)
+
+
 def test_tc_form_24_qubits():
     g = qs.qs_circuit_generate(4, 6, 30, 5)
     ref = O.simulate(24, g)

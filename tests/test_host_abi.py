@@ -2,6 +2,7 @@
 declare, validates arguments on the host, and its host-side parts (circuit
 generator, planner) agree with the oracle -- no GPU needed."""
 import ctypes
+import math
 import glob
 import os
 import re
@@ -136,6 +137,14 @@ def emulator():
     lib.emulate_plan_mode.restype = ctypes.c_int
     lib.emulate_plan_mode.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.emul_bf16.restype = ctypes.c_uint16
+    lib.emul_bf16.argtypes = [ctypes.c_double]
+    lib.emul_tf32.restype = ctypes.c_uint32
+    lib.emul_tf32.argtypes = [ctypes.c_double]
+    lib.emulate_plan_prec.restype = ctypes.c_int
+    lib.emulate_plan_prec.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.check_plan_order.restype = ctypes.c_int
     lib.check_plan_order.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -301,3 +310,62 @@ def test_plan_semantics_deep_lookahead(emulator, look, rows, cols, depth, t, see
                                       psi.ctypes.data, ctypes.byref(passes)) == 0
     ref = O.simulate(n, g)
     assert np.max(np.abs(psi - ref)) < 1e-12
+
+
+def _round_frac_exact(x, frac):
+    """Round-to-nearest-even of x to `frac` fraction bits, in exact rational
+    arithmetic (an independent restatement of the rounding rule)."""
+    from fractions import Fraction
+    if x == 0:
+        return 0.0
+    m, e = math.frexp(abs(x))               # |x| = m 2^e, m in [0.5, 1)
+    q = Fraction(2) ** (e - 1 - frac)       # spacing of representable values
+    v = Fraction(abs(x)) / q
+    f = math.floor(v)
+    r = v - f
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and f % 2 == 1):
+        f += 1
+    return math.copysign(float(f * q), x)
+
+
+def test_bf16_and_tf32_rounding(emulator):
+    """Host splitting of the tensor-core block matrices: BF16 and TF32
+    rounding (nearest, ties to even) against exact rational rounding, and
+    BF16 against torch's float32 -> bfloat16 conversion."""
+    import struct
+    import torch
+    rng = np.random.default_rng(5)
+    vals = np.concatenate([rng.normal(size=3000), rng.normal(size=500) * 1e-6,
+                           [1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -11, 1 + 3 * 2 ** -11, -0.75, 0.0]])
+    for v in vals:
+        b = emulator.emul_bf16(float(v))
+        bf = struct.unpack("<f", struct.pack("<I", b << 16))[0]
+        assert bf == _round_frac_exact(float(v), 7), v
+        t = emulator.emul_tf32(float(v))
+        assert t & 0x1FFF == 0
+        tf = struct.unpack("<f", struct.pack("<I", t))[0]
+        assert tf == _round_frac_exact(float(v), 10), v
+    f32 = vals.astype(np.float32)
+    ref = torch.from_numpy(f32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    got = np.array([emulator.emul_bf16(float(v)) for v in f32], dtype=np.uint16)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("prec,bound", [(qs.QS_PREC_FP16X3, 1e-6), (qs.QS_PREC_BF16X3, 2e-4),
+                                        (qs.QS_PREC_BF16X6, 1e-7), (qs.QS_PREC_TF32X3, 1e-6),
+                                        (qs.QS_PREC_TF32, 5e-3)])
+def test_tc_plan_semantics_every_precision(emulator, prec, bound):
+    """Tensor-core block phases in every operand precision: the stored block
+    terms (decoded and summed in FP64) reproduce the circuit within the
+    precision's split error."""
+    rows, cols, depth, seed = 4, 4, 40, 2
+    n = rows * cols
+    g = np.ascontiguousarray(qs.qs_circuit_generate(rows, cols, depth, seed), dtype=qs.GATE_DTYPE)
+    psi = O.zero_state(n)
+    passes, tcp = ctypes.c_int(0), ctypes.c_int(0)
+    assert emulator.emulate_plan_prec(n, g.ctypes.data, g.size, 13, 5, 5, qs.QS_MODE_FUSED_TC, prec,
+                                      psi.ctypes.data, ctypes.byref(passes), ctypes.byref(tcp)) == 0
+    ref = O.simulate(n, g)
+    err = np.linalg.norm(psi - ref) / np.linalg.norm(ref)
+    assert tcp.value > 0
+    assert err < bound, err

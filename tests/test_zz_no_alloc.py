@@ -41,6 +41,18 @@ def test_noalloc_rejects_a_bad_dtype_before_any_device_work():
     assert e.value.status == _native.QS_ERR_INVALID_ARG
 
 
+def _justified(p, x, seed, bound):
+    """Every sample x_j satisfies the inversion C_{x-1} <= u_j C_{N-1} < C_x
+    of the FP64 cumulative sum of p within `bound`."""
+    C = np.cumsum(p)
+    u = np.array([O.sample_uniform(seed, j) for j in range(x.size)])
+    target = u * C[-1]
+    xi = x.astype(np.int64)
+    lo = np.where(xi > 0, C[np.maximum(xi - 1, 0)], 0.0)
+    ok = (lo - bound <= target) & (target < C[xi] + bound)
+    assert ok.all(), np.nonzero(~ok)[0][:10]
+
+
 def _state(n, dtype, cseed):
     """A random-circuit state of n qubits (grids 1 x n up to 4 x 7)."""
     rows = 1 if n < 4 else (2 if n < 9 else 4)
@@ -80,9 +92,15 @@ def test_noalloc_matches_qs_sample_and_oracle_on_consecutive_calls(dtype):
                 assert np.array_equal(got, expect), (n, call)
                 # the oracle's sampler on the same probabilities: identical
                 # up to targets that land within rounding of a CDF boundary
-                # (complex64 in-chunk prefix sums are FP32)
-                xo = O.sample(psi.real ** 2 + psi.imag ** 2, m, seed + call)
-                limit = 1e-5 if dtype == qs.QS_C128 else 1e-3
-                assert np.mean(got != xo) <= limit, (n, call, np.mean(got != xo))
+                # (complex64: |psi|^2 and the in-chunk prefix sums are FP32,
+                # so within 256 2^-22 of a 256-amplitude chunk's mass)
+                p = psi.real ** 2 + psi.imag ** 2
+                xo = O.sample(p, m, seed + call)
+                if dtype == qs.QS_C128:
+                    assert np.mean(got != xo) <= 1e-5, (n, call, np.mean(got != xo))
+                else:
+                    chunk = p.reshape(-1, min(256, p.size)).sum(1).max()
+                    _justified(p, got, seed + call, 256 * 2.0 ** -22 * chunk)
+                    assert np.mean(got != xo) <= 0.05, (n, call, np.mean(got != xo))
         finally:
             qs.qs_state_destroy(h)
