@@ -523,28 +523,42 @@ def ensemble_instance(s):
 
 def ensemble_4096(qs, torch, hbm_peak):
     """Aggregate cycles/s and effective bandwidth of the batched ensemble
-    (graph replay of 4096 circuits, statistics included)."""
+    (graph replay of 4096 circuits, statistics included): with the default
+    13-qubit tiles, and with the tile size autotuned per instance size."""
     import numpy as np
     inst = [ensemble_instance(s) for s in range(4096)]
     gl = [qs.qs_circuit_generate(r, c, d, s, np.array(dd, dtype=np.uint8))
           for s, (n, d, r, c, dd) in enumerate(inst)]
-    b = qs.qs_batch_create([x[0] for x in inst])
-    try:
-        t0 = time.perf_counter()
-        qs.qs_batch_run(b, gl, kmax=10)            # plan, capture, first run
-        first = time.perf_counter() - t0
-        reps = 3
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            st = qs.qs_batch_run(b, gl, kmax=10)
-        dt = (time.perf_counter() - t0) / reps
-    finally:
-        qs.qs_batch_destroy(b)
     cycles = sum(x[1] for x in inst)
     bytes_state = sum(8 << x[0] for x in inst)
-    return {"instances": 4096, "state_gb": round(bytes_state / 1e9, 1), "first_run_s": round(first, 3),
-            "replay_s": round(dt, 4), "cycles_per_s": round(cycles / dt, 1),
-            "mean_norm": round(float(np.mean(st[:, 0])), 7)}
+    out = {"instances": 4096, "state_gb": round(bytes_state / 1e9, 1)}
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        for name, tune in (("default", 0), ("autotuned", 1)):
+            qs.qs_batch_set_options(b, autotune=tune)
+            t0 = time.perf_counter()
+            qs.qs_batch_run(b, gl, kmax=10)            # (tune,) plan, capture, first run
+            first = time.perf_counter() - t0
+            reps = 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                st = qs.qs_batch_run(b, gl, kmax=10)
+            dt = (time.perf_counter() - t0) / reps
+            tiles, run_bytes = qs.qs_batch_plan_info(b)
+            gbs = run_bytes / dt / 1e9
+            rec = {"first_run_s": round(first, 3), "replay_s": round(dt, 4),
+                   "cycles_per_s": round(cycles / dt, 1), "algorithmic_gb": round(run_bytes / 1e9, 2),
+                   "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                   "mean_norm": round(float(np.mean(st[:, 0])), 7)}
+            if tune:
+                rec["tile_per_n"] = {int(n): int(t) for n, t in sorted(set(zip([x[0] for x in inst], tiles)))}
+            out[name] = rec
+    finally:
+        qs.qs_batch_destroy(b)
+    best = max(("default", "autotuned"), key=lambda k: out[k]["cycles_per_s"])
+    out.update({"replay_s": out[best]["replay_s"], "cycles_per_s": out[best]["cycles_per_s"],
+                "gbs": out[best]["gbs"], "frac": out[best]["frac"], "best": best})
+    return out
 
 
 def noisy_trajectories(qs, torch, T=4096, r=0.005):

@@ -117,3 +117,43 @@ def test_ensemble_4096():
             assert st[i, 1] == pytest.approx(O.entropy(p), rel=1e-6)
     finally:
         qs.qs_batch_destroy(b)
+
+
+def test_autotuned_ensemble_matches_oracle_and_reports_its_choices():
+    """qs_batch_set_options(autotune=1): the tile size per instance size is
+    chosen by timing the batch's own rounds (9..13 qubits, at most n); the
+    run still matches the oracle instance by instance, every instance of one
+    size uses the same tile, and the run reports its algorithmic bytes."""
+    seeds = [s for s in range(300) if ensemble_instance(s)[0] <= 16][:20]
+    inst = [instance(s) for s in seeds]
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        with pytest.raises(qs.QSError):
+            qs.qs_batch_plan_info(b)                     # nothing prepared yet
+        with pytest.raises(qs.QSError):
+            qs.qs_batch_set_options(b, mode=qs.QS_MODE_FUSED_TC)
+        with pytest.raises(qs.QSError):
+            qs.qs_batch_set_options(b, tile_log2=14)
+        qs.qs_batch_set_options(b, autotune=1)
+        st = qs.qs_batch_run(b, [x[2] for x in inst], kmax=2)
+        tiles, run_bytes = qs.qs_batch_plan_info(b)
+        by_n = {}
+        for i, (n, depth, g) in enumerate(inst):
+            assert min(9, n) <= tiles[i] <= min(13, n), (n, tiles[i])
+            assert by_n.setdefault(n, tiles[i]) == tiles[i]
+            ref = O.simulate(n, g)
+            err = np.linalg.norm(device_state(b, i, n).astype(complex) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (i, n, err)
+            assert st[i, 1] == pytest.approx(O.entropy(O.probabilities(ref)), rel=1e-6)
+        assert run_bytes >= 16 * sum(1 << x[0] for x in inst)
+        # a fixed tile size for every instance
+        qs.qs_batch_set_options(b, tile_log2=10)
+        qs.qs_batch_run(b, [x[2] for x in inst], kmax=2)
+        tiles, _ = qs.qs_batch_plan_info(b)
+        assert np.all(tiles == 10)
+        for i, (n, depth, g) in enumerate(inst[:5]):
+            ref = O.simulate(n, g)
+            err = np.linalg.norm(device_state(b, i, n).astype(complex) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (i, n, err)
+    finally:
+        qs.qs_batch_destroy(b)

@@ -621,3 +621,26 @@ def test_cycle_statistics_vs_oracle(mode):
     # are diagonal, later the entropy approaches ln N - 1 + gamma
     assert st[0, 2] == pytest.approx(n * math.log(2), abs=1e-6)
     assert abs(st[-1, 2] - (n * math.log(2) - 1 + O.EULER_GAMMA)) < 0.01
+
+
+@pytest.mark.parametrize("dtype,mode", [(qs.QS_C64, qs.QS_MODE_FUSED), (qs.QS_C128, qs.QS_MODE_FUSED),
+                                        (qs.QS_C64, qs.QS_MODE_FUSED_TC)])
+def test_autotuned_apply_matches_oracle(dtype, mode):
+    """qs_opts.autotune = 1: the library times the candidate forms on a
+    scratch copy and applies the circuit with the fastest; the result is the
+    oracle's, the state's own contents before the call are respected (two
+    circuits in a row), and a second call reuses the cached choice."""
+    n = 16
+    g1 = qs.qs_circuit_generate(4, 4, 20, 3)
+    g2 = qs.qs_circuit_generate(4, 4, 12, 4)[16:]          # no leading H layer
+    h = qs.qs_state_create(n, dtype)
+    try:
+        qs.qs_apply_circuit(h, g1, mode=mode, autotune=1)
+        qs.qs_apply_circuit(h, g2, mode=mode, autotune=1)
+        ref = O.simulate(n, np.concatenate([g1, g2]))
+        assert rel_l2(qs.qs_state_copy_out(h, n, dtype), ref) < TOL[dtype]
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_apply_circuit(h, g2, mode=mode, autotune=1, tile_log2=10)
+        assert e.value.status == _native.QS_ERR_INVALID_ARG
+    finally:
+        qs.qs_state_destroy(h)
