@@ -493,6 +493,24 @@ qs_status qs_circuit_generate(int rows, int cols, const uint8_t *dead,
  * stream-ordered.  QS_ERR_INVALID_ARG for another kind. */
 qs_status qs_alu_rate(int kind, void *cuda_stream, double *fma_per_s);
 
+/* Build information (no counterpart in the paper).  qs_build_flags()
+ * returns QS_BUILD_CHECKED for the checked build (libqs_checked.so,
+ * compiled with QS_CHECKED): its kernels check their global-memory indices
+ * against the state's size before each guarded access; a failed check skips
+ * the access (no trap, no out-of-range access) and records a site code, and
+ * the public calls that launch work (qs_apply_circuit, qs_probabilities,
+ * qs_sample, qs_pt_moments, qs_cross_entropy, qs_batch_run) synchronise the
+ * device and return QS_ERR_INVALID_ARG naming the site.  The normal build
+ * compiles the checks away. */
+#define QS_BUILD_CHECKED 1
+int qs_build_flags(void);
+
+/* Checked build only: runs one guarded access one element past a small
+ * device buffer, which the check catches (site 901), and returns the
+ * resulting QS_ERR_INVALID_ARG -- a test of the check plumbing that touches
+ * no memory out of range.  QS_ERR_UNSUPPORTED in the normal build. */
+qs_status qs_check_probe(void);
+
 #ifdef __cplusplus
 }
 #endif

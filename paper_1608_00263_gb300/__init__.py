@@ -31,7 +31,8 @@ __all__ = [
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
     "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit", "qs_batch_apply",
-    "qs_alu_rate", "qs_batch_set_options", "qs_batch_plan_info", "library_path",
+    "qs_alu_rate", "qs_batch_set_options", "qs_batch_plan_info", "qs_build_flags", "qs_check_probe",
+    "library_path",
 ]
 
 
@@ -381,3 +382,15 @@ def qs_batch_plan_info(b):
     by = ctypes.c_double()
     N.check(N.lib().qs_batch_plan_info(b, t.ctypes.data, ctypes.byref(by)))
     return t, by.value
+
+
+def qs_build_flags():
+    """QS_BUILD_CHECKED (1) for the checked build, else 0."""
+    return int(N.lib().qs_build_flags())
+
+
+def qs_check_probe():
+    """Checked build: a guarded out-of-range access that the device check
+    catches; raises QSError (QS_ERR_INVALID_ARG).  Normal build: raises
+    QSError (QS_ERR_UNSUPPORTED)."""
+    N.check(N.lib().qs_check_probe())

@@ -11,7 +11,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libqs.so")
+# QS_CHECKED=1 selects the checked build (device-side index checks)
+CHECKED = os.environ.get("QS_CHECKED") == "1"
+LIB_PATH = os.path.join(_PKG, "libqs_checked.so" if CHECKED else "libqs.so")
 
 QS_OK, QS_ERR_INVALID_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
@@ -91,6 +93,8 @@ SIGNATURES = {
     "qs_circuit_generate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, ctypes.c_int, U64, P,
                                            ctypes.POINTER(ctypes.c_size_t)]),
     "qs_alu_rate": (ctypes.c_int, [ctypes.c_int, P, PD]),
+    "qs_build_flags": (ctypes.c_int, []),
+    "qs_check_probe": (ctypes.c_int, []),
     "qs_batch_set_options": (ctypes.c_int, [P, ctypes.POINTER(qs_opts)]),
     "qs_batch_plan_info": (ctypes.c_int, [P, P, PD]),
 }
@@ -103,7 +107,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise OSError("libqs.so is not built: run paper_1608_00263_gb300.build.build()")
+            raise OSError("%s is not built: run paper_1608_00263_gb300.build.build(%s)"
+                          % (os.path.basename(LIB_PATH), "checked=True" if CHECKED else ""))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)

@@ -3,6 +3,9 @@
 Each translation unit under ``csrc/`` is compiled in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3``), then linked
 into ``paper_1608_00263_gb300/libqs.so``.  Objects go to ``_build/``.
+``build(checked=True)`` makes the checked build ``libqs_checked.so``
+(``-DQS_CHECKED``: device-side index checks, objects in ``_build_checked/``),
+which the binding loads when the environment sets ``QS_CHECKED=1``.
 Host code carries no architecture-specific flags, so the same sources build
 on x86_64 and aarch64 hosts.
 """
@@ -18,6 +21,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqs.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "libqs_checked.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -40,9 +45,9 @@ def _headers():
     return hs
 
 
-def _flags():
+def _flags(checked=False):
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
-    return common + ["-gencode", GENCODE, "-lineinfo"]
+    return common + ["-gencode", GENCODE, "-lineinfo"] + (["-DQS_CHECKED"] if checked else [])
 
 
 def _digest(paths, extra):
@@ -54,8 +59,8 @@ def _digest(paths, extra):
     return h.hexdigest()
 
 
-def _compile(nvcc, src, flags, verbose):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(nvcc, src, flags, verbose, build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc] + flags + ["-c", src, "-o", obj]
     if verbose and src.endswith(".cu"):
         cmd += ["-Xptxas", "-v"]
@@ -65,33 +70,34 @@ def _compile(nvcc, src, flags, verbose):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False):
+def build(force=False, verbose=False, checked=False):
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
-    flags = _flags()
+    flags = _flags(checked)
     digest = _digest(srcs + _headers(), flags + [nvcc, sys.platform, os.uname().machine])
-    stamp = os.path.join(BUILD, "stamp")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = os.path.join(build_dir, "stamp")
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
-                return LIB
+                return lib
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(nvcc, s, flags, verbose), srcs))
+        results = list(ex.map(lambda s: _compile(nvcc, s, flags, verbose, build_dir), srcs))
     if verbose:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc, "-shared", "-gencode", GENCODE, "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(digest)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -361,7 +361,7 @@ static qs_status autotune_opts(qs_state *s, const qs_gate *gates, size_t ngates,
     return QS_OK;
 }
 
-extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates,
+static qs_status qs_apply_circuit_impl(qs_state *s, const qs_gate *gates, size_t ngates,
                                       const qs_opts *opts)
 {
     clear_error();
@@ -444,7 +444,7 @@ extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_
     return get_plan(s, gates, ngates, opts, &plan, &dev);
 }
 
-extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64)
+static qs_status qs_probabilities_impl(const qs_state *s, void *out, int out_is_fp64)
 {
     clear_error();
     if (qs_status st = check_state(s)) return st;
@@ -545,7 +545,7 @@ extern "C" qs_status qs_state_sync(const qs_state *s)
     return QS_OK;
 }
 
-extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
+static qs_status qs_sample_impl(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
 {
     clear_error();
     if (qs_status st = check_state(s)) return st;
@@ -565,7 +565,7 @@ extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uin
     return QS_OK;
 }
 
-extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples, uint64_t m,
+static qs_status qs_cross_entropy_impl(const qs_state *s, const uint64_t *samples, uint64_t m,
                                       double *ce, double *delta_h)
 {
     clear_error();
@@ -595,7 +595,7 @@ extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples
     return QS_OK;
 }
 
-extern "C" qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments, double *entropy,
+static qs_status qs_pt_moments_impl(const qs_state *s, int kmax, double *moments, double *entropy,
                                    double *uniform_ce, double *norm)
 {
     clear_error();
@@ -701,4 +701,86 @@ extern "C" qs_status qs_cycle_statistics(qs_state *s, const qs_gate *gates, size
         for (int k = 0; k < kmax; ++k) row[4 + k] = mom[k];
     }
     return QS_OK;
+}
+
+// ---- public entry points that launch device work: in the checked build
+// they end with a poll of the device check words ----
+extern "C" qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t ngates, const qs_opts *opts)
+{
+    const qs_status st = qs_apply_circuit_impl(s, gates, ngates, opts);
+    return st ? st : check_poll_all();
+}
+
+extern "C" qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64)
+{
+    const qs_status st = qs_probabilities_impl(s, out, out_is_fp64);
+    return st ? st : check_poll_all();
+}
+
+extern "C" qs_status qs_sample(const qs_state *s, uint64_t k, uint64_t seed, uint64_t *out)
+{
+    const qs_status st = qs_sample_impl(s, k, seed, out);
+    return st ? st : check_poll_all();
+}
+
+extern "C" qs_status qs_pt_moments(const qs_state *s, int kmax, double *moments, double *entropy, double *uniform_ce, double *norm)
+{
+    const qs_status st = qs_pt_moments_impl(s, kmax, moments, entropy, uniform_ce, norm);
+    return st ? st : check_poll_all();
+}
+
+extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples, uint64_t m, double *ce, double *delta_h)
+{
+    const qs_status st = qs_cross_entropy_impl(s, samples, m, ce, delta_h);
+    return st ? st : check_poll_all();
+}
+
+namespace qs {
+QS_CHECK_READER(check_poll_api)
+
+qs_status check_poll_all()
+{
+#ifdef QS_CHECKED
+    QS_CUDA_TRY(cudaDeviceSynchronize());
+    for (qs_status (*f)() : {check_poll_api, check_poll_plain, check_poll_fused, check_poll_stats,
+                             check_poll_batch})
+        if (qs_status st = f()) return st;
+#endif
+    return QS_OK;
+}
+}  // namespace qs
+
+#ifdef QS_CHECKED
+// A guarded access one element past a 4-element buffer: the check records
+// site 901 and skips the access.
+__global__ void k_check_probe(float *buf, uint64_t n, uint64_t i)
+{
+    if (QS_DCHECK(i < n, 901)) buf[i] = 1.f;
+}
+#endif
+
+extern "C" qs_status qs_check_probe(void)
+{
+    clear_error();
+#ifdef QS_CHECKED
+    float *buf = nullptr;
+    QS_CUDA_TRY(cudaMalloc((void **)&buf, 4 * sizeof(float)));
+    k_check_probe<<<1, 1>>>(buf, 4, 4);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(buf);
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "check probe: %s", cudaGetErrorString(e));
+    return check_poll_all();
+#else
+    return set_error(QS_ERR_UNSUPPORTED, "not a checked build (QS_CHECKED)");
+#endif
+}
+
+extern "C" int qs_build_flags(void)
+{
+#ifdef QS_CHECKED
+    return QS_BUILD_CHECKED;
+#else
+    return 0;
+#endif
 }

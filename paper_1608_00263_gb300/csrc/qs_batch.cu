@@ -549,8 +549,8 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     return QS_OK;
 }
 
-extern "C" qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
-                                  double *stats)
+static qs_status batch_run_impl(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
+                                double *stats)
 {
     clear_error();
     if (!b || !offsets || (kmax && !stats) || kmax < 0 || kmax > kMaxMoments)
@@ -579,6 +579,17 @@ extern "C" qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint6
             stats_from_sums(&b->host_sums[(size_t)i * kStatSums], b->n[i], kmax, &o[0], &o[1], &o[2], o + 3);
         }
     return QS_OK;
+}
+
+extern "C" qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
+                                  double *stats)
+{
+    const qs_status st = batch_run_impl(b, gates, offsets, kmax, stats);
+    return st ? st : check_poll_all();
+}
+
+namespace qs {
+QS_CHECK_READER(check_poll_batch)
 }
 
 extern "C" qs_status qs_batch_apply(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)

@@ -51,6 +51,42 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return false;
 }
 
+// ---------------------------------------------------------------------------
+// Checked build (QS_CHECKED): device-side index checks.  A failed check
+// records its site code in this translation unit's check word (the first
+// failure wins) and evaluates to false, so the guarded access is skipped --
+// no out-of-range access, no trap.  The host turns a nonzero word into
+// QS_ERR_INVALID_ARG (check_poll_all, after every public call that
+// launches work).  In the normal build every check is `true` and compiles
+// away.
+// ---------------------------------------------------------------------------
+#ifdef QS_CHECKED
+static __device__ unsigned int g_qs_check_word;
+__device__ __forceinline__ bool qs_dcheck_fail(unsigned int site)
+{
+    atomicCAS(&g_qs_check_word, 0u, site);
+    return false;
+}
+#define QS_DCHECK(cond, site) ((cond) ? true : qs_dcheck_fail(site))
+// Host reader of this translation unit's check word: returns
+// QS_ERR_INVALID_ARG naming the site and clears the word if it is set.
+#define QS_CHECK_READER(fn)                                                                 \
+    qs_status fn()                                                                          \
+    {                                                                                       \
+        unsigned int w = 0;                                                                 \
+        cudaError_t e = cudaMemcpyFromSymbol(&w, g_qs_check_word, sizeof w);               \
+        if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "check word: %s", cudaGetErrorString(e)); \
+        if (!w) return QS_OK;                                                               \
+        const unsigned int z = 0;                                                           \
+        cudaMemcpyToSymbol(g_qs_check_word, &z, sizeof z);                                  \
+        return set_error(QS_ERR_INVALID_ARG, "device index check failed at site %u", w);   \
+    }
+#else
+#define QS_DCHECK(cond, site) true
+#define QS_CHECK_READER(fn) \
+    qs_status fn() { return QS_OK; }
+#endif
+
 #define QS_CUDA_TRY(expr)                                                        \
     do {                                                                         \
         cudaError_t e_ = (expr);                                                 \

@@ -928,6 +928,9 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     // increment over the contiguous tile range
     uint64_t gmask = 0;
     for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
+    uint64_t lmask = 0;             // every tile bit's qubit (checked build)
+    for (int b = 0; b < t; ++b) lmask |= 1ULL << S.P.L[b];
+    (void)lmask;
     uint64_t base = deposit(t_begin, S.P.G, ng);
     uint32_t tc_parity = 0;
     // runs of consecutive amplitudes per tile = 2^(t - c); with c = RB for
@@ -938,6 +941,8 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
     for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
         if (TCP && TS.abort) break;
+        // the tile's highest element index must lie inside the state
+        if (!QS_DCHECK(((base | lmask) >> S.P.n) == 0, 201)) break;
         // out-of-tile and thread bits are disjoint from it_off: OR = add
         const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
@@ -1230,6 +1235,8 @@ void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, ui
     BatchItem w{amp_off, pass, tb, te, 0};
     std::memcpy(dst, &w, sizeof w);
 }
+
+QS_CHECK_READER(check_poll_fused)
 
 qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan)
 {

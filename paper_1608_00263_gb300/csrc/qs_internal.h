@@ -300,6 +300,17 @@ qs_status adjoint_run(qs_state *s, const qs_gate *g, size_t ng, const uint64_t *
 
 size_t dtype_bytes(qs_dtype dt);
 
+// Checked build: synchronises the device and reads every translation unit's
+// device check word (QS_ERR_INVALID_ARG if one is set); QS_OK at once in
+// the normal build.  Site codes: 1xx plain kernels, 2xx fused pass, 3xx
+// statistics and sampler, 4xx batch, 9xx the check probe.
+qs_status check_poll_all();
+qs_status check_poll_plain();
+qs_status check_poll_fused();
+qs_status check_poll_stats();
+qs_status check_poll_api();
+qs_status check_poll_batch();
+
 constexpr size_t kHostBoxBytes = 4096;
 // Copies `bytes` (a multiple of 8, at most kHostBoxBytes) of device memory
 // to `host` through the state's mapped host box: a one-block kernel on the

@@ -26,6 +26,7 @@ __global__ void k_dense1(typename V2T<R>::T *__restrict__ a, int q, uint64_t npa
     const uint64_t bit = 1ULL << q;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
         uint64_t i0 = insert_zero(p, q), i1 = i0 | bit;
+        if (!QS_DCHECK(i1 < 2 * npairs, 101)) continue;
         V x = a[i0], y = a[i1];
         V o0, o1;
         o0.x = u.m[0] * x.x - u.m[1] * x.y + u.m[2] * y.x - u.m[3] * y.y;
@@ -46,6 +47,7 @@ __global__ void k_dense1_c64v(float4 *__restrict__ a4, int q, uint64_t nquads, M
     for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nquads; w += stride) {
         // pairs p = 2w, 2w+1 -> i0 = insert_zero(2w, q) (even), i0 + 1
         uint64_t i0 = insert_zero(2 * w, q) >> 1;    // float4 index
+        if (!QS_DCHECK(i0 + half < 2 * nquads, 102)) continue;
         float4 x = a4[i0], y = a4[i0 + half];
         float4 o0, o1;
         o0.x = u.m[0] * x.x - u.m[1] * x.y + u.m[2] * y.x - u.m[3] * y.y;
@@ -92,6 +94,7 @@ __global__ void k_phase_sel(typename V2T<R>::T *__restrict__ a, int qa, int qb, 
         uint64_t i = insert_zero(j, qa);
         if (qb >= 0) i = insert_zero(i, qb);
         i |= set;
+        if (!QS_DCHECK(i < (count << (qb >= 0 ? 2 : 1)), 103)) continue;
         V v = a[i];
         if (negate_only) {
             v.x = -v.x; v.y = -v.y;
@@ -233,5 +236,7 @@ qs_status launch_plain_gate(qs_state *s, const qs_gate &g)
 {
     return s->dt == QS_C64 ? plain_gate_t<float>(s, g) : plain_gate_t<double>(s, g);
 }
+
+QS_CHECK_READER(check_poll_plain)
 
 }  // namespace qs

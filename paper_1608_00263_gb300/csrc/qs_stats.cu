@@ -590,7 +590,8 @@ __global__ void k_sample_search(const typename V2T<R>::T *__restrict__ a, uint64
                 res = c * kChunk + (uint64_t)L * 8 + (uint64_t)pick;
             }
             res = __shfl_sync(0xffffffffu, res, L);
-            if (lane == q) out[j0 + q] = res;
+            // the sample lies inside the state (checked build)
+            if (lane == q && QS_DCHECK(res < N && c < nchunks, 301)) out[j0 + q] = res;
         }
     }
 }
@@ -1135,6 +1136,8 @@ qs_status cross_entropy_run(const qs_state *s, const uint64_t *dev_samples, uint
     *ce = sum / (double)m;
     return QS_OK;
 }
+
+QS_CHECK_READER(check_poll_stats)
 
 }  // namespace qs
 
