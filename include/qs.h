@@ -499,7 +499,8 @@ qs_status qs_alu_rate(int kind, void *cuda_stream, double *fma_per_s);
  * against the state's size before each guarded access; a failed check skips
  * the access (no trap, no out-of-range access) and records a site code, and
  * the public calls that launch work (qs_apply_circuit, qs_probabilities,
- * qs_sample, qs_pt_moments, qs_cross_entropy, qs_batch_run) synchronise the
+ * qs_sample, qs_pt_moments, qs_cross_entropy, qs_batch_run,
+ * qs_adjoint_gradient) synchronise the
  * device and return QS_ERR_INVALID_ARG naming the site.  The normal build
  * compiles the checks away. */
 #define QS_BUILD_CHECKED 1

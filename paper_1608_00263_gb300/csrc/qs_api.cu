@@ -635,7 +635,7 @@ extern "C" qs_status qs_state_copy_in(qs_state *s, const void *host_amps)
     return QS_OK;
 }
 
-extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates,
+static qs_status qs_adjoint_gradient_impl(qs_state *s, const qs_gate *gates, size_t ngates,
                                          const uint64_t *samples, uint64_t m, const qs_opts *opts,
                                          double *loss, double *grad)
 {
@@ -735,6 +735,12 @@ extern "C" qs_status qs_cross_entropy(const qs_state *s, const uint64_t *samples
     return st ? st : check_poll_all();
 }
 
+extern "C" qs_status qs_adjoint_gradient(qs_state *s, const qs_gate *gates, size_t ngates, const uint64_t *samples, uint64_t m, const qs_opts *opts, double *loss, double *grad)
+{
+    const qs_status st = qs_adjoint_gradient_impl(s, gates, ngates, samples, m, opts, loss, grad);
+    return st ? st : check_poll_all();
+}
+
 namespace qs {
 QS_CHECK_READER(check_poll_api)
 
@@ -743,7 +749,7 @@ qs_status check_poll_all()
 #ifdef QS_CHECKED
     QS_CUDA_TRY(cudaDeviceSynchronize());
     for (qs_status (*f)() : {check_poll_api, check_poll_plain, check_poll_fused, check_poll_stats,
-                             check_poll_batch})
+                             check_poll_batch, check_poll_adjoint})
         if (qs_status st = f()) return st;
 #endif
     return QS_OK;

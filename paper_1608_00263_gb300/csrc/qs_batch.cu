@@ -139,6 +139,7 @@ static qs_status plan_instances(const qs_batch *b, const qs_gate *gates, const u
 struct RoundLaunch {
     int round, tbits;
     size_t first, count;
+    bool full;          // some item's pass needs the full interpreter
 };
 struct Rounds {
     std::vector<DevPass> passes;
@@ -174,11 +175,12 @@ static void build_rounds(const qs_batch *b, const std::vector<Plan> &plans, cons
     const size_t isz = batch_item_bytes();
     for (int r = 0; r < max_passes; ++r)
         for (int tb = 5; tb <= 13; ++tb) {
-            RoundLaunch L{r, tb, R->items.size() / isz, 0};
+            RoundLaunch L{r, tb, R->items.size() / isz, 0, false};
             for (int i : idx) {
                 if (r >= (int)plans[i].passes.size()) continue;
                 const DevPass &p = plans[i].passes[r];
                 if (p.t != tb) continue;
+                L.full = L.full || plan_pass_needs_full(plans[i], r);
                 const uint64_t ntiles = 1ULL << (b->n[i] - p.t);
                 for (uint64_t t0 = 0; t0 < ntiles; t0 += kItemTiles) {
                     const uint64_t t1 = std::min<uint64_t>(ntiles, t0 + kItemTiles);
@@ -224,7 +226,7 @@ static qs_status launch_rounds(const qs_batch *b, cudaStream_t st, const Rounds 
     for (const RoundLaunch &L : R.launches)
         if (qs_status rs = launch_batch_round(st, b->num_sms, b->amps, D + o.item + L.first * isz, (int)L.count,
                                               L.tbits, (const DevPass *)(D + o.pass),
-                                              (const DevPhase *)(D + o.phase), (const DevOp *)(D + o.op)))
+                                              (const DevPhase *)(D + o.phase), (const DevOp *)(D + o.op), L.full))
             return rs;
     return QS_OK;
 }

@@ -1130,7 +1130,7 @@ struct BatchItem {
     uint32_t pad;
 };
 
-template <typename R, int RB>
+template <typename R, int RB, bool FULL>
 __global__ void __launch_bounds__(kThreadsMax, 2)
 k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict__ items, int nitems,
              const DevPass *__restrict__ passes, const DevPhase *__restrict__ phases_g,
@@ -1141,7 +1141,7 @@ k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict_
     __shared__ TcSmem TS;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem w = items[it];
-        fused_pass_body<R, RB, 0, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
+        fused_pass_body<R, RB, 0, FULL>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
                                       w.tile_end, nullptr, nullptr, S, TS, smem_raw);
     }
 }
@@ -1208,11 +1208,17 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
     return QS_OK;
 }
 
+bool plan_pass_needs_full(const Plan &plan, int pass)
+{
+    return pass_needs_full(plan, plan.passes[pass]);
+}
+
 qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const void *items, int nitems,
-                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops)
+                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops,
+                             bool full)
 {
     if (tile_bits < 5 || tile_bits > 13) return set_error(QS_ERR_INVALID_ARG, "batch tile bits %d", tile_bits);
-    auto kern = k_batch_pass<float, 5>;
+    auto kern = full ? k_batch_pass<float, 5, true> : k_batch_pass<float, 5, false>;
     const size_t smem = (size_t(1) << tile_bits) * sizeof(float2);
     const int cap = num_sms * 2;
     const int grid = nitems < cap ? nitems : cap;
@@ -1224,7 +1230,8 @@ qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const voi
 
 qs_status batch_kernel_setup()
 {
-    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     return QS_OK;
 }
 

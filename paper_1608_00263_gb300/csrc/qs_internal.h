@@ -310,6 +310,7 @@ qs_status check_poll_fused();
 qs_status check_poll_stats();
 qs_status check_poll_api();
 qs_status check_poll_batch();
+qs_status check_poll_adjoint();
 
 constexpr size_t kHostBoxBytes = 4096;
 // Copies `bytes` (a multiple of 8, at most kHostBoxBytes) of device memory
@@ -333,8 +334,13 @@ qs_status stage_view(const qs_state *s, size_t bytes, void **host, void **dev);
 
 // batched ensemble helpers
 constexpr int kStatSums = 12;
+// One lockstep round of the batched pass; `full` selects the interpreter
+// with the parameterised-gate cases (else the Clifford+T one, valid when
+// plan_pass_needs_full is false for every pass of the round's items).
 qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const void *items, int nitems,
-                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops);
+                             int tile_bits, const DevPass *passes, const DevPhase *phases, const DevOp *ops,
+                             bool full);
+bool plan_pass_needs_full(const Plan &plan, int pass);
 size_t batch_item_bytes();
 qs_status batch_kernel_setup();
 void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, uint32_t te);
