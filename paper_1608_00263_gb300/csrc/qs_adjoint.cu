@@ -73,7 +73,7 @@ struct AdjGate {        // one gate of a group, in reverse (un-apply) order
     int32_t b0, b1;
     int32_t deriv;      // D_* kind
     int32_t slot;       // parameter index (deriv != D_NONE)
-    int32_t pad;
+    int32_t diag;       // single-qubit gate with G^dagger diagonal (m[2..5] zero)
     double m[8];        // G^dagger (u00 u01 u10 u11 as re, im), or conj(d) in m[0], m[1]
 };
 
@@ -107,9 +107,20 @@ __device__ __forceinline__ void adj_pair(typename V2T<R>::T *ps, typename V2T<R>
         else
             acc += (l0r * a0i - l0i * a0r) - (l1r * a1i - l1i * a1r);
     }
-    const R m0 = (R)g.m[0], m1 = (R)g.m[1], m2 = (R)g.m[2], m3 = (R)g.m[3];
-    const R m4 = (R)g.m[4], m5 = (R)g.m[5], m6 = (R)g.m[6], m7 = (R)g.m[7];
+    const R m0 = (R)g.m[0], m1 = (R)g.m[1], m6 = (R)g.m[6], m7 = (R)g.m[7];
     V y0, y1, k0, k1;
+    // diagonal G^dagger (T, RZ): one complex product per amplitude -- taken
+    // for complex128, whose sweep is FP64-bound; the complex64 sweep is
+    // bound elsewhere and measured faster without the extra branch
+    if (sizeof(R) == 8 && g.diag) {
+        y0.x = m0 * x0.x - m1 * x0.y; y0.y = m0 * x0.y + m1 * x0.x;
+        y1.x = m6 * x1.x - m7 * x1.y; y1.y = m6 * x1.y + m7 * x1.x;
+        k0.x = m0 * l0.x - m1 * l0.y; k0.y = m0 * l0.y + m1 * l0.x;
+        k1.x = m6 * l1.x - m7 * l1.y; k1.y = m6 * l1.y + m7 * l1.x;
+        ps[i0] = y0; ps[i1] = y1; lm[i0] = k0; lm[i1] = k1;
+        return;
+    }
+    const R m2 = (R)g.m[2], m3 = (R)g.m[3], m4 = (R)g.m[4], m5 = (R)g.m[5];
     y0.x = m0 * x0.x - m1 * x0.y + m2 * x1.x - m3 * x1.y;
     y0.y = m0 * x0.y + m1 * x0.x + m2 * x1.y + m3 * x1.x;
     y1.x = m4 * x0.x - m5 * x0.y + m6 * x1.x - m7 * x1.y;
@@ -122,7 +133,7 @@ __device__ __forceinline__ void adj_pair(typename V2T<R>::T *ps, typename V2T<R>
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kAdjThreads)
+__global__ void __launch_bounds__(kAdjThreads, 3)
 k_adj_group(typename V2T<R>::T *__restrict__ psi, typename V2T<R>::T *__restrict__ lam,
             const AdjGroup *__restrict__ grp_g, const AdjGate *__restrict__ gates_g, uint64_t ntiles,
             double *__restrict__ part, int nparts)
@@ -312,6 +323,7 @@ static void adjoint_groups(int n, const qs_gate *g, size_t ng, int t, int low, s
                     d.m[2 * e + 1] = -u[perm[e]].im;
                 }
                 d.deriv = x.kind == QS_RX ? D_X : x.kind == QS_RY ? D_Y : x.kind == QS_RZ ? D_Z : D_NONE;
+                d.diag = d.m[2] == 0 && d.m[3] == 0 && d.m[4] == 0 && d.m[5] == 0;
             }
             if (param) {
                 --pidx;
@@ -345,7 +357,7 @@ static qs_status adjoint_t(qs_state *s, const qs_gate *g, size_t ng, const uint6
     adjoint_groups<R>(n, g, ng, t, low, &groups, &gates, &pslot, &scale);
     const size_t nparam = pslot.size();
     V *psi = (V *)s->amps, *lam = nullptr;
-    const int ctas = 2 * s->num_sms;
+    const int ctas = 3 * s->num_sms;          // three CTAs per SM (64 KB of tiles each)
     const size_t smem = 2 * ((size_t)1 << t) * sizeof(V);
     QS_CUDA_TRY(cudaFuncSetAttribute(k_adj_group<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // device tables: groups | gates | scale (in sweep-slot order) | partials | sums
