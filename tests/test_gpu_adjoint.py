@@ -107,3 +107,22 @@ def test_torch_autograd_binding():
     ref = np.array([oracle_shift_grad(n, noisy, x, int(k)) for k in idx])
     assert float(loss.detach()) == pytest.approx(oracle_loss(n, noisy, x), rel=1e-10)
     assert np.max(np.abs(theta.grad.numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+def test_torch_autograd_binding_keeps_theta_device():
+    """theta on the GPU: loss and gradient come back on the GPU."""
+    import torch
+    from paper_1608_00263_gb300.autograd import circuit_cross_entropy
+    n = 8
+    nominal, noisy, idx = parameterised_circuit(2, 4, 10, 3, 5)
+    x = O.sample(O.probabilities(O.simulate(n, nominal)), 2000, 8)
+    theta = torch.tensor(noisy["theta"][idx], dtype=torch.float32, device="cuda", requires_grad=True)
+    h = qs.qs_state_create(n, qs.QS_C128)
+    try:
+        loss = circuit_cross_entropy(theta, h, noisy, idx, x)
+        loss.backward()
+    finally:
+        qs.qs_state_destroy(h)
+    assert loss.device.type == "cuda" and theta.grad.device.type == "cuda"
+    ref = np.array([oracle_shift_grad(n, noisy, x, int(k)) for k in idx])
+    assert np.max(np.abs(theta.grad.cpu().numpy() - ref)) < 1e-5 * np.max(np.abs(ref))
