@@ -875,6 +875,74 @@ double plan_bytes(const Plan &p, qs_dtype dt)
     return (double)p.passes.size() * 2.0 * std::ldexp(1.0, p.n) * (double)dtype_bytes(dt);
 }
 
+// The last register phase of a pass always multiplies every slot by a
+// thread-uniform factor (the pass-wide scale), so diagonal ops that reach it
+// as thread-uniform ops cost no dispatch.  A diagonal op of an earlier
+// phase moves to that phase's tail when none of its qubits is a register
+// bit of the last phase and no non-diagonal op on one of its qubits follows
+// it in the pass (diagonal ops commute with each other and with
+// non-diagonal ops on other qubits, so the pass's product is unchanged).
+static void hoist_diagonals_to_last_phase(Plan *P, const DevPass &dp)
+{
+    const int p0 = dp.phase_begin, np = dp.nphases;
+    if (np < 2) return;
+    for (int ph = 0; ph < np; ++ph)
+        if (P->phases[p0 + ph].kind != 0) return;     // tensor-core passes keep their layout
+    auto qubits = [&](int ph, const DevOp &d) {
+        uint64_t q = d.qmask;
+        for (int j = 0; j < dp.r; ++j)
+            if ((d.rmask >> j) & 1) q |= 1ULL << dp.L[P->phases[p0 + ph].R[j]];
+        return q;
+    };
+    auto nondiag_qubit = [&](int ph, const DevOp &d) -> uint64_t {
+        if (d.type == OP_PHASE || d.type == OP_NEG) return 0;
+        return 1ULL << dp.L[P->phases[p0 + ph].R[d.a]];
+    };
+    uint64_t last_reg = 0;
+    for (int j = 0; j < dp.r; ++j) last_reg |= 1ULL << dp.L[P->phases[p0 + np - 1].R[j]];
+    // qubits touched by non-diagonal ops from each position to the end of
+    // the pass, scanned backwards
+    std::vector<std::vector<DevOp>> keep(np);
+    std::vector<DevOp> moved;
+    uint64_t later_nd = 0;
+    for (int o = P->phases[p0 + np - 1].op_begin; o < P->phases[p0 + np - 1].op_end; ++o)
+        later_nd |= nondiag_qubit(np - 1, P->ops[o]);
+    for (int ph = np - 2; ph >= 0; --ph) {
+        const DevPhase &H = P->phases[p0 + ph];
+        std::vector<DevOp> kept_rev;
+        for (int o = H.op_end - 1; o >= H.op_begin; --o) {
+            const DevOp &d = P->ops[o];
+            const bool diag = d.type == OP_PHASE || d.type == OP_NEG;
+            if (diag && d.rmask) {
+                const uint64_t q = qubits(ph, d);
+                if (!(q & last_reg) && !(q & later_nd)) {
+                    DevOp m = d;
+                    m.rmask = 0;
+                    m.qmask = q;
+                    moved.push_back(m);
+                    continue;
+                }
+            }
+            later_nd |= nondiag_qubit(ph, d);
+            kept_rev.push_back(d);
+        }
+        keep[ph].assign(kept_rev.rbegin(), kept_rev.rend());
+    }
+    if (moved.empty()) return;
+    for (int o = P->phases[p0 + np - 1].op_begin; o < P->phases[p0 + np - 1].op_end; ++o)
+        keep[np - 1].push_back(P->ops[o]);
+    // the moved ops join the last phase's thread-uniform tail (diagonal ops
+    // commute, so their order there is free)
+    for (const DevOp &m : moved) keep[np - 1].push_back(m);
+    int o = P->phases[p0].op_begin;
+    for (int ph = 0; ph < np; ++ph) {
+        DevPhase &H = P->phases[p0 + ph];
+        H.op_begin = o;
+        for (const DevOp &d : keep[ph]) P->ops[o++] = d;
+        H.op_end = o;
+    }
+}
+
 qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *out)
 {
     const int n = pp.n;
@@ -1078,6 +1146,7 @@ qs_status build_plan(const PlanParams &pp, const qs_gate *gin, size_t ng, Plan *
             P.phases.push_back(ph);
             ++dp.nphases;
         }
+        if (pp.hoist_diagonals) hoist_diagonals_to_last_phase(&P, dp);
         int placed = 0;
         for (int i : pass_gates)
             if (pdone[i]) { done[i] = 1; --remaining; ++placed; }

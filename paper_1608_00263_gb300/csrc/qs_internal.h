@@ -174,6 +174,7 @@ struct PlanParams {
     int precision = QS_PREC_FP16X3;   // TC operand precision (qs_precision, not DEFAULT)
     int look_steps = 2;   // tile choice: additions scored by greedy completion
     int look_top = 6;     // ... among this many best-scoring candidates
+    int hoist_diagonals = 1;   // move late diagonal ops to the last phase's uniform tail
 };
 
 // XOR swizzle of the shared-memory tile (element e -> element index): the
