@@ -52,6 +52,13 @@ def parse():
                     help="skip the one-off plain-mode comparison run")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="time only the 24-qubit adjoint gradient (a profiling case)")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="time only the 4096-circuit ensemble (a profiling case)")
+    ap.add_argument("--ensemble-runs", default="default,autotuned,lockstep_default",
+                    help="ensemble runs to time: default, autotuned (persistent engine), "
+                         "lockstep_default (lockstep engine)")
+    ap.add_argument("--ensemble-count", type=int, default=4096,
+                    help="instances of the ensemble recipe (the first K; a smaller profiling case)")
     return ap.parse_args()
 
 
@@ -400,7 +407,7 @@ def run_ours(args, rank, world, local):
             qs.qs_state_destroy(h)
         h = None
         torch.cuda.empty_cache()
-        ens = ensemble_4096(qs, torch, hbm_peak)
+        ens = ensemble_4096(qs, torch, hbm_peak, args.ensemble_runs.split(","))
         noisy = noisy_trajectories(qs, torch)
         single = single_error_sweep(qs, torch)
         small = grid20_forms(qs, torch)
@@ -523,20 +530,27 @@ def ensemble_instance(s):
     return n, depth, rows, cols, dead
 
 
-def ensemble_4096(qs, torch, hbm_peak):
+def ensemble_4096(qs, torch, hbm_peak, runs=("default", "autotuned", "lockstep_default"), count=4096):
     """Aggregate cycles/s and effective bandwidth of the batched ensemble
-    (graph replay of 4096 circuits, statistics included): with the default
-    13-qubit tiles, and with the tile size autotuned per instance size."""
+    (graph replay of 4096 circuits, statistics included).  Persistent
+    engine (one launch per run): with the default 13-qubit tiles and with
+    the tile size autotuned per instance size; lockstep engine (one launch
+    per round and tile size) with the default tiles, for comparison.
+    `count` < 4096 takes the recipe's first instances (a profiling case)."""
     import numpy as np
-    inst = [ensemble_instance(s) for s in range(4096)]
+    inst = [ensemble_instance(s) for s in range(count)]
     gl = [qs.qs_circuit_generate(r, c, d, s, np.array(dd, dtype=np.uint8))
           for s, (n, d, r, c, dd) in enumerate(inst)]
     cycles = sum(x[1] for x in inst)
     bytes_state = sum(8 << x[0] for x in inst)
-    out = {"instances": 4096, "state_gb": round(bytes_state / 1e9, 1)}
+    out = {"instances": count, "state_gb": round(bytes_state / 1e9, 1)}
+    known = {"default": (qs.QS_BATCH_PERSISTENT, 0), "autotuned": (qs.QS_BATCH_PERSISTENT, 1),
+             "lockstep_default": (qs.QS_BATCH_ROUNDS, 0)}
     b = qs.qs_batch_create([x[0] for x in inst])
     try:
-        for name, tune in (("default", 0), ("autotuned", 1)):
+        for name in runs:
+            engine, tune = known[name]
+            qs.qs_batch_set_engine(b, engine)
             qs.qs_batch_set_options(b, autotune=tune)
             t0 = time.perf_counter()
             qs.qs_batch_run(b, gl, kmax=10)            # (tune,) plan, capture, first run
@@ -548,7 +562,8 @@ def ensemble_4096(qs, torch, hbm_peak):
             dt = (time.perf_counter() - t0) / reps
             tiles, run_bytes = qs.qs_batch_plan_info(b)
             gbs = run_bytes / dt / 1e9
-            rec = {"first_run_s": round(first, 3), "replay_s": round(dt, 4),
+            rec = {"engine": "persistent" if engine == qs.QS_BATCH_PERSISTENT else "lockstep",
+                   "first_run_s": round(first, 3), "replay_s": round(dt, 4),
                    "cycles_per_s": round(cycles / dt, 1), "algorithmic_gb": round(run_bytes / 1e9, 2),
                    "gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
                    "mean_norm": round(float(np.mean(st[:, 0])), 7)}
@@ -557,7 +572,8 @@ def ensemble_4096(qs, torch, hbm_peak):
             out[name] = rec
     finally:
         qs.qs_batch_destroy(b)
-    best = max(("default", "autotuned"), key=lambda k: out[k]["cycles_per_s"])
+    cand = [k for k in ("default", "autotuned", "lockstep_default") if k in out]
+    best = max(cand, key=lambda k: out[k]["cycles_per_s"])
     out.update({"replay_s": out[best]["replay_s"], "cycles_per_s": out[best]["cycles_per_s"],
                 "gbs": out[best]["gbs"], "frac": out[best]["frac"], "best": best})
     return out
@@ -841,6 +857,16 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.ensemble_only:
+        import torch
+
+        import paper_1608_00263_gb300 as qs
+        from paper_1608_00263_gb300 import build as qs_build
+        qs_build.build()
+        peaks, _ = load_peaks()
+        print(json.dumps({"ensemble": ensemble_4096(qs, torch, float(peaks["hbm_gbs"]),
+                                                    args.ensemble_runs.split(","), args.ensemble_count)}),
+              flush=True)
     elif args.adjoint_only:
         import torch
 

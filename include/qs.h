@@ -362,11 +362,15 @@ qs_status qs_batch_create(int count, const int *nqubits, void *cuda_stream, qs_b
  * entries, offsets[0] = 0), and writes per-instance statistics of the
  * normalised output distribution (as qs_pt_moments) to stats[i*(3+kmax) ..]:
  * norm, entropy, uniform cross entropy, moments 1..kmax (kmax <= 10; stats
- * may be NULL when kmax = 0).  Instances run in lockstep rounds of the fused
- * tile pass, one launch per round and tile size over all instances; the
- * device work is captured once into a CUDA graph and replayed while the gate
- * lists are unchanged (a new gate list replans and recaptures).
- * Synchronous. */
+ * may be NULL when kmax = 0).  The engine (qs_batch_set_engine) decides how
+ * the device work is issued: by default one persistent launch runs the reset,
+ * every instance's fused tile passes and the statistics from a device work
+ * queue (each work item waits, bounded, only for its own instance's earlier
+ * items; QS_ERR_TIMEOUT if such a wait runs out, which a correct run never
+ * meets); the lockstep engine runs round r (pass r of every instance) as
+ * one launch per tile size.  The device work is captured once into a CUDA
+ * graph and replayed while the gate lists are unchanged (a new gate list
+ * replans and recaptures).  Synchronous. */
 qs_status qs_batch_run(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
                        double *stats);
 
@@ -437,14 +441,41 @@ qs_status qs_batch_state(const qs_batch *b, int i, void **device_amps);
  * QS_ERR_UNSUPPORTED for QS_MODE_FUSED_TC); opts->tile_log2 in 5..13 fixes
  * the tile size of every instance (0 = the planner's default, 13 qubits or
  * n if smaller); opts->autotune = 1 lets the library choose the tile size
- * per instance size n instead: on the next run it times the lockstep rounds
- * of the batch's own instances of each size n with every candidate tile
- * size (9..13 qubits, at most n) on their own state memory (CUDA events;
- * one untimed and one timed run per candidate), keeps the fastest, and
- * caches the choice per (device, n) for the rest of the process, so later
- * batches with instances of a size already seen skip the timing.  NULL
+ * per instance size n instead: on the next run it times the evolution of
+ * the batch's own instances of each size n on the batch's engine with every
+ * candidate tile size (9..13 qubits, at most n) on their own state memory
+ * (CUDA events; one untimed and one timed run per candidate), keeps the
+ * fastest, and caches the choice per (device, n, engine) for the rest of
+ * the process, so later batches with instances of a size already seen skip
+ * the timing.  NULL
  * restores the defaults.  The next run replans.  Host only. */
 qs_status qs_batch_set_options(qs_batch *b, const qs_opts *opts);
+
+/* Engines of the batched ensemble (qs_batch_set_engine). */
+enum {
+    QS_BATCH_PERSISTENT = 0,   /* one launch per run: a persistent kernel
+                                  (two CTAs of 256 threads per SM) takes
+                                  work items from a device queue: every
+                                  instance's initial-state chunks (2^16
+                                  amplitudes), then its fused passes in
+                                  items of 2^16 amplitudes, round-major
+                                  (pass r of every instance before pass
+                                  r + 1 of any; larger instances first),
+                                  then its statistics chunks; an item waits
+                                  for its own instance's earlier items
+                                  only, so instances overlap freely */
+    QS_BATCH_ROUNDS = 1        /* lockstep rounds: round r (pass r of every
+                                  instance) is one launch per tile size,
+                                  the statistics two more launches */
+};
+
+/* Engine of later runs of the batch (the paper has no counterpart; how
+ * the ensemble's device work is issued): QS_BATCH_PERSISTENT (the default)
+ * or QS_BATCH_ROUNDS; anything else is QS_ERR_INVALID_ARG.  Both compute
+ * the same states (per-tile arithmetic of the same plans) and the same
+ * statistics partials, summed in the same order.  A change replans on the
+ * next run; autotuned tile sizes are cached per engine.  Host only. */
+qs_status qs_batch_set_engine(qs_batch *b, int engine);
 
 /* After a run: tile_log2[i] (count entries, may be NULL) receives the tile
  * size of instance i's passes (0 when its list is only the Hadamard layer),

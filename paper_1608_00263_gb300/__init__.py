@@ -15,13 +15,14 @@ from . import _native as N
 from ._native import (GATE_DTYPE, QSError, QS_C64, QS_C128, QS_H, QS_X_HALF, QS_Y_HALF, QS_T,
                       QS_CZ, QS_RX, QS_RY, QS_RZ, QS_CPHASE, QS_MODE_PLAIN, QS_MODE_FUSED,
                       QS_MODE_FUSED_TC, QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3,
-                      QS_PREC_BF16X6, QS_PREC_TF32X3, QS_PREC_TF32)
+                      QS_PREC_BF16X6, QS_PREC_TF32X3, QS_PREC_TF32, QS_BATCH_PERSISTENT,
+                      QS_BATCH_ROUNDS)
 
 __all__ = [
     "GATE_DTYPE", "QSError", "QS_C64", "QS_C128", "QS_H", "QS_X_HALF", "QS_Y_HALF", "QS_T",
     "QS_CZ", "QS_RX", "QS_RY", "QS_RZ", "QS_CPHASE", "QS_MODE_PLAIN", "QS_MODE_FUSED",
     "QS_MODE_FUSED_TC", "QS_PREC_DEFAULT", "QS_PREC_FP16X3", "QS_PREC_BF16X3",
-    "QS_PREC_BF16X6", "QS_PREC_TF32X3", "QS_PREC_TF32",
+    "QS_PREC_BF16X6", "QS_PREC_TF32X3", "QS_PREC_TF32", "QS_BATCH_PERSISTENT", "QS_BATCH_ROUNDS",
     "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
@@ -31,7 +32,7 @@ __all__ = [
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
     "qs_circuit_generate_dense", "qs_pt_convergence", "qs_noisy_circuit", "qs_batch_sample",
     "qs_batch_correlation", "qs_batch_mean_probabilities", "qs_single_error_circuit", "qs_batch_apply",
-    "qs_alu_rate", "qs_batch_set_options", "qs_batch_plan_info", "qs_build_flags", "qs_check_probe",
+    "qs_alu_rate", "qs_batch_set_options", "qs_batch_plan_info", "qs_batch_set_engine", "qs_build_flags", "qs_check_probe",
     "library_path",
 ]
 
@@ -373,6 +374,12 @@ def qs_batch_set_options(b, tile_log2=0, autotune=0, mode=QS_MODE_FUSED):
     include/qs.h."""
     o = _opts(mode, QS_PREC_DEFAULT, 0, tile_log2, autotune)
     N.check(N.lib().qs_batch_set_options(b, ctypes.byref(o)))
+
+
+def qs_batch_set_engine(b, engine):
+    """QS_BATCH_PERSISTENT (one persistent launch per run, the default) or
+    QS_BATCH_ROUNDS (lockstep rounds) for later runs; see include/qs.h."""
+    N.check(N.lib().qs_batch_set_engine(b, int(engine)))
 
 
 def qs_batch_plan_info(b):

@@ -21,6 +21,7 @@ QS_C64, QS_C128 = 0, 1
 QS_MODE_PLAIN, QS_MODE_FUSED, QS_MODE_FUSED_TC = 0, 1, 2
 (QS_PREC_DEFAULT, QS_PREC_FP16X3, QS_PREC_BF16X3, QS_PREC_BF16X6, QS_PREC_TF32X3,
  QS_PREC_TF32) = range(6)
+QS_BATCH_PERSISTENT, QS_BATCH_ROUNDS = 0, 1
 
 GATE_DTYPE = np.dtype([("kind", np.uint8), ("q0", np.uint8), ("q1", np.uint8),
                        ("pad", np.uint8), ("cycle", np.uint32), ("theta", np.float64)])
@@ -97,6 +98,7 @@ SIGNATURES = {
     "qs_check_probe": (ctypes.c_int, []),
     "qs_batch_set_options": (ctypes.c_int, [P, ctypes.POINTER(qs_opts)]),
     "qs_batch_plan_info": (ctypes.c_int, [P, P, PD]),
+    "qs_batch_set_engine": (ctypes.c_int, [P, ctypes.c_int]),
 }
 
 _lib = None

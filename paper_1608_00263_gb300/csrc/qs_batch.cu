@@ -3,19 +3,24 @@
 // The paper averages statistics over ensembles of circuit instances (Sec.
 // "Characterizing quantum supremacy": 10 instances per point; Sec.
 // "Convergence to Porter-Thomas": means and spreads over instances).  Here
-// every instance keeps its complex64 state resident in one device buffer;
-// instances advance in lockstep rounds: round r is one launch of the batched
-// fused-pass kernel over (instance, tile range) work items of every
-// instance's pass r (one launch per tile size).  Per-instance statistics
-// follow in two fixed-order reductions.  The device work of a run (reset,
-// rounds, statistics) is captured once into a CUDA graph and replayed while
-// the gate lists stay the same.
+// every instance keeps its complex64 state resident in one device buffer.
+// The default engine runs a whole batch as one persistent launch: a work
+// list of initial-state chunks, every instance's fused passes (round-major:
+// pass r of every instance before pass r + 1 of any) and statistics chunks,
+// taken from a device queue, each item waiting only for its own instance's
+// earlier items (per-instance completion counters, bounded waits).  The
+// lockstep engine instead makes round r one launch of the batched
+// fused-pass kernel over (instance, tile range) items of every instance's
+// pass r (one launch per tile size), with the statistics in two more
+// launches.  Either way the device work of a run is captured once into a
+// CUDA graph and replayed while the gate lists stay the same.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -26,7 +31,7 @@ using namespace qs;
 namespace {
 
 constexpr int kItemTiles = 8;              // tiles per work item of a round
-constexpr uint64_t kStatChunk = 1 << 16;   // amplitudes per statistics item
+constexpr uint64_t kStatChunk = kWorkChunk;   // amplitudes per statistics item
 
 // Initial states, one statistics item (<= 2^16 amplitudes of one instance,
 // a multiple of 32 at a 32-amplitude boundary) per block iteration: every
@@ -79,6 +84,8 @@ struct qs_batch {
     // (0 = the planner's default), or the autotuned size of each n
     int tile_log2 = 0;
     int autotune = 0;
+    int engine = QS_BATCH_PERSISTENT;
+    uint32_t *sync = nullptr;         // persistent engine: PersistCtl, then done[count]
     std::map<int, int> tile_for_n;    // tile bits chosen per instance size (autotune)
     std::map<int, double> tune_ms;     // the winner's time per size class
     std::vector<int> tile_used;        // tile bits of each instance's plan (0: no pass)
@@ -91,15 +98,17 @@ static void batch_release_plan(qs_batch *b)
     if (b->dev) cudaFree(b->dev);
     if (b->part) cudaFree(b->part);
     if (b->sums) cudaFree(b->sums);
+    if (b->sync) cudaFree(b->sync);
     b->dev = nullptr;
+    b->sync = nullptr;
     b->part = b->sums = nullptr;
     b->ready = false;
 }
 
-// Tile sizes chosen by the autotuner, per (device, qubits): a process-wide
+// Tile sizes chosen by the autotuner, per (device, qubits, engine): a process-wide
 // cache, so later batches with instances of the same size skip the timing.
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int>, int> g_tuned_tile;
+static std::map<std::tuple<int, int, int>, int> g_tuned_tile;
 
 // Plans for instances `idx` with tile size tbits[i] (0 = default), on host
 // threads.  plans[i] is left empty for instances not listed or whose list
@@ -231,11 +240,123 @@ static qs_status launch_rounds(const qs_batch *b, cudaStream_t st, const Rounds 
     return QS_OK;
 }
 
+// The per-pass interpreter choice of the listed instances' plans (the
+// persistent work items carry it).
+static std::vector<std::vector<char>> full_flags(const std::vector<Plan> &plans)
+{
+    std::vector<std::vector<char>> f(plans.size());
+    for (size_t i = 0; i < plans.size(); ++i)
+        for (size_t r = 0; r < plans[i].passes.size(); ++r) f[i].push_back(plan_pass_needs_full(plans[i], (int)r));
+    return f;
+}
+
+// Work layout in one device buffer: passes | phases | ops | items, each
+// 256-byte aligned.
+static RoundOffsets work_offsets(const Work &W)
+{
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    RoundOffsets o;
+    o.pass = 0;
+    o.phase = align(o.pass + W.passes.size() * sizeof(DevPass));
+    o.op = align(o.phase + W.phases.size() * sizeof(DevPhase));
+    o.item = align(o.op + W.ops.size() * sizeof(DevOp));
+    o.total = align(o.item + W.items.size() * sizeof(PersistItem));
+    return o;
+}
+
+static void work_pack(const Work &W, const RoundOffsets &o, unsigned char *host)
+{
+    std::memcpy(host + o.pass, W.passes.data(), W.passes.size() * sizeof(DevPass));
+    std::memcpy(host + o.phase, W.phases.data(), W.phases.size() * sizeof(DevPhase));
+    std::memcpy(host + o.op, W.ops.data(), W.ops.size() * sizeof(DevOp));
+    if (!W.items.empty()) std::memcpy(host + o.item, W.items.data(), W.items.size() * sizeof(PersistItem));
+}
+
+// Zeroes the queue head, the abort / error words and the completion
+// counters, then launches the persistent kernel over the packed work.
+static qs_status launch_work(const qs_batch *b, cudaStream_t st, const Work &W, const RoundOffsets &o,
+                             const unsigned char *D, uint32_t *sync, double *part, double *sums)
+{
+    const size_t words = sizeof(PersistCtl) / 4 + (size_t)b->count;
+    QS_CUDA_TRY(cudaMemsetAsync(sync, 0, words * 4, st));
+    bool any_full = false;
+    for (const PersistItem &w : W.items) any_full = any_full || w.kind == kPersistPassFull;
+    return launch_batch_persistent(st, b->num_sms, b->amps, (const PersistItem *)(D + o.item), (int)W.items.size(),
+                                   (const DevPass *)(D + o.pass), (const DevPhase *)(D + o.phase),
+                                   (const DevOp *)(D + o.op), sync + sizeof(PersistCtl) / 4, (PersistCtl *)sync,
+                                   part, sums, any_full);
+}
+
+// Reads the persistent kernel's error word after its stream has finished.
+static qs_status work_error(const uint32_t *sync)
+{
+    PersistCtl c;
+    QS_CUDA_TRY(cudaMemcpy(&c, sync, sizeof c, cudaMemcpyDeviceToHost));
+    if (c.err) return set_error(QS_ERR_TIMEOUT, "ensemble kernel: a dependency wait ran out");
+    return QS_OK;
+}
+
+// One untimed and one timed run (CUDA events) of the listed instances'
+// evolution with the given plans on the batch's engine; *ms = the timed
+// run.  The runs overwrite those instances' states.
+static qs_status time_plans(qs_batch *b, const std::vector<Plan> &plans, const std::vector<int> &idx,
+                            const std::vector<size_t> &hl, cudaEvent_t e0, cudaEvent_t e1, float *ms, bool *empty)
+{
+    Rounds R;
+    Work W;
+    RoundOffsets o;
+    std::vector<unsigned char> host;
+    if (b->engine == QS_BATCH_ROUNDS) {
+        build_rounds(b, plans, idx, &R);
+        *empty = R.launches.empty();
+        o = round_offsets(R);
+        host.assign(o.total, 0);
+        round_pack(R, o, host.data());
+    } else {
+        build_work(b->n, b->off, plans, full_flags(plans), idx, hl, false, &W);
+        *empty = W.passes.empty();
+        o = work_offsets(W);
+        host.assign(o.total, 0);
+        work_pack(W, o, host.data());
+    }
+    if (*empty) return QS_OK;
+    void *dev = nullptr, *sync = nullptr;
+    cudaError_t e = cudaMalloc(&dev, o.total);
+    if (e == cudaSuccess) e = cudaMalloc(&sync, sizeof(PersistCtl) + 4 * (size_t)b->count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (dev) cudaFree(dev);
+        return set_error(QS_ERR_OOM, "autotune plan buffer: %s", cudaGetErrorString(e));
+    }
+    qs_status rc = QS_OK;
+    e = cudaMemcpy(dev, host.data(), o.total, cudaMemcpyHostToDevice);
+    auto run = [&]() -> qs_status {
+        if (b->engine == QS_BATCH_ROUNDS) return launch_rounds(b, b->cap_stream, R, o, (const unsigned char *)dev);
+        return launch_work(b, b->cap_stream, W, o, (const unsigned char *)dev, (uint32_t *)sync, nullptr, nullptr);
+    };
+    if (e == cudaSuccess) rc = run();
+    if (e == cudaSuccess && !rc) {
+        cudaEventRecord(e0, b->cap_stream);
+        rc = run();
+        cudaEventRecord(e1, b->cap_stream);
+        if (!rc) e = cudaEventSynchronize(e1);
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    }
+    cudaError_t ef = cudaStreamSynchronize(b->cap_stream);
+    if (e == cudaSuccess) e = ef;
+    if (!rc && e != cudaSuccess) rc = set_error(QS_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
+    if (!rc && b->engine != QS_BATCH_ROUNDS) rc = work_error((const uint32_t *)sync);
+    cudaFree(dev);
+    cudaFree(sync);
+    return rc;
+}
+
 // Autotuner: for every instance size n not yet in the cache, time the
-// lockstep rounds of the batch's own instances of that size (their real
-// circuits, on their own state memory, which the run resets afterwards)
-// with each candidate tile size -- 9..13 qubits, capped at n -- and keep
-// the fastest.  One untimed and one timed run (CUDA events) per candidate.
+// evolution of the batch's own instances of that size (their real circuits,
+// on their own state memory, which the run resets afterwards) on the
+// batch's engine with each candidate tile size -- 9..13 qubits, capped at
+// n -- and keep the fastest.  One untimed and one timed run (CUDA events)
+// per candidate.  The cache is per (device, n, engine).
 static qs_status batch_autotune(qs_batch *b, const qs_gate *gates, const uint64_t *offsets,
                                 const std::vector<size_t> &hl)
 {
@@ -250,7 +371,7 @@ static qs_status batch_autotune(qs_batch *b, const qs_gate *gates, const uint64_
         const int n = kv.first;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tuned_tile.find({b->device, n});
+            auto it = g_tuned_tile.find(std::make_tuple(b->device, n, b->engine));
             if (it != g_tuned_tile.end()) {
                 b->tile_for_n[n] = it->second;
                 continue;
@@ -262,34 +383,10 @@ static qs_status batch_autotune(qs_batch *b, const qs_gate *gates, const uint64_
             std::vector<int> tb(b->count, t);
             std::vector<Plan> plans;
             if ((rc = plan_instances(b, gates, offsets, hl, kv.second, tb, &plans))) break;
-            Rounds R;
-            build_rounds(b, plans, kv.second, &R);
-            if (R.launches.empty()) break;          // only Hadamard layers: nothing to time
-            const RoundOffsets o = round_offsets(R);
-            std::vector<unsigned char> host(o.total, 0);
-            round_pack(R, o, host.data());
-            void *dev = nullptr;
-            cudaError_t e = cudaMalloc(&dev, o.total);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                rc = set_error(QS_ERR_OOM, "autotune plan buffer: %s", cudaGetErrorString(e));
-                break;
-            }
-            e = cudaMemcpy(dev, host.data(), o.total, cudaMemcpyHostToDevice);
             float ms = 0;
-            if (e == cudaSuccess) rc = launch_rounds(b, b->cap_stream, R, o, (const unsigned char *)dev);
-            if (e == cudaSuccess && !rc) {
-                cudaEventRecord(e0, b->cap_stream);
-                rc = launch_rounds(b, b->cap_stream, R, o, (const unsigned char *)dev);
-                cudaEventRecord(e1, b->cap_stream);
-                if (!rc) e = cudaEventSynchronize(e1);
-                if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            }
-            cudaError_t ef = cudaStreamSynchronize(b->cap_stream);
-            cudaFree(dev);
-            if (e == cudaSuccess) e = ef;
-            if (!rc && e != cudaSuccess) rc = set_error(QS_ERR_CUDA, "autotune run: %s", cudaGetErrorString(e));
-            if (rc) break;
+            bool empty = false;
+            if ((rc = time_plans(b, plans, kv.second, hl, e0, e1, &ms, &empty))) break;
+            if (empty) break;                       // only Hadamard layers: nothing to time
             if (ms < best_ms) {
                 best_ms = ms;
                 best_t = t;
@@ -300,7 +397,7 @@ static qs_status batch_autotune(qs_batch *b, const qs_gate *gates, const uint64_
             b->tile_for_n[n] = best_t;
             b->tune_ms[n] = best_ms;
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            g_tuned_tile[{b->device, n}] = best_t;
+            g_tuned_tile[std::make_tuple(b->device, n, b->engine)] = best_t;
         }
     }
     cudaEventDestroy(e0);
@@ -360,6 +457,21 @@ extern "C" qs_status qs_batch_set_options(qs_batch *b, const qs_opts *opts)
     b->tile_for_n.clear();
     b->tune_ms.clear();
     b->ready = false;                 // the next run replans
+    return QS_OK;
+}
+
+extern "C" qs_status qs_batch_set_engine(qs_batch *b, int engine)
+{
+    clear_error();
+    if (!b) return set_error(QS_ERR_INVALID_ARG, "batch is NULL");
+    if (engine != QS_BATCH_PERSISTENT && engine != QS_BATCH_ROUNDS)
+        return set_error(QS_ERR_INVALID_ARG, "engine %d is neither QS_BATCH_PERSISTENT nor QS_BATCH_ROUNDS", engine);
+    if (engine != b->engine) {
+        b->engine = engine;
+        b->tile_for_n.clear();
+        b->tune_ms.clear();
+        b->ready = false;             // the next run replans
+    }
     return QS_OK;
 }
 
@@ -453,6 +565,24 @@ extern "C" qs_status qs_batch_mean_probabilities(qs_batch *b, double *out)
     return st;
 }
 
+// Ends the capture of a run on the batch's private stream and instantiates
+// its graph (rs: the status of the captured launches).
+static qs_status batch_end_capture(qs_batch *b, qs_status rs)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rs) {
+        if (graph) cudaGraphDestroy(graph);
+        return rs;
+    }
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    b->ready = true;
+    return QS_OK;
+}
+
 // Plans every instance, lays out the concatenated plan, work items and
 // statistics items in one device buffer, and records the run as a graph.
 static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t *offsets)
@@ -472,12 +602,32 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
     }
     std::vector<Plan> plans;
     if (qs_status s0 = plan_instances(b, gates, offsets, hl, all, tbits, &plans)) return s0;
-    Rounds R;
-    build_rounds(b, plans, all, &R);
-    b->round_bytes = R.bytes;
     b->tile_used.assign(C, 0);
     for (int i = 0; i < C; ++i)
         if (!plans[i].passes.empty()) b->tile_used[i] = plans[i].passes[0].t;
+    if (b->engine == QS_BATCH_PERSISTENT) {
+        // one persistent launch: initial states, passes, statistics
+        Work W;
+        build_work(b->n, b->off, plans, full_flags(plans), all, hl, true, &W);
+        b->round_bytes = W.bytes;
+        const RoundOffsets wo = work_offsets(W);
+        std::vector<unsigned char> host(wo.total, 0);
+        work_pack(W, wo, host.data());
+        batch_release_plan(b);
+        QS_CUDA_TRY(cudaMalloc(&b->dev, wo.total));
+        QS_CUDA_TRY(cudaMalloc((void **)&b->part, (size_t)std::max(1, W.nslots) * kStatSums * sizeof(double)));
+        QS_CUDA_TRY(cudaMalloc((void **)&b->sums, (size_t)C * kStatSums * sizeof(double)));
+        QS_CUDA_TRY(cudaMalloc((void **)&b->sync, sizeof(PersistCtl) + 4 * (size_t)C));
+        QS_CUDA_TRY(cudaMemcpy(b->dev, host.data(), wo.total, cudaMemcpyHostToDevice));
+        if (qs_status s0 = batch_kernel_setup()) return s0;
+        QS_CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const qs_status rs =
+            launch_work(b, b->cap_stream, W, wo, (const unsigned char *)b->dev, b->sync, b->part, b->sums);
+        return batch_end_capture(b, rs);
+    }
+    Rounds R;
+    build_rounds(b, plans, all, &R);
+    b->round_bytes = R.bytes;
     // statistics items
     std::vector<uint64_t> s_off, s_cnt;
     std::vector<float> s_scale, s_fill, s_first;
@@ -537,18 +687,7 @@ static qs_status batch_prepare(qs_batch *b, const qs_gate *gates, const uint64_t
         rs = launch_batch_stats(b->cap_stream, b->num_sms, b->amps, (const uint64_t *)(D + o_so),
                                 (const uint64_t *)(D + o_sc), (const float *)(D + o_ss), nsi,
                                 (const int *)(D + o_fi), C, b->part, b->sums);
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
-    if (rs) {
-        if (graph) cudaGraphDestroy(graph);
-        return rs;
-    }
-    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&b->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return set_error(QS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    b->ready = true;
-    return QS_OK;
+    return batch_end_capture(b, rs);
 }
 
 static qs_status batch_run_impl(qs_batch *b, const qs_gate *gates, const uint64_t *offsets, int kmax,
@@ -573,7 +712,11 @@ static qs_status batch_run_impl(qs_batch *b, const qs_gate *gates, const uint64_
     b->host_sums.resize((size_t)b->count * kStatSums);
     QS_CUDA_TRY(cudaMemcpyAsync(b->host_sums.data(), b->sums, b->host_sums.size() * sizeof(double),
                                 cudaMemcpyDeviceToHost, b->user_stream));
+    PersistCtl ctl{};
+    if (b->sync)
+        QS_CUDA_TRY(cudaMemcpyAsync(&ctl, b->sync, sizeof ctl, cudaMemcpyDeviceToHost, b->user_stream));
     QS_CUDA_TRY(cudaStreamSynchronize(b->user_stream));
+    if (ctl.err) return set_error(QS_ERR_TIMEOUT, "ensemble kernel: a dependency wait ran out");
     const int w = 3 + kmax;
     if (stats)
         for (int i = 0; i < b->count; ++i) {

@@ -51,6 +51,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return false;
 }
 
+// Acquire load of a global counter at GPU scope: writes released before the
+// increments it observes are visible to this thread's later loads.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Waits until the counter *count reaches `target` (acquire), for at most
+// `limit_ns` nanoseconds of the global timer and `max_iter` polls.  Gives
+// up early when *abort becomes nonzero (another CTA's wait ran out).
+// Returns 0 when the target was reached, 1 when the limit ran out, 2 on
+// abort; never blocks longer.
+__device__ __forceinline__ int flag_wait_bounded(const unsigned int *count, unsigned int target,
+                                                 const unsigned int *abort, uint64_t limit_ns,
+                                                 uint32_t max_iter = 1u << 24)
+{
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t it = 0; it < max_iter; ++it) {
+        if (ld_acquire_gpu(count) >= target) return 0;
+        if (*(volatile const unsigned int *)abort) return 2;
+        uint64_t t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 >= limit_ns) return 1;
+        __nanosleep(128);
+    }
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
 // Checked build (QS_CHECKED): device-side index checks.  A failed check
 // records its site code in this translation unit's check word (the first

@@ -29,6 +29,7 @@
 #include <cstring>
 
 #include "qs_device.cuh"
+#include "qs_stats_device.cuh"
 
 namespace qs {
 
@@ -790,14 +791,35 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
     __syncthreads();
 }
 
+// Barrier of the threads that work on one tile: the whole CTA, or in the
+// grouped form the tile's thread group (named barrier 1 + group for groups
+// of whole warps, a warp-lane barrier for smaller groups).
+template <bool GROUPED>
+__device__ __forceinline__ void tile_sync(int nthr, int gi)
+{
+    if constexpr (!GROUPED) {
+        __syncthreads();
+    } else if (nthr >= 32) {
+        asm volatile("bar.sync %0, %1;" ::"r"(gi + 1), "r"(nthr) : "memory");
+    } else {
+        const unsigned lane0 = (threadIdx.x & 31u) & ~(unsigned)(nthr - 1);
+        __syncwarp((nthr == 32 ? 0xffffffffu : ((1u << nthr) - 1u)) << lane0);
+    }
+}
+
 // One launch = one pass over the state.  blockDim.x = 2^(t - RB).
 // TCP > 0: tensor-core variant of operand precision TCP (complex64, t = 13);
 // its dynamic shared memory holds the tile (and a separate B buffer when
 // the precision's B terms exceed the tile's 64 KB).
 // Runs tiles [t_begin, t_end) of one pass on `amps`: stages the pass's
 // phases and ops into shared memory, then loads, transforms and stores each
-// tile.  Shared by the single-state kernel and the batched kernel.
-template <typename R, int RB, int TCP, bool FULL>
+// tile.  Shared by the single-state kernel and the batched kernels.
+// GROUPED: the CTA has kThreadsMax threads whatever the tile size; it splits
+// into blockDim.x / 2^(t - RB) groups of 2^(t - RB) threads, each with its
+// own tile buffer (2^t amplitudes at 2^t * group in the dynamic shared
+// memory), and group g runs tiles t_begin + g, t_begin + g + groups, ...
+// with its own barriers (the staged pass is shared).
+template <typename R, int RB, int TCP, bool FULL, bool GROUPED = false>
 __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__ amps,
                                                 const DevPass *__restrict__ pass_g,
                                                 const DevPhase *__restrict__ phases_g,
@@ -810,20 +832,24 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     constexpr int NS = 1 << RB;                 // register slots per thread
     constexpr int CE = 16 / (int)sizeof(V);     // elements per 16-byte unit
     constexpr int CPT = NS / CE;                // 16-byte units per thread
+    static_assert(!(GROUPED && TCP), "the grouped form has no tensor-core phases");
     V *tile = reinterpret_cast<V *>(smem_raw);
 
-    const int tid = threadIdx.x;
-    const int nthr = blockDim.x;
-    for (int i = tid; i < (int)(sizeof(DevPass) / 4); i += nthr)
+    for (int i = threadIdx.x; i < (int)(sizeof(DevPass) / 4); i += blockDim.x)
         reinterpret_cast<uint32_t *>(&S.P)[i] = reinterpret_cast<const uint32_t *>(pass_g)[i];
     __syncthreads();
     const int t = S.P.t;
     const int ng = S.P.n - t;                   // out-of-tile qubits
     const int nph = S.P.nphases;
+    // tile threads: the CTA, or one group of the grouped form
+    const int nthr = GROUPED ? (1 << (t - RB)) : (int)blockDim.x;
+    const int tid = GROUPED ? (int)(threadIdx.x & (unsigned)(nthr - 1)) : (int)threadIdx.x;
+    const int gi = GROUPED ? (int)(threadIdx.x >> (t - RB)) : 0;
+    const int ngr = GROUPED ? (int)(blockDim.x >> (t - RB)) : 1;
     // ---- stage phases, ops and per-thread phase tables (once per CTA) ----
     for (int ph = 0; ph < nph; ++ph) {
         const DevPhase &D = phases_g[S.P.phase_begin + ph];
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             for (int j = 0; j < RB; ++j) S.ph[ph].pb[j] = swz<CE>(1u << D.R[j]) * (uint32_t)sizeof(V);
             S.ph[ph].op_begin = D.op_begin - phases_g[S.P.phase_begin].op_begin;
             S.ph[ph].op_end = D.op_end - phases_g[S.P.phase_begin].op_begin;
@@ -850,8 +876,10 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                 q |= (uint64_t)bit << S.P.L[b];
             }
         }
-        S.th[ph][tid].phys = swz<CE>(e) * (uint32_t)sizeof(V);
-        S.th[ph][tid].qoff = q;
+        if (gi == 0) {
+            S.th[ph][tid].phys = swz<CE>(e) * (uint32_t)sizeof(V);
+            S.th[ph][tid].qoff = q;
+        }
     }
     int ntc = 0;
     if (TCP) {
@@ -884,7 +912,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     {
         const int o0 = phases_g[S.P.phase_begin].op_begin;
         const int o1 = phases_g[S.P.phase_begin + nph - 1].op_end;
-        for (int o = o0 + tid; o < o1; o += nthr) {
+        for (int o = o0 + (int)threadIdx.x; o < o1; o += (int)blockDim.x) {
             const DevOp &d = ops_g[o];
             SOp<R> so;
             const bool tphase = d.type == OP_PHASE && d.m[0] == d.m[1] && d.m[0] > 0.7071 && d.m[0] < 0.7072;
@@ -910,7 +938,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             S.ops[o - o0] = so;
         }
     }
-    for (int i = tid; i < CPT; i += nthr) S.it_off[i] = deposit((uint64_t)(CE * nthr) * i, S.P.L, t);
+    for (int i = threadIdx.x; i < CPT; i += blockDim.x) S.it_off[i] = deposit((uint64_t)(CE * nthr) * i, S.P.L, t);
     const uint64_t tid_off = deposit((uint64_t)CE * tid, S.P.L, t);
     const R gsr = (R)S.P.gscale_re, gsi = (R)S.P.gscale_im;
     const bool gscale_one = (S.P.gscale_re == 1.0 && S.P.gscale_im == 0.0);
@@ -919,19 +947,22 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     // register phase; otherwise it is applied at the tile store
     const bool gs_in_phase = !gscale_one && S.ph[nph - 1].kind == 0;
     const bool gs_at_store = !gscale_one && !gs_in_phase;
+    // this thread's tile buffer (the group's in the grouped form)
+    unsigned char *gsm = GROUPED ? smem_raw + ((size_t)gi << t) * sizeof(V) : smem_raw;
     // tile element CE (it nthr + tid) sits at swizzled byte offset
     // sw_tid ^ swz(CE it nthr) (the swizzle is linear, the bits are disjoint)
-    const uint32_t tile_sa = smem_addr(smem_raw);
+    const uint32_t tile_sa = smem_addr(gsm);
     const uint32_t sw_tid = swz<CE>((uint32_t)(CE * tid)) * (uint32_t)sizeof(V);
 
     // the tile base (bits of the out-of-tile qubits) advances by a masked
-    // increment over the contiguous tile range
+    // increment over the contiguous tile range (grouped: deposited afresh,
+    // the group's tiles being `ngr` apart)
     uint64_t gmask = 0;
     for (int i = 0; i < ng; ++i) gmask |= 1ULL << S.P.G[i];
     uint64_t lmask = 0;             // every tile bit's qubit (checked build)
     for (int b = 0; b < t; ++b) lmask |= 1ULL << S.P.L[b];
     (void)lmask;
-    uint64_t base = deposit(t_begin, S.P.G, ng);
+    uint64_t base = deposit(t_begin + (uint64_t)gi, S.P.G, ng);
     uint32_t tc_parity = 0;
     // runs of consecutive amplitudes per tile = 2^(t - c); with c = RB for
     // complex64 (5) and complex128 (4) there is one 256-byte run per thread
@@ -939,26 +970,39 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     const bool prefetch_runs = (t - kRunBits) >= 0 && (1 << (t - kRunBits)) == nthr &&
                                S.P.L[kRunBits - 1] == kRunBits - 1;
     const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
-    for (uint64_t tau = t_begin; tau < t_end; ++tau, base = ((base | ~gmask) + 1) & gmask) {
+    // grouped form: every group runs the same number of iterations, so the
+    // warps that hold several small groups stay converged up to the CTA's
+    // closing barrier; a group past the end of the range (inactive) only
+    // takes part in its barriers
+    for (uint64_t tau0 = t_begin; tau0 < t_end;
+         tau0 += (uint64_t)ngr,
+                  base = GROUPED ? deposit(tau0 + (uint64_t)gi, S.P.G, ng) : (((base | ~gmask) + 1) & gmask)) {
+        const uint64_t tau = tau0 + (uint64_t)gi;
+        bool active = !GROUPED || tau < t_end;
         if (TCP && TS.abort) break;
         // the tile's highest element index must lie inside the state
-        if (!QS_DCHECK(((base | lmask) >> S.P.n) == 0, 201)) break;
+        if (active && !QS_DCHECK(((base | lmask) >> S.P.n) == 0, 201)) {
+            if constexpr (!GROUPED) break;
+            active = false;
+        }
         // out-of-tile and thread bits are disjoint from it_off: OR = add
         const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
+        if (active) {
 #pragma unroll
-        for (int it = 0; it < CPT; ++it) {
-            const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tile_sa + sw),
-                         "l"(tsrc + S.it_off[it])
-                         : "memory");
+            for (int it = 0; it < CPT; ++it) {
+                const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tile_sa + sw),
+                             "l"(tsrc + S.it_off[it])
+                             : "memory");
+            }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncthreads();
+        tile_sync<GROUPED>(nthr, gi);
         // warm L2 with the next tile: thread i prefetches run i (2^c
         // consecutive amplitudes, 256 bytes) while this tile is processed
-        if (prefetch_runs && tau + 1 < t_end) {
-            const uint64_t nb = ((base | ~gmask) + 1) & gmask;
+        if (active && prefetch_runs && tau + (uint64_t)ngr < t_end) {
+            const uint64_t nb = GROUPED ? deposit(tau + (uint64_t)ngr, S.P.G, ng) : (((base | ~gmask) + 1) & gmask);
             const V *p = amps + (nb | run_off);
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
         }
@@ -974,6 +1018,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                     continue;
                 }
             }
+            if (active) {
             const SThread T = S.th[ph][tid];
             const uint64_t idx_th = base | T.qoff;
             uint32_t pb[RB];
@@ -983,9 +1028,9 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             V a[NS];
             // slots in Gray-code order: one XOR per slot address
             if (CE == 2 && paired)
-                SlotIO<NS / 2, 1>::template load<V>(a, reinterpret_cast<const char *>(smem_raw), T.phys, pb);
+                SlotIO<NS / 2, 1>::template load<V>(a, reinterpret_cast<const char *>(gsm), T.phys, pb);
             else
-                SlotIO<NS, 0>::template load<V>(a, reinterpret_cast<const char *>(smem_raw), T.phys, pb);
+                SlotIO<NS, 0>::template load<V>(a, reinterpret_cast<const char *>(gsm), T.phys, pb);
             R fr = (R)1, fi = (R)0;             // thread-uniform pending factor
             const int ob = S.ph[ph].op_begin, oe = S.ph[ph].op_end, ub = S.ph[ph].uniform_begin;
             const bool fpend = ub < oe;
@@ -1043,19 +1088,20 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                 for (int j = 0; j < RB; ++j) pb2[j] = S.ph[ph].pb[j];
                 const uint32_t phys = S.th[ph][tid].phys;
                 if (CE == 2 && S.ph[ph].paired)
-                    SlotIO<NS / 2, 1>::template store<V>(a, reinterpret_cast<char *>(smem_raw), phys, pb2);
+                    SlotIO<NS / 2, 1>::template store<V>(a, reinterpret_cast<char *>(gsm), phys, pb2);
                 else
-                    SlotIO<NS, 0>::template store<V>(a, reinterpret_cast<char *>(smem_raw), phys, pb2);
+                    SlotIO<NS, 0>::template store<V>(a, reinterpret_cast<char *>(gsm), phys, pb2);
             }
-            __syncthreads();
+            }  // active
+            tile_sync<GROUPED>(nthr, gi);
         }
         // ---- store the tile ----
         V *tdst = amps + (base | tid_off);
 #pragma unroll
-        for (int it = 0; it < CPT; ++it) {
+        for (int it = 0; it < CPT && active; ++it) {
             const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
             V v[CE];
-            *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(smem_raw + sw);
+            *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(gsm + sw);
             if (gs_at_store) {
 #pragma unroll
                 for (int q = 0; q < CE; ++q) {
@@ -1066,7 +1112,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
             }
             *reinterpret_cast<float4 *>(tdst + S.it_off[it]) = *reinterpret_cast<const float4 *>(v);
         }
-        __syncthreads();
+        tile_sync<GROUPED>(nthr, gi);
     }
     if constexpr (TCP > 0)
         if (ntc) tc_teardown<TCP>(TS);
@@ -1143,6 +1189,84 @@ k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict_
         const BatchItem w = items[it];
         fused_pass_body<R, RB, 0, FULL>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.tile_begin,
                                       w.tile_end, nullptr, nullptr, S, TS, smem_raw);
+    }
+}
+
+// Persistent ensemble kernel (see PersistItem): kThreadsMax threads per CTA
+// whatever the instances' tile sizes (passes run in the grouped form), two
+// CTAs per SM.  Thread 0 takes the next item from the queue head, waits for
+// the item's dependencies (acquire, bounded by kPersistWaitNs), the CTA
+// runs it, and thread 0 publishes its completion (release).  A wait that
+// runs out sets ctl->err and ctl->abort; from then on items are taken and
+// counted without work, so every CTA finishes and the host reports the
+// timeout.  The last statistics item of an instance to finish sums the
+// instance's partials in slot order (deterministic).
+template <int RB, bool ANY_FULL>
+__global__ void __launch_bounds__(kThreadsMax, 2)
+k_batch_persistent(float2 *amps, const PersistItem *__restrict__ items, int nitems,
+                   const DevPass *__restrict__ passes, const DevPhase *__restrict__ phases_g,
+                   const DevOp *__restrict__ ops_g, uint32_t *done, PersistCtl *ctl, double *part,
+                   double *sums, uint64_t wait_ns)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FusedSmem<float, RB> S;
+    __shared__ TcSmem TS;
+    __shared__ int s_item, s_go, s_last;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&ctl->next, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const PersistItem w = items[it];
+        if (threadIdx.x == 0) {
+            int go = *(volatile const uint32_t *)&ctl->abort == 0;
+            if (go && w.need) {
+                const int r = flag_wait_bounded(done + w.inst, w.need, &ctl->abort, wait_ns);
+                if (r == 1) {
+                    atomicExch(&ctl->err, 1u);
+                    atomicExch(&ctl->abort, 1u);
+                }
+                go = r == 0;
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (s_go) {
+            if (w.kind == kPersistInit) {
+                float4 *a = reinterpret_cast<float4 *>(amps + w.amp_off);
+                const float4 u = make_float4(w.f0, 0.f, w.f0, 0.f);
+                for (uint32_t e = threadIdx.x; e < w.lo / 2; e += blockDim.x) a[e] = u;
+                if (threadIdx.x == 0) a[0] = make_float4(w.f1, 0.f, w.f0, 0.f);
+            } else if (w.kind == kPersistPass) {
+                fused_pass_body<float, RB, 0, false, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.lo,
+                                                           w.hi, nullptr, nullptr, S, TS, smem_raw);
+            } else if (w.kind == kPersistPassFull) {
+                // (the launch compiles the full interpreter in only when
+                // some item needs it)
+                if constexpr (ANY_FULL)
+                    fused_pass_body<float, RB, 0, true, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g,
+                                                              w.lo, w.hi, nullptr, nullptr, S, TS, smem_raw);
+            } else {
+                batch_stats_chunk(amps + w.amp_off, w.lo, w.f0, part + (size_t)w.pass * kStatAcc);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint32_t prev = atomicAdd(done + w.inst, 1u);
+            if (w.kind == kPersistStats) {
+                s_last = prev + 1 == w.total;
+                __threadfence();
+            }
+        }
+        if (w.kind == kPersistStats) {
+            __syncthreads();
+            if (s_last && threadIdx.x < kStatAcc) {
+                double acc = 0;
+                for (uint32_t j = 0; j < w.nslots; ++j) acc += __ldcg(part + (size_t)(w.hi + j) * kStatAcc + threadIdx.x);
+                sums[(size_t)w.inst * kStatAcc + threadIdx.x] = acc;
+            }
+        }
     }
 }
 
@@ -1228,8 +1352,35 @@ qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const voi
     return QS_OK;
 }
 
+// Resident CTAs per SM of the two persistent-kernel variants (occupancy
+// API, set by batch_kernel_setup before any launch or capture).
+static int g_persist_per_sm[2] = {2, 2};
+
+qs_status launch_batch_persistent(cudaStream_t st, int num_sms, void *amps, const PersistItem *items, int nitems,
+                                  const DevPass *passes, const DevPhase *phases, const DevOp *ops,
+                                  uint32_t *done, PersistCtl *ctl, double *part, double *sums, bool any_full)
+{
+    if (nitems <= 0) return QS_OK;
+    const int cap = num_sms * g_persist_per_sm[any_full ? 1 : 0];
+    const int grid = nitems < cap ? nitems : cap;
+    auto kern = any_full ? k_batch_persistent<5, true> : k_batch_persistent<5, false>;
+    kern<<<grid, kThreadsMax, 65536, st>>>((float2 *)amps, items, nitems, passes, phases, ops, done, ctl, part, sums,
+                                           kPersistWaitNs);
+    QS_LAUNCH_CHECK();
+    return QS_OK;
+}
+
+int batch_persistent_ctas_per_sm(bool any_full) { return g_persist_per_sm[any_full ? 1 : 0]; }
+
 qs_status batch_kernel_setup()
 {
+    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_persistent<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_persistent<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
+    QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_persist_per_sm[0], k_batch_persistent<5, false>,
+                                                              kThreadsMax, 65536));
+    QS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_persist_per_sm[1], k_batch_persistent<5, true>,
+                                                              kThreadsMax, 65536));
+    for (int &v : g_persist_per_sm) v = v < 1 ? 1 : v;
     QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     QS_CUDA_TRY(cudaFuncSetAttribute(k_batch_pass<float, 5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536));
     return QS_OK;

@@ -846,6 +846,101 @@ static void pack_block(const std::vector<Cplx> &U, int precision, std::vector<ui
 
 }  // namespace
 
+// Persistent ensemble work list (declared with its order and dependency
+// rules in qs_internal.h).
+static uint64_t tiles_per_item(int t) { return t >= 16 ? 1 : (1ULL << (16 - t)); }
+
+void build_work(const std::vector<int> &n, const std::vector<uint64_t> &off, const std::vector<Plan> &plans,
+                const std::vector<std::vector<char>> &full, const std::vector<int> &idx,
+                const std::vector<size_t> &hl, bool stats, Work *W)
+{
+    *W = Work();
+    const size_t C = n.size();
+    std::vector<int> first_pass(C, 0);
+    std::vector<uint32_t> ninit(C, 0), npass(C, 0), nstat(C, 0), before(C, 0);
+    int max_passes = 0;
+    for (int i : idx) {
+        first_pass[i] = (int)W->passes.size();
+        const int pb = (int)W->phases.size(), ob = (int)W->ops.size();
+        for (DevPass p : plans[i].passes) {
+            p.phase_begin += pb;
+            W->passes.push_back(p);
+        }
+        for (DevPhase h : plans[i].phases) {
+            h.op_begin += ob;
+            h.op_end += ob;
+            W->phases.push_back(h);
+        }
+        W->ops.insert(W->ops.end(), plans[i].ops.begin(), plans[i].ops.end());
+        max_passes = std::max(max_passes, (int)plans[i].passes.size());
+        W->bytes += (double)plans[i].passes.size() * 16.0 * std::ldexp(1.0, n[i]);
+        const uint64_t N = 1ULL << n[i];
+        ninit[i] = (uint32_t)((N + kWorkChunk - 1) / kWorkChunk);
+        nstat[i] = stats ? ninit[i] : 0;
+        for (const DevPass &p : plans[i].passes) {
+            const uint64_t nt = 1ULL << (n[i] - p.t), per = tiles_per_item(p.t);
+            npass[i] += (uint32_t)((nt + per - 1) / per);
+        }
+    }
+    auto item = [&](uint32_t kind, int i) {
+        PersistItem w;
+        std::memset(&w, 0, sizeof w);
+        w.kind = kind;
+        w.inst = (uint32_t)i;
+        w.total = ninit[i] + npass[i] + nstat[i];
+        return w;
+    };
+    for (int i : idx) {
+        const uint64_t N = 1ULL << n[i];
+        const float v = hl[i] ? (float)std::pow(2.0, -0.5 * n[i]) : 0.f;
+        for (uint64_t a = 0; a < N; a += kWorkChunk) {
+            PersistItem w = item(kPersistInit, i);
+            w.amp_off = off[i] + a;
+            w.lo = (uint32_t)std::min<uint64_t>(kWorkChunk, N - a);
+            w.f0 = v;
+            w.f1 = hl[i] ? v : (a == 0 ? 1.f : 0.f);
+            W->items.push_back(w);
+        }
+        before[i] = ninit[i];
+    }
+    std::vector<int> order(idx);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return n[x] > n[y]; });
+    for (int r = 0; r < max_passes; ++r)
+        for (int i : order) {
+            if (r >= (int)plans[i].passes.size()) continue;
+            const DevPass &p = plans[i].passes[r];
+            const uint32_t kind = full[i][r] ? kPersistPassFull : kPersistPass;
+            const uint64_t nt = 1ULL << (n[i] - p.t), per = tiles_per_item(p.t);
+            uint32_t cnt = 0;
+            for (uint64_t t0 = 0; t0 < nt; t0 += per, ++cnt) {
+                PersistItem w = item(kind, i);
+                w.amp_off = off[i];
+                w.pass = (uint32_t)(first_pass[i] + r);
+                w.lo = (uint32_t)t0;
+                w.hi = (uint32_t)std::min<uint64_t>(nt, t0 + per);
+                w.need = before[i];
+                W->items.push_back(w);
+            }
+            before[i] += cnt;
+        }
+    if (stats)
+        for (int i : idx) {
+            const uint64_t N = 1ULL << n[i];
+            const uint32_t first = (uint32_t)W->nslots;
+            for (uint64_t a = 0; a < N; a += kWorkChunk) {
+                PersistItem w = item(kPersistStats, i);
+                w.amp_off = off[i] + a;
+                w.lo = (uint32_t)std::min<uint64_t>(kWorkChunk, N - a);
+                w.pass = (uint32_t)W->nslots++;
+                w.hi = first;
+                w.nslots = nstat[i];
+                w.f0 = (float)std::ldexp(1.0, n[i]);
+                w.need = ninit[i] + npass[i];
+                W->items.push_back(w);
+            }
+        }
+}
+
 PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
 {
     PlanParams pp;
@@ -855,7 +950,10 @@ PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o)
     int tile = dt == QS_C128 ? 12 : 13;
     if (o && o->tile_log2 > 0) tile = o->tile_log2;
     pp.t = std::min(tile, n);
-    pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t);
+    // the always-resident low qubits leave at least one tile bit free when
+    // the tile is smaller than the state (else no pass could bring in
+    // another qubit); a 16-byte load still takes consecutive amplitudes
+    pp.c = std::min(dt == QS_C128 ? 4 : 5, pp.t < n ? pp.t - 1 : pp.t);
     pp.k = kTcBits;
     pp.tc_ok = pp.mode == QS_MODE_FUSED_TC && dt == QS_C64 && pp.t == 13 ? 1 : 0;
     pp.precision = (o && o->precision != QS_PREC_DEFAULT) ? o->precision : QS_PREC_FP16X3;

@@ -206,6 +206,62 @@ double tf32_bits_to_f64(uint32_t w);
 PlanParams default_plan_params(int n, qs_dtype dt, const qs_opts *o);
 double plan_bytes(const Plan &p, qs_dtype dt);
 
+// Persistent ensemble kernel: one launch runs a batch's whole work list
+// from a device queue.  Items are taken in list order by an atomic head;
+// item j of instance i waits (bounded) until done[i] >= need, runs, then
+// increments done[i] (release).  Every item's dependencies precede it in
+// the list, so the earliest unfinished item can always run.
+enum PersistKind : uint32_t {
+    kPersistInit = 0,      // write the initial amplitudes of one chunk
+    kPersistPass = 1,      // fused tile pass, Clifford+T interpreter
+    kPersistPassFull = 2,  // fused tile pass, full interpreter
+    kPersistStats = 3      // statistics partials of one chunk
+};
+struct PersistItem {
+    uint64_t amp_off;      // pass: the instance's state; init / stats: the chunk
+    uint32_t kind;         // PersistKind
+    uint32_t inst;         // instance (its completion counter)
+    uint32_t need;         // completed items of the instance this one waits for
+    uint32_t total;        // items of the instance (the last statistics item sums)
+    uint32_t pass;         // pass: index into the pass array; stats: partial slot
+    uint32_t lo, hi;       // pass: tile range [lo, hi); init / stats: lo = amplitudes
+                           // of the chunk; stats: hi = the instance's first slot
+    uint32_t nslots;       // stats: the instance's partial slots
+    float f0, f1;          // init: fill value, first amplitude; stats: f0 = N
+};
+struct PersistCtl {
+    uint32_t next;         // queue head
+    uint32_t abort;        // a wait ran out: the remaining items drain without work
+    uint32_t err;          // 1 when a wait ran out
+    uint32_t pad;
+};
+
+// Work list of the persistent ensemble engine for the instances `idx` of a
+// batch (instance i: n[i] qubits at element offset off[i]; plans[i] its
+// plan, empty when its list is only the Hadamard layer; full[i][r] whether
+// pass r needs the full interpreter; hl[i] nonzero when the circuit opens
+// with a Hadamard layer, so the initial state is uniform).  Order: every
+// instance's initial-state chunks (kWorkChunk amplitudes), then the passes
+// round-major (pass r of every instance, larger instances first, before
+// pass r + 1 of any; items of kWorkChunk amplitudes = 2^(16 - t) tiles),
+// then, with `stats`, the statistics chunks (kWorkChunk amplitudes; slot
+// order = list order).  Item need = the number of the instance's items in
+// all earlier levels (initial chunks; pass 0; pass 1; ...; statistics), so
+// done[i] >= need holds exactly when those levels are complete, and every
+// one of them precedes the item in the list.
+constexpr uint64_t kWorkChunk = 1ULL << 16;
+struct Work {
+    std::vector<DevPass> passes;
+    std::vector<DevPhase> phases;
+    std::vector<DevOp> ops;
+    std::vector<PersistItem> items;
+    double bytes = 0;                // algorithmic bytes of the passes
+    int nslots = 0;                  // statistics partial slots
+};
+void build_work(const std::vector<int> &n, const std::vector<uint64_t> &off, const std::vector<Plan> &plans,
+                const std::vector<std::vector<char>> &full, const std::vector<int> &idx,
+                const std::vector<size_t> &hl, bool stats, Work *W);
+
 // ---------------------------------------------------------------------------
 // State handle
 // ---------------------------------------------------------------------------
@@ -344,6 +400,18 @@ qs_status launch_batch_round(cudaStream_t st, int num_sms, void *amps, const voi
 bool plan_pass_needs_full(const Plan &plan, int pass);
 size_t batch_item_bytes();
 qs_status batch_kernel_setup();
+
+constexpr uint64_t kPersistWaitNs = 2000000000ull;   // per dependency wait
+// Launches the persistent kernel over nitems items (device array) with
+// counters done[count instances] and ctl zeroed beforehand; statistics
+// partials go to part[slot * kStatSums], per-instance sums to
+// sums[inst * kStatSums].  any_full: some item is kPersistPassFull (the
+// variant with the full interpreter); grid = resident CTAs (occupancy API).
+qs_status launch_batch_persistent(cudaStream_t st, int num_sms, void *amps, const PersistItem *items, int nitems,
+                                  const DevPass *passes, const DevPhase *phases, const DevOp *ops,
+                                  uint32_t *done, PersistCtl *ctl, double *part, double *sums, bool any_full);
+// Resident CTAs per SM of the persistent kernel (after batch_kernel_setup).
+int batch_persistent_ctas_per_sm(bool any_full);
 void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, uint32_t te);
 // Batched sampler over instances laid out at element offsets off_h[i]
 // (2^n_h[i] complex64 each): k samples per instance into host_out[i k + j].

@@ -24,11 +24,10 @@
 #include <vector>
 
 #include "qs_device.cuh"
+#include "qs_stats_device.cuh"
 
 namespace qs {
 
-constexpr int kStatThreads = 256;
-constexpr int kStatAcc = 12;   // sum y, sum y ln y, sum ln y, sum y^k (k=2..10)
 constexpr int kChunk = 256;    // sampler chunk (amplitudes)
 
 // ---------------------------------------------------------------------------
@@ -115,50 +114,6 @@ qs_status launch_probabilities(const qs_state *s, void *out, int fp64, uint64_t 
     }
     QS_LAUNCH_CHECK();
     return QS_OK;
-}
-
-// ---------------------------------------------------------------------------
-// block reduction helpers (fixed order)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int K>
-__device__ __forceinline__ void block_sum_store(double (&acc)[K], double *dst)
-{
-    __shared__ double red[kStatThreads / 32][K];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double v = warp_sum(acc[k]);
-        if (lane == 0) red[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        double s = 0;
-        for (int w = 0; w < kStatThreads / 32; ++w) s += red[w][threadIdx.x];
-        dst[threadIdx.x] = s;
-    }
-}
-
-// Accumulates one element's contributions.  y = N p.
-template <typename T>
-__device__ __forceinline__ void stat_terms(T y, T (&c)[kStatAcc])
-{
-    T ly = (sizeof(T) == 4) ? (T)__logf((float)y) : (T)log((double)y);
-    c[0] += y;
-    c[1] += (y > (T)0) ? y * ly : (T)0;
-    c[2] += ly;
-    T yk = y;
-#pragma unroll
-    for (int k = 2; k <= 10; ++k) {
-        yk *= y;
-        c[k + 1] += yk;
-    }
 }
 
 // The same for two probabilities already formed in FP32 (the second one
@@ -295,40 +250,7 @@ k_batch_stats(const float2 *__restrict__ amps, const uint64_t *__restrict__ item
               double *__restrict__ part)
 {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const float2 *a = amps + item_off[it];
-        const uint64_t cnt = item_cnt[it];
-        const float scaleN = item_scale[it];
-        double acc[kStatAcc];
-#pragma unroll
-        for (int k = 0; k < kStatAcc; ++k) acc[k] = 0;
-        for (uint64_t i0 = threadIdx.x; i0 < cnt; i0 += (uint64_t)blockDim.x * 64) {
-            float c[kStatAcc];
-#pragma unroll
-            for (int k = 0; k < kStatAcc; ++k) c[k] = 0.f;
-            double big[kStatAcc];
-            bool any_big = false;
-            for (uint64_t i = i0, j = 0; j < 64 && i < cnt; ++j, i += blockDim.x) {
-                const float2 v = a[i];
-                const float y = (v.x * v.x + v.y * v.y) * scaleN;
-                if (y > 4096.f) {
-                    if (!any_big) {
-#pragma unroll
-                        for (int k = 0; k < kStatAcc; ++k) big[k] = 0;
-                        any_big = true;
-                    }
-                    stat_terms<double>(((double)v.x * v.x + (double)v.y * v.y) * (double)scaleN, big);
-                } else {
-                    stat_terms<float>(y, c);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kStatAcc; ++k) acc[k] += (double)c[k];
-            if (any_big) {
-#pragma unroll
-                for (int k = 0; k < kStatAcc; ++k) acc[k] += big[k];
-            }
-        }
-        block_sum_store<kStatAcc>(acc, part + (size_t)it * kStatAcc);
+        batch_stats_chunk(amps + item_off[it], item_cnt[it], item_scale[it], part + (size_t)it * kStatAcc);
         __syncthreads();
     }
 }

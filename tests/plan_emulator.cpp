@@ -7,8 +7,11 @@
 // factors applied at the end of each pass.  Comparing its result with the
 // oracle checks the planner (dependency order, register mapping, masks,
 // scales) without a GPU.
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "../paper_1608_00263_gb300/csrc/qs_internal.h"
@@ -78,16 +81,15 @@ extern "C" int emulate_plan(int n, const qs_gate *g, size_t ng, int t, int r, in
     return emulate_plan_mode(n, g, ng, t, r, c, QS_MODE_FUSED, psi_interleaved, passes_out, nullptr);
 }
 
-// Executes a built plan on a double-precision state (the semantics the
-// fused kernels give each op).
-static int emulate_built_plan(const Plan &plan, double *psi_interleaved, int *passes_out,
-                              int *tc_phases_out = nullptr)
+// Tiles [lo, hi) of pass P of a plan (phase and op indexes into `plan`)
+// on a double-precision state, with the semantics the fused kernels give
+// each op.
+static void emulate_tiles(const Plan &plan, const DevPass &P, uint64_t lo, uint64_t hi, cd *psi)
 {
-    cd *psi = reinterpret_cast<cd *>(psi_interleaved);
-    for (const DevPass &P : plan.passes) {
+    {
         const int T = P.t, ngl = P.n - T;
         std::vector<cd> tile(size_t(1) << T);
-        for (uint64_t tau = 0; tau < (1ULL << ngl); ++tau) {
+        for (uint64_t tau = lo; tau < hi; ++tau) {
             uint64_t base = 0;
             for (int i = 0; i < ngl; ++i) base |= ((tau >> i) & 1ULL) << P.G[i];
             auto addr = [&](uint64_t e) {
@@ -139,6 +141,14 @@ static int emulate_built_plan(const Plan &plan, double *psi_interleaved, int *pa
             for (uint64_t e = 0; e < tile.size(); ++e) psi[addr(e)] = tile[e] * gs;
         }
     }
+}
+
+// Executes a built plan on a double-precision state.
+static int emulate_built_plan(const Plan &plan, double *psi_interleaved, int *passes_out,
+                              int *tc_phases_out = nullptr)
+{
+    cd *psi = reinterpret_cast<cd *>(psi_interleaved);
+    for (const DevPass &P : plan.passes) emulate_tiles(plan, P, 0, 1ULL << (P.n - P.t), psi);
     if (passes_out) *passes_out = (int)plan.passes.size();
     if (tc_phases_out) {
         int k = 0;
@@ -281,4 +291,205 @@ extern "C" int emulate_plan_look(int n, const qs_gate *g, size_t ng, int t, int 
     Plan plan;
     if (build_plan(pp, g, ng, &plan) != QS_OK) return -1;
     return emulate_built_plan(plan, psi_interleaved, passes_out);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent ensemble engine: the library's work list (build_work) run on
+// double-precision states under a randomized schedule of `workers`
+// concurrent workers that follows the device protocol: a worker takes the
+// next item from the queue, waits until done[inst] >= need, runs it and
+// increments done[inst]; the last statistics item of an instance to finish
+// sums the instance's partials in slot order.  The list is checked first.
+// Returns 0, or the failed check: -1 planning, -2 item bounds, -3 coverage,
+// -4 level structure, -5 deadlock, -6 totals.  corrupt = 1 / 2 lowers /
+// raises the need of the list's last pass item by one before the checks (a
+// planted mistake the level check must catch).
+// ---------------------------------------------------------------------------
+static void work_stats_chunk(const cd *a, uint64_t cnt, double N, double *c)
+{
+    for (int k = 0; k < 12; ++k) c[k] = 0;
+    for (uint64_t i = 0; i < cnt; ++i) {
+        const double y = std::norm(a[i]) * N;
+        const double ly = std::log(y);
+        c[0] += y;
+        c[1] += y > 0 ? y * ly : 0.0;
+        c[2] += ly;
+        double yk = y;
+        for (int k = 2; k <= 10; ++k) {
+            yk *= y;
+            c[k + 1] += yk;
+        }
+    }
+}
+
+static bool covers_once(std::vector<std::pair<uint64_t, uint64_t>> r, uint64_t end)
+{
+    std::sort(r.begin(), r.end());
+    uint64_t at = 0;
+    for (auto &x : r) {
+        if (x.first != at || x.second <= x.first) return false;
+        at = x.second;
+    }
+    return at == end;
+}
+
+extern "C" int emulate_work(int count, const int *nq, const qs_gate *gates, const uint64_t *offsets, int workers,
+                            uint64_t seed, int corrupt, double *psi_out, double *sums_out, int *nitems_out)
+{
+    std::vector<int> n(nq, nq + count), idx(count);
+    std::vector<uint64_t> off(count);
+    std::vector<size_t> hl(count);
+    std::vector<Plan> plans(count);
+    std::vector<std::vector<char>> full(count);
+    uint64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        idx[i] = i;
+        off[i] = total;
+        total += 1ULL << n[i];
+        const size_t ng = (size_t)(offsets[i + 1] - offsets[i]);
+        hl[i] = leading_h_layer(gates + offsets[i], ng, n[i]);
+        if (ng > hl[i]) {
+            qs_opts o{};
+            o.mode = QS_MODE_FUSED;
+            if (build_plan(default_plan_params(n[i], QS_C64, &o), gates + offsets[i] + hl[i], ng - hl[i], &plans[i]))
+                return -1;
+        }
+        full[i].assign(plans[i].passes.size(), 0);
+    }
+    Work W;
+    build_work(n, off, plans, full, idx, hl, true, &W);
+    if (corrupt)
+        for (size_t j = W.items.size(); j-- > 0;)
+            if (W.items[j].kind == kPersistPass && W.items[j].need > 0) {
+                W.items[j].need += corrupt == 1 ? -1 : 1;
+                break;
+            }
+    const std::vector<PersistItem> &it = W.items;
+    if (nitems_out) *nitems_out = (int)it.size();
+    Plan view;
+    view.passes = W.passes;
+    view.phases = W.phases;
+    view.ops = W.ops;
+    // bounds
+    std::vector<int> first_pass(count, 0);
+    for (int i = 0, acc = 0; i < count; ++i) {
+        first_pass[i] = acc;
+        acc += (int)plans[i].passes.size();
+    }
+    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> init_r(count), stat_r(count);
+    std::vector<std::vector<std::vector<std::pair<uint64_t, uint64_t>>>> pass_r(count);
+    for (int i = 0; i < count; ++i) pass_r[i].resize(plans[i].passes.size());
+    std::vector<uint32_t> nitem(count, 0);
+    for (const PersistItem &w : it) {
+        if (w.inst >= (uint32_t)count || w.kind > kPersistStats) return -2;
+        const int i = (int)w.inst;
+        const uint64_t N = 1ULL << n[i];
+        ++nitem[i];
+        if (w.kind == kPersistInit || w.kind == kPersistStats) {
+            if (w.amp_off < off[i] || w.lo == 0 || w.amp_off + w.lo > off[i] + N) return -2;
+            (w.kind == kPersistInit ? init_r : stat_r)[i].push_back({w.amp_off - off[i], w.amp_off - off[i] + w.lo});
+            if (w.kind == kPersistStats &&
+                (w.pass >= (uint32_t)W.nslots || w.hi + w.nslots > (uint32_t)W.nslots || w.pass < w.hi ||
+                 w.pass >= w.hi + w.nslots))
+                return -2;
+        } else {
+            const int r = (int)w.pass - first_pass[i];
+            if (w.amp_off != off[i] || r < 0 || r >= (int)plans[i].passes.size()) return -2;
+            const DevPass &P = W.passes[w.pass];
+            if (P.n != n[i] || w.lo >= w.hi || w.hi > (1ULL << (n[i] - P.t))) return -2;
+            pass_r[i][r].push_back({w.lo, w.hi});
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        const uint64_t N = 1ULL << n[i];
+        if (!covers_once(init_r[i], N) || !covers_once(stat_r[i], N)) return -3;
+        for (size_t r = 0; r < plans[i].passes.size(); ++r)
+            if (!covers_once(pass_r[i][r], 1ULL << (n[i] - plans[i].passes[r].t))) return -3;
+    }
+    // dependencies: an initial chunk waits for nothing, an item of pass r
+    // for every initial chunk and every item of passes 0..r-1, a statistics
+    // chunk for every pass item
+    std::vector<std::vector<uint32_t>> level_start(count);
+    for (int i = 0; i < count; ++i) {
+        uint32_t acc = (uint32_t)init_r[i].size();
+        level_start[i].push_back(acc);
+        for (auto &pr : pass_r[i]) {
+            acc += (uint32_t)pr.size();
+            level_start[i].push_back(acc);
+        }
+    }
+    for (const PersistItem &w : it) {
+        const int i = (int)w.inst;
+        const uint32_t want = w.kind == kPersistInit    ? 0u
+                              : w.kind == kPersistStats ? level_start[i].back()
+                                                        : level_start[i][w.pass - first_pass[i]];
+        if (w.need != want) return -4;
+    }
+    // level structure: need = the number of the instance's items with a
+    // smaller need, all of which come earlier in the list
+    for (int i = 0; i < count; ++i) {
+        std::vector<std::pair<uint32_t, size_t>> lv;      // (need, list position)
+        for (size_t j = 0; j < it.size(); ++j)
+            if (it[j].inst == (uint32_t)i) {
+                if (it[j].total != nitem[i]) return -6;
+                lv.push_back({it[j].need, j});
+            }
+        for (auto &x : lv) {
+            uint32_t smaller = 0;
+            size_t last = 0;
+            bool any = false;
+            for (auto &y : lv)
+                if (y.first < x.first) {
+                    ++smaller;
+                    last = std::max(last, y.second);
+                    any = true;
+                }
+            if (smaller != x.first || (any && last > x.second)) return -4;
+        }
+    }
+    // randomized schedule
+    cd *psi = reinterpret_cast<cd *>(psi_out);
+    std::vector<double> part((size_t)std::max(1, W.nslots) * 12, 0.0);
+    std::vector<uint32_t> done(count, 0);
+    uint64_t z = seed;
+    auto rnd = [&]() {
+        z += 0x9E3779B97F4A7C15ULL;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+        return x ^ (x >> 31);
+    };
+    size_t head = 0;
+    std::vector<size_t> inflight;
+    while (head < it.size() || !inflight.empty()) {
+        std::vector<size_t> ready;
+        for (size_t k = 0; k < inflight.size(); ++k)
+            if (done[it[inflight[k]].inst] >= it[inflight[k]].need) ready.push_back(k);
+        const bool can_take = head < it.size() && (int)inflight.size() < workers;
+        if (!can_take && ready.empty()) return -5;
+        if (can_take && (ready.empty() || (rnd() & 1))) {
+            inflight.push_back(head++);
+            continue;
+        }
+        const size_t k = ready[rnd() % ready.size()];
+        const PersistItem w = it[inflight[k]];
+        inflight.erase(inflight.begin() + (long)k);
+        if (w.kind == kPersistInit) {
+            for (uint32_t e = 0; e < w.lo; ++e) psi[w.amp_off + e] = cd(w.f0, 0.0);
+            psi[w.amp_off] = cd(w.f1, 0.0);
+        } else if (w.kind == kPersistStats) {
+            work_stats_chunk(psi + w.amp_off, w.lo, (double)w.f0, &part[(size_t)w.pass * 12]);
+        } else {
+            emulate_tiles(view, W.passes[w.pass], w.lo, w.hi, psi + w.amp_off);
+        }
+        if (++done[w.inst] == w.total && w.kind == kPersistStats)
+            for (int c = 0; c < 12; ++c) {
+                double s = 0;
+                for (uint32_t j = 0; j < w.nslots; ++j) s += part[(size_t)(w.hi + j) * 12 + c];
+                sums_out[(size_t)w.inst * 12 + c] = s;
+            }
+    }
+    for (int i = 0; i < count; ++i)
+        if (done[i] != nitem[i]) return -6;
+    return 0;
 }

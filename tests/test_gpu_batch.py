@@ -8,6 +8,7 @@ import pytest
 
 import oracle as O
 import paper_1608_00263_gb300 as qs
+from paper_1608_00263_gb300 import _native as N
 from paper_1608_00263_gb300 import build as qs_build
 
 from seeded_inputs import ensemble_instance
@@ -152,6 +153,77 @@ def test_autotuned_ensemble_matches_oracle_and_reports_its_choices():
         tiles, _ = qs.qs_batch_plan_info(b)
         assert np.all(tiles == 10)
         for i, (n, depth, g) in enumerate(inst[:5]):
+            ref = O.simulate(n, g)
+            err = np.linalg.norm(device_state(b, i, n).astype(complex) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (i, n, err)
+    finally:
+        qs.qs_batch_destroy(b)
+
+
+def _mixed_instances():
+    """5..17 qubits, shallow and deep: with a fixed tile size t every pass
+    runs in thread groups of 2^(t-5) threads (t = 5: one thread, t = 9: half
+    a warp, t = 12: four warps)."""
+    out = []
+    for k, (n, depth) in enumerate([(17, 12), (5, 8), (12, 20), (9, 16), (17, 3), (14, 25), (6, 10),
+                                    (13, 14), (11, 18), (16, 9)]):
+        rows = 1 if n < 4 else (2 if n < 9 else 4)
+        cols = -(-n // rows)
+        dead = np.zeros(rows * cols, dtype=np.uint8)
+        dead[n:] = 1
+        out.append((n, depth, qs.qs_circuit_generate(rows, cols, depth, 100 + k, dead)))
+    return out
+
+
+@pytest.mark.parametrize("tile", [0, 5, 7, 9, 10, 12])
+def test_persistent_and_lockstep_engines_agree_with_each_other_and_the_oracle(tile):
+    """The persistent engine (one launch, grouped passes, dependency waits)
+    against the lockstep rounds on the same plans: identical states and
+    statistics (the same per-tile arithmetic and the same partials summed in
+    the same order), and both against the FP64 oracle."""
+    inst = _mixed_instances()
+    if tile:
+        inst = [x for x in inst if x[0] >= tile]
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        if tile:
+            qs.qs_batch_set_options(b, tile_log2=tile)
+        gl = [x[2] for x in inst]
+        res = {}
+        for engine in (qs.QS_BATCH_ROUNDS, qs.QS_BATCH_PERSISTENT):
+            qs.qs_batch_set_engine(b, engine)
+            st = qs.qs_batch_run(b, gl, kmax=6)
+            st2 = qs.qs_batch_run(b, gl, kmax=6)               # graph replay
+            assert np.array_equal(st, st2)
+            res[engine] = (st, [device_state(b, i, x[0]) for i, x in enumerate(inst)])
+        st_r, psi_r = res[qs.QS_BATCH_ROUNDS]
+        st_p, psi_p = res[qs.QS_BATCH_PERSISTENT]
+        assert np.array_equal(st_r, st_p)
+        for i, (n, depth, g) in enumerate(inst):
+            assert np.array_equal(psi_r[i], psi_p[i]), (i, n, depth)
+            ref = O.simulate(n, g)
+            err = np.linalg.norm(psi_p[i].astype(complex) - ref) / np.linalg.norm(ref)
+            assert err < 1e-5, (i, n, depth, err)
+            p = O.probabilities(ref)
+            assert st_p[i, 1] == pytest.approx(O.entropy(p), rel=1e-6)
+            assert np.allclose(st_p[i, 3:], O.moments(p, 6), rtol=1e-5)
+    finally:
+        qs.qs_batch_destroy(b)
+
+
+def test_engine_choice_is_validated_and_autotuned_per_engine():
+    inst = _mixed_instances()[:4]
+    b = qs.qs_batch_create([x[0] for x in inst])
+    try:
+        with pytest.raises(qs.QSError) as e:
+            qs.qs_batch_set_engine(b, 2)
+        assert e.value.status == N.QS_ERR_INVALID_ARG
+        qs.qs_batch_set_engine(b, qs.QS_BATCH_PERSISTENT)
+        qs.qs_batch_set_options(b, autotune=1)
+        qs.qs_batch_run(b, [x[2] for x in inst], kmax=2)
+        tiles, _ = qs.qs_batch_plan_info(b)
+        for i, (n, depth, g) in enumerate(inst):
+            assert min(9, n) <= tiles[i] <= min(13, n)
             ref = O.simulate(n, g)
             err = np.linalg.norm(device_state(b, i, n).astype(complex) - ref) / np.linalg.norm(ref)
             assert err < 1e-5, (i, n, err)

@@ -156,6 +156,10 @@ def emulator():
     lib.emulate_plan_look.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]
+    lib.emulate_work.restype = ctypes.c_int
+    lib.emulate_work.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_int)]
     lib.emulate_plan.restype = ctypes.c_int
     lib.emulate_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -187,7 +191,7 @@ def random_gates(rng, n, count):
 
 
 @pytest.mark.parametrize("n,t,r,c", [(10, 7, 5, 5), (12, 8, 3, 2), (11, 11, 5, 5),
-                                     (13, 9, 4, 4), (9, 6, 5, 0), (14, 10, 5, 5)])
+                                     (13, 9, 4, 4), (9, 6, 5, 0), (14, 10, 5, 5), (12, 5, 5, 4)])
 def test_plan_semantics_random_gates(emulator, n, t, r, c):
     rng = np.random.default_rng(n * 100 + t)
     g = random_gates(rng, n, 300)
@@ -369,3 +373,98 @@ def test_tc_plan_semantics_every_precision(emulator, prec, bound):
     err = np.linalg.norm(psi - ref) / np.linalg.norm(ref)
     assert tcp.value > 0
     assert err < bound, err
+
+
+def _work_batch():
+    """Mixed instances for the persistent-engine work list: 5..17 qubits
+    (17: two 2^16-amplitude chunks and two items per pass), one list that is
+    only the Hadamard layer, one without the leading layer (|0...0> start),
+    one depth-3 circuit among deep ones."""
+    def circ(n, depth, seed):
+        rows = 1 if n < 4 else (2 if n < 9 else 4)
+        cols = -(-n // rows)
+        dead = np.zeros(rows * cols, dtype=np.uint8)
+        dead[n:] = 1
+        return O.generate_circuit(rows, cols, depth, seed, dead)
+    spec = [(17, 12, 1), (5, 8, 2), (12, 20, 3), (9, 16, 4), (17, 3, 5), (14, 25, 6), (6, 10, 7), (13, 14, 8)]
+    ns, gl = [], []
+    for n, depth, seed in spec:
+        ns.append(n)
+        gl.append(circ(n, depth, seed))
+    ns.append(11)
+    gl.append(circ(11, 9, 9)[:11])            # the Hadamard layer only
+    ns.append(10)
+    gl.append(circ(10, 12, 10)[1:])           # no leading layer: starts in |0...0>
+    return ns, gl
+
+
+def _emulate_work(lib, ns, gl, workers, seed, corrupt=0):
+    g = np.ascontiguousarray(np.concatenate(gl), dtype=qs.GATE_DTYPE)
+    offs = np.zeros(len(gl) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([x.size for x in gl])
+    nq = np.array(ns, dtype=np.int32)
+    psi = np.zeros(sum(1 << n for n in ns), dtype=np.complex128)
+    sums = np.full((len(ns), 12), np.nan)
+    cnt = ctypes.c_int(0)
+    rc = lib.emulate_work(len(ns), nq.ctypes.data, g.ctypes.data, offs.ctypes.data, workers, seed, corrupt,
+                          psi.ctypes.data, sums.ctypes.data, ctypes.byref(cnt))
+    return rc, psi, sums, cnt.value
+
+
+@pytest.mark.parametrize("workers,seed", [(1, 0), (3, 11), (16, 12), (304, 13)])
+def test_persistent_work_list_matches_oracle_in_any_dependency_order(emulator, workers, seed):
+    """The persistent ensemble engine's work list (the library's own
+    build_work): every item in bounds, every state and pass covered exactly
+    once, each item's need equal to its instance's items in earlier levels
+    (all earlier in the list), and, run under a randomized schedule of
+    concurrent workers that follows the device protocol (take in list
+    order, wait for done >= need, run, count), states equal to the oracle's
+    and statistics sums equal to the oracle's probabilities' sums."""
+    ns, gl = _work_batch()
+    rc, psi, sums, nitems = _emulate_work(emulator, ns, gl, workers, seed)
+    assert rc == 0
+    at = 0
+    for i, (n, g) in enumerate(zip(ns, gl)):
+        ref = O.simulate(n, g)
+        if g.size >= n and np.all(g["kind"][:n] == qs.QS_H):
+            # the uniform start 2^(-n/2) is written as the kernel writes it,
+            # rounded to FP32: the whole state carries that factor
+            v = 2.0 ** (-n / 2)
+            ref = ref * (float(np.float32(v)) / v)
+        got = psi[at:at + (1 << n)]
+        at += 1 << n
+        assert np.max(np.abs(got - ref)) < 1e-12, i
+        N = float(1 << n)
+        y = O.probabilities(ref) * N
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ly = np.log(y)
+            expect = [y.sum(), np.sum(np.where(y > 0, y * ly, 0.0)), ly.sum()] + \
+                     [np.sum(y ** k) for k in range(2, 11)]
+        for k in range(12):
+            if k == 2 and y.min() < 1e-8:
+                continue      # sum ln y over amplitudes at rounding level: ill-conditioned
+            if np.isfinite(expect[k]):
+                assert sums[i, k] == pytest.approx(expect[k], rel=1e-9, abs=1e-9), (i, k)
+            else:
+                assert sums[i, k] == expect[k], (i, k)
+    assert nitems > 0
+
+
+@pytest.mark.parametrize("corrupt", [1, 2])
+def test_persistent_work_list_check_catches_a_wrong_need(emulator, corrupt):
+    """A planted off-by-one in one item's need (lowered: the item could run
+    before its pass's inputs are complete; raised: it waits for an item of
+    its own level) fails the level check."""
+    ns, gl = _work_batch()
+    rc, _, _, _ = _emulate_work(emulator, ns, gl, 4, 0, corrupt)
+    assert rc == -4
+
+
+@pytest.mark.parametrize("dtype,t", [(qs.QS_C64, 5), (qs.QS_C64, 6), (qs.QS_C128, 4), (qs.QS_C128, 5)])
+def test_smallest_tiles_plan(dtype, t):
+    """A tile of as many qubits as the register set still leaves a free
+    tile bit beside the always-resident low qubits, so the planner makes
+    progress (the plan's semantics at t = 5, c = 4 are emulated above)."""
+    g = O.generate_circuit(3, 4, 12, 4)
+    st = qs.qs_plan_circuit(12, dtype, g, tile_log2=t)
+    assert st["tile_log2"] == t and st["passes"] >= 2 and st["gates"] == g.size
