@@ -458,7 +458,7 @@ enum {
                                   work items from a device queue: every
                                   instance's initial-state chunks (2^16
                                   amplitudes), then its fused passes in
-                                  items of 2^16 amplitudes, round-major
+                                  items of 2^18 amplitudes, round-major
                                   (pass r of every instance before pass
                                   r + 1 of any; larger instances first),
                                   then its statistics chunks; an item waits

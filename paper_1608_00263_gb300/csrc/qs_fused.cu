@@ -975,8 +975,8 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     // closing barrier; a group past the end of the range (inactive) only
     // takes part in its barriers
     for (uint64_t tau0 = t_begin; tau0 < t_end;
-         tau0 += (uint64_t)ngr,
-                  base = GROUPED ? deposit(tau0 + (uint64_t)gi, S.P.G, ng) : (((base | ~gmask) + 1) & gmask)) {
+         tau0 += (uint64_t)ngr, base = (GROUPED && ngr > 1) ? deposit(tau0 + (uint64_t)gi, S.P.G, ng)
+                                                            : (((base | ~gmask) + 1) & gmask)) {
         const uint64_t tau = tau0 + (uint64_t)gi;
         bool active = !GROUPED || tau < t_end;
         if (TCP && TS.abort) break;
@@ -1002,7 +1002,8 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         // warm L2 with the next tile: thread i prefetches run i (2^c
         // consecutive amplitudes, 256 bytes) while this tile is processed
         if (active && prefetch_runs && tau + (uint64_t)ngr < t_end) {
-            const uint64_t nb = GROUPED ? deposit(tau + (uint64_t)ngr, S.P.G, ng) : (((base | ~gmask) + 1) & gmask);
+            const uint64_t nb = (GROUPED && ngr > 1) ? deposit(tau + (uint64_t)ngr, S.P.G, ng)
+                                                     : (((base | ~gmask) + 1) & gmask);
             const V *p = amps + (nb | run_off);
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
         }
@@ -1097,8 +1098,9 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         }
         // ---- store the tile ----
         V *tdst = amps + (base | tid_off);
+        if (active)
 #pragma unroll
-        for (int it = 0; it < CPT && active; ++it) {
+        for (int it = 0; it < CPT; ++it) {
             const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
             V v[CE];
             *reinterpret_cast<float4 *>(v) = *reinterpret_cast<const float4 *>(gsm + sw);
@@ -1193,8 +1195,8 @@ k_batch_pass(typename V2T<R>::T *__restrict__ amps, const BatchItem *__restrict_
 }
 
 // Persistent ensemble kernel (see PersistItem): kThreadsMax threads per CTA
-// whatever the instances' tile sizes (passes run in the grouped form), two
-// CTAs per SM.  Thread 0 takes the next item from the queue head, waits for
+// whatever the instances' tile sizes (13-qubit tiles take the whole CTA,
+// smaller ones run in the grouped form), two CTAs per SM.  Thread 0 takes the next item from the queue head, waits for
 // the item's dependencies (acquire, bounded by kPersistWaitNs), the CTA
 // runs it, and thread 0 publishes its completion (release).  A wait that
 // runs out sets ctl->err and ctl->abort; from then on items are taken and
@@ -1238,8 +1240,14 @@ k_batch_persistent(float2 *amps, const PersistItem *__restrict__ items, int nite
                 for (uint32_t e = threadIdx.x; e < w.lo / 2; e += blockDim.x) a[e] = u;
                 if (threadIdx.x == 0) a[0] = make_float4(w.f1, 0.f, w.f0, 0.f);
             } else if (w.kind == kPersistPass) {
-                fused_pass_body<float, RB, 0, false, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g, w.lo,
-                                                           w.hi, nullptr, nullptr, S, TS, smem_raw);
+                // a tile of 2^(RB + 8) amplitudes takes the whole CTA: the
+                // plain body (CTA barriers); smaller tiles run grouped
+                if (passes[w.pass].t == RB + 8)
+                    fused_pass_body<float, RB, 0, false, false>(amps + w.amp_off, passes + w.pass, phases_g, ops_g,
+                                                                w.lo, w.hi, nullptr, nullptr, S, TS, smem_raw);
+                else
+                    fused_pass_body<float, RB, 0, false, true>(amps + w.amp_off, passes + w.pass, phases_g, ops_g,
+                                                               w.lo, w.hi, nullptr, nullptr, S, TS, smem_raw);
             } else if (w.kind == kPersistPassFull) {
                 // (the launch compiles the full interpreter in only when
                 // some item needs it)

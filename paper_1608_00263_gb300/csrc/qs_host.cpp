@@ -848,7 +848,10 @@ static void pack_block(const std::vector<Cplx> &U, int precision, std::vector<ui
 
 // Persistent ensemble work list (declared with its order and dependency
 // rules in qs_internal.h).
-static uint64_t tiles_per_item(int t) { return t >= 16 ? 1 : (1ULL << (16 - t)); }
+static uint64_t tiles_per_item(int t)
+{
+    return t >= kPassItemBits ? 1 : (1ULL << (kPassItemBits - t));
+}
 
 void build_work(const std::vector<int> &n, const std::vector<uint64_t> &off, const std::vector<Plan> &plans,
                 const std::vector<std::vector<char>> &full, const std::vector<int> &idx,

@@ -243,13 +243,15 @@ struct PersistCtl {
 // with a Hadamard layer, so the initial state is uniform).  Order: every
 // instance's initial-state chunks (kWorkChunk amplitudes), then the passes
 // round-major (pass r of every instance, larger instances first, before
-// pass r + 1 of any; items of kWorkChunk amplitudes = 2^(16 - t) tiles),
-// then, with `stats`, the statistics chunks (kWorkChunk amplitudes; slot
-// order = list order).  Item need = the number of the instance's items in
+// pass r + 1 of any; items of 2^kPassItemBits amplitudes = 2^(18 - t)
+// tiles, so a CTA restages a pass once per 32 tiles of 2^13), then, with
+// `stats`, the statistics chunks (kWorkChunk amplitudes, as the lockstep
+// engine's; slot order = list order).  Item need = the number of the instance's items in
 // all earlier levels (initial chunks; pass 0; pass 1; ...; statistics), so
 // done[i] >= need holds exactly when those levels are complete, and every
 // one of them precedes the item in the list.
 constexpr uint64_t kWorkChunk = 1ULL << 16;
+constexpr int kPassItemBits = 18;
 struct Work {
     std::vector<DevPass> passes;
     std::vector<DevPhase> phases;

@@ -161,11 +161,12 @@ def test_autotuned_ensemble_matches_oracle_and_reports_its_choices():
 
 
 def _mixed_instances():
-    """5..17 qubits, shallow and deep: with a fixed tile size t every pass
-    runs in thread groups of 2^(t-5) threads (t = 5: one thread, t = 9: half
-    a warp, t = 12: four warps)."""
+    """5..19 qubits, shallow and deep: with a fixed tile size t < 13 every
+    pass runs in thread groups of 2^(t-5) threads (t = 5: one thread, t = 9:
+    half a warp, t = 12: four warps); 13-qubit tiles take the whole CTA; 19
+    qubits give two 2^18-amplitude work items per pass."""
     out = []
-    for k, (n, depth) in enumerate([(17, 12), (5, 8), (12, 20), (9, 16), (17, 3), (14, 25), (6, 10),
+    for k, (n, depth) in enumerate([(19, 12), (5, 8), (12, 20), (9, 16), (17, 3), (14, 25), (6, 10),
                                     (13, 14), (11, 18), (16, 9)]):
         rows = 1 if n < 4 else (2 if n < 9 else 4)
         cols = -(-n // rows)

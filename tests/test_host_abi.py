@@ -376,17 +376,18 @@ def test_tc_plan_semantics_every_precision(emulator, prec, bound):
 
 
 def _work_batch():
-    """Mixed instances for the persistent-engine work list: 5..17 qubits
-    (17: two 2^16-amplitude chunks and two items per pass), one list that is
-    only the Hadamard layer, one without the leading layer (|0...0> start),
-    one depth-3 circuit among deep ones."""
+    """Mixed instances for the persistent-engine work list: 5..19 qubits
+    (17: two 2^16-amplitude initial and statistics chunks; 19: also two
+    2^18-amplitude items per pass), one list that is only the Hadamard
+    layer, one without the leading layer (|0...0> start), one depth-3
+    circuit among deep ones."""
     def circ(n, depth, seed):
         rows = 1 if n < 4 else (2 if n < 9 else 4)
         cols = -(-n // rows)
         dead = np.zeros(rows * cols, dtype=np.uint8)
         dead[n:] = 1
         return O.generate_circuit(rows, cols, depth, seed, dead)
-    spec = [(17, 12, 1), (5, 8, 2), (12, 20, 3), (9, 16, 4), (17, 3, 5), (14, 25, 6), (6, 10, 7), (13, 14, 8)]
+    spec = [(19, 10, 1), (5, 8, 2), (12, 20, 3), (9, 16, 4), (17, 3, 5), (14, 25, 6), (6, 10, 7), (13, 14, 8)]
     ns, gl = [], []
     for n, depth, seed in spec:
         ns.append(n)
