@@ -791,6 +791,18 @@ __device__ __forceinline__ void tc_phase(TcSmem &TS, int slot, int scale_exp, fl
     __syncthreads();
 }
 
+// complex64 slot <-> 64-bit word (re in the low half) for the PTX op loop
+__device__ __forceinline__ unsigned long long f2_bits(float2 v)
+{
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long b)
+{
+    return make_float2(__uint_as_float((uint32_t)b), __uint_as_float((uint32_t)(b >> 32)));
+}
+
+#include "qs_ct_asm.inc"
+
 // Barrier of the threads that work on one tile: the whole CTA, or in the
 // grouped form the tile's thread group (named barrier 1 + group for groups
 // of whole warps, a warp-lane barrier for smaller groups).
@@ -1039,6 +1051,17 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                 for (int o = ob; o < ub; ++o) {
                     const SOp<R> op = S.ops[o];
                     exec_op<RB, FULL>(op.code, a, idx_th, op.qmask, fr, fi, S.phase[op.aux]);
+                }
+            } else if constexpr (sizeof(R) == 4 && RB == 5) {
+                // complex64: the op loop in PTX with an indexed branch per op
+                // (the same arithmetic as exec_ct, see qs_ct_asm.inc)
+                if (ob < ub) {
+                    unsigned long long u[NS];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) u[s] = f2_bits(a[s]);
+                    CtAsm<GROUPED ? 1 : 0>::run(u, smem_addr(S.code8), smem_addr(S.ops) + 8u, ob, ub, idx_th);
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) a[s] = bits_f2(u[s]);
                 }
             } else {
                 // the next op's code is loaded while the current op runs
