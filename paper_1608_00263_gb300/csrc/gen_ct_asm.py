@@ -14,8 +14,10 @@ dense range (see exec_ct / ct_code in qs_fused.cu):
     C_Z  + j   (35..39)  sign on the slots with bit j set
 
 A C++ switch over these codes compiles to a tree of compares and branches
-(about ten branches per op); here the loop loads the code and takes one
-indexed branch (brx.idx) into the case.  Every case does exactly the
+(about ten branches per op); here every case ends with its own copy of the
+dispatch (threaded code): the next op's code, loaded while the case ran,
+picks the next case by one indexed branch (brx.idx), and the code after it
+is loaded in turn.  Every case does exactly the
 arithmetic of the C++ cases (the same operations in the same order, packed
 FP32x2 where both components see the same operation), so results are the
 same bit for bit.
@@ -110,8 +112,9 @@ def case_sign(mask, factor):
 
 def case_czo(j):
     # the selection outside the register set: (idx & qmask) == qmask, the
-    # op's qmask at byte 8 of its 16-byte staged record
-    return ["mad.lo.u32 qa, qcur, 16, %33;",
+    # op's qmask at byte 8 of its 16-byte staged record (op qo - 1: the
+    # dispatch has already advanced qo)
+    return ["mad.lo.u32 qa, qo, 16, qmb;",
             "ld.shared.u64 qm, [qa];",
             "and.b64 qt, %36, qm;",
             "setp.eq.u64 qp, qt, qm;",
@@ -135,6 +138,21 @@ def cases():
     return body
 
 
+def dispatch(L):
+    """Runs op qo (its code in qcn, loaded earlier): leaves when qo reaches
+    the end, loads op qo + 1's code (the staged codes run past the last op),
+    and branches to op qo's case; a code outside the table is clamped to the
+    extra entry, which only dispatches the next op (the staging never makes
+    one)."""
+    return ["setp.ge.s32 qp, qo, %35;",
+            "@qp bra.uni " + L("DONE") + ";",
+            "min.u32 qc, qcn, %d;" % NCODES,
+            "add.u32 qo, qo, 1;",
+            "add.u32 qa, %32, qo;",
+            "ld.shared.u8 qcn, [qa];",
+            "brx.idx.uni qc, " + L("TBL") + ";"]
+
+
 def asm_text(prefix):
     """PTX of the loop over ops [%34, %35): %0..%31 the slots (re in the low
     word, im in the high word), %32 the shared address of the byte codes,
@@ -143,29 +161,23 @@ def asm_text(prefix):
     L = lambda name: "%s_%s" % (prefix, name)
     lines = ["{",
              ".reg .pred qp;",
-             ".reg .u32 qo, qc, qa, qcur;",
+             ".reg .u32 qo, qc, qcn, qa, qmb;",
              ".reg .b64 qm, qt, qS, qM2, qM1, qP2;",
              ".reg .f32 xr, xi, yr, yi, tn, qsg;",
              "mov.b64 qM2, {0fC0000000, 0fC0000000};",
              "mov.b64 qM1, {%s, %s};" % (F_M1, F_M1),
              "mov.b64 qP2, {%s, %s};" % (F_2, F_2),
+             "sub.u32 qmb, %33, 16;",
              "mov.u32 qo, %34;",
-             L("LOOP") + ":",
-             "setp.ge.s32 qp, qo, %35;",
-             "@qp bra.uni " + L("DONE") + ";",
              "add.u32 qa, %32, qo;",
-             "ld.shared.u8 qc, [qa];",
-             "mov.u32 qcur, qo;",
-             "add.u32 qo, qo, 1;",
-             # a code outside the table is skipped (the staging never makes one)
-             "setp.ge.u32 qp, qc, %d;" % NCODES,
-             "@qp bra.uni " + L("LOOP") + ";",
-             L("TBL") + ": .branchtargets " + ", ".join(L("C%d" % c) for c in range(NCODES)) + ";",
-             "brx.idx.uni qc, " + L("TBL") + ";"]
+             "ld.shared.u8 qcn, [qa];",
+             L("TBL") + ": .branchtargets " + ", ".join([L("C%d" % c) for c in range(NCODES)] + [L("NEXT")]) + ";",
+             L("NEXT") + ":"]
+    lines += dispatch(L)
     for c, b in enumerate(cases()):
         lines.append(L("C%d" % c) + ":")
         lines += b
-        lines.append("bra.uni " + L("LOOP") + ";")
+        lines += dispatch(L)
     lines += [L("DONE") + ":", "}"]
     return lines
 

@@ -54,17 +54,18 @@ def _fma(a, b, c):
 
 class Machine:
     """Registers of one thread: %k (k < 32) are the slots as (re, im) FP32
-    pairs; %33 the byte address of op 0's qmask; %36 the index bits."""
+    pairs; the op runs as op 0 (qo = 1 after the dispatch, its qmask at
+    byte 8 of the op records); %36 the index bits."""
 
     def __init__(self, slots, idx, qmask):
         self.r = {"%%%d" % s: [f32(v.real), f32(v.imag)] for s, v in enumerate(slots)}
-        self.r["%33"] = 8
-        self.r["%36"] = idx
+        self.r["qo"] = 1
+        self.r["qmb"] = 8 - 16
         self.qmask = qmask
+        self.r["%36"] = idx
         self.r["qM2"] = [f32(-2), f32(-2)]
         self.r["qM1"] = [f32(-1), f32(-1)]
         self.r["qP2"] = [f32(2), f32(2)]
-        self.r["qcur"] = 0
 
     def val(self, tok):
         return _imm(tok) if tok.startswith("0f") else self.r[tok]
@@ -176,4 +177,8 @@ def test_case_table_covers_every_code_once():
     targets = [ln for ln in g.asm_text("P") if ".branchtargets" in ln]
     assert len(targets) == 1
     assert targets[0].split(".branchtargets")[1].strip(" ;").split(", ") == \
-        ["P_C%d" % c for c in range(g.NCODES)]
+        ["P_C%d" % c for c in range(g.NCODES)] + ["P_NEXT"]
+    # threaded dispatch: the entry and every case end in the same dispatch
+    d = g.dispatch(lambda name: "P_" + name)
+    assert text.count("\n".join(d)) == g.NCODES + 1
+    assert text.count("brx.idx.uni") == g.NCODES + 1
