@@ -976,12 +976,6 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     (void)lmask;
     uint64_t base = deposit(t_begin + (uint64_t)gi, S.P.G, ng);
     uint32_t tc_parity = 0;
-    // runs of consecutive amplitudes per tile = 2^(t - c); with c = RB for
-    // complex64 (5) and complex128 (4) there is one 256-byte run per thread
-    constexpr int kRunBits = (sizeof(V) == 8) ? 5 : 4;
-    const bool prefetch_runs = (t - kRunBits) >= 0 && (1 << (t - kRunBits)) == nthr &&
-                               S.P.L[kRunBits - 1] == kRunBits - 1;
-    const uint64_t run_off = prefetch_runs ? deposit((uint64_t)tid << kRunBits, S.P.L, t) : 0;
     // grouped form: every group runs the same number of iterations, so the
     // warps that hold several small groups stay converged up to the CTA's
     // closing barrier; a group past the end of the range (inactive) only
@@ -1011,14 +1005,6 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         tile_sync<GROUPED>(nthr, gi);
-        // warm L2 with the next tile: thread i prefetches run i (2^c
-        // consecutive amplitudes, 256 bytes) while this tile is processed
-        if (active && prefetch_runs && tau + (uint64_t)ngr < t_end) {
-            const uint64_t nb = (GROUPED && ngr > 1) ? deposit(tau + (uint64_t)ngr, S.P.G, ng)
-                                                     : (((base | ~gmask) + 1) & gmask);
-            const V *p = amps + (nb | run_off);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(p) : "memory");
-        }
 
         for (int ph = 0; ph < nph; ++ph) {
             if constexpr (TCP > 0) {
