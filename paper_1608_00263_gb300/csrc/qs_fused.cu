@@ -1312,13 +1312,17 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                     return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need 13-bit tiles");
                 if (!any_tc) QS_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s->stream));
                 any_tc = true;
+                // register phases of a Clifford+T pass run the byte-code op loop
+                const bool full = pass_needs_full(plan, hp);
                 decltype(&k_fused_pass<R, RB, 1, true>) kern;
                 switch (plan.precision) {
-                case QS_PREC_BF16X3: kern = k_fused_pass<R, RB, QS_PREC_BF16X3, true>; break;
-                case QS_PREC_BF16X6: kern = k_fused_pass<R, RB, QS_PREC_BF16X6, true>; break;
-                case QS_PREC_TF32X3: kern = k_fused_pass<R, RB, QS_PREC_TF32X3, true>; break;
-                case QS_PREC_TF32: kern = k_fused_pass<R, RB, QS_PREC_TF32, true>; break;
-                case QS_PREC_FP16X3: kern = k_fused_pass<R, RB, QS_PREC_FP16X3, true>; break;
+#define QS_TC_KERN(P) (full ? k_fused_pass<R, RB, P, true> : k_fused_pass<R, RB, P, false>)
+                case QS_PREC_BF16X3: kern = QS_TC_KERN(QS_PREC_BF16X3); break;
+                case QS_PREC_BF16X6: kern = QS_TC_KERN(QS_PREC_BF16X6); break;
+                case QS_PREC_TF32X3: kern = QS_TC_KERN(QS_PREC_TF32X3); break;
+                case QS_PREC_TF32: kern = QS_TC_KERN(QS_PREC_TF32); break;
+                case QS_PREC_FP16X3: kern = QS_TC_KERN(QS_PREC_FP16X3); break;
+#undef QS_TC_KERN
                 default: return set_error(QS_ERR_INVALID_ARG, "tensor-core precision %d", plan.precision);
                 }
                 const size_t smem = tc_dyn_smem(plan.precision);
