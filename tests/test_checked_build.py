@@ -103,3 +103,17 @@ def test_parity_small_cases_pass_in_the_checked_build():
                         "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider", "-k", sel],
                        env=env, capture_output=True, text=True, timeout=1200, cwd=ROOT)
     assert r.returncode == 0 and " passed" in r.stdout, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+@pytest.mark.gpu
+def test_batch_engines_pass_in_the_checked_build():
+    """The persistent ensemble engine (whole-CTA and grouped pass bodies for
+    tiles of 5 to 13 qubits, dependency waits) and the lockstep engine with
+    every device check armed: the same states and statistics as each other
+    and the oracle, and no check fires."""
+    env = dict(os.environ, QS_CHECKED="1", PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_gpu_batch.py"),
+                        "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider", "-k",
+                        "persistent_and_lockstep or initial_states"],
+                       env=env, capture_output=True, text=True, timeout=1200, cwd=ROOT)
+    assert r.returncode == 0 and " passed" in r.stdout, r.stdout[-3000:] + r.stderr[-2000:]
