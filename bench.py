@@ -157,17 +157,18 @@ class ClockSampler:
 
 
 def kernel_launches_per_step(passes):
-    # fused passes + uniform fill (the leading Hadamard layer on the reset
-    # state) + fused read-out (probabilities, statistics partials and chunk
-    # sums: 1) + statistics (final sum, read-back = 2) + sampler (3 scan
-    # kernels, read-back, search = 5) + cross entropy (kernel, final sum,
-    # 2 read-backs = 4)
-    return passes + 1 + 1 + 2 + 5 + 4
+    # fused passes (the first one generates the leading Hadamard layer's
+    # uniform state itself) + fused read-out (probabilities, statistics
+    # partials and chunk sums: 1) + statistics (final sum, read-back = 2) +
+    # sampler (3 scan kernels, read-back, search = 5) + cross entropy
+    # (kernel, final sum, 2 read-backs = 4)
+    return passes + 1 + 2 + 5 + 4
 
 
 def leading_h_layer(qs, g, n):
     """Length of a leading layer of H on every qubit (n, else 0): applied to
-    |0...0>, the library writes that layer as one uniform fill."""
+    |0...0>, the library generates that layer's uniform state in the first
+    fused pass (or writes it as one uniform fill)."""
     import numpy as np
     if len(g) < n or not np.all(g["kind"][:n] == qs.QS_H):
         return 0
@@ -204,13 +205,21 @@ class _CudaArray:
 
 
 def applied_plan(qs, n, g, md, prec=0):
-    """Launches and algorithmic bytes of applying g to the reset state: the
-    uniform fill (2^n complex64 written) and the plan of the remaining gates."""
+    """Launches and algorithmic bytes of applying g (complex64) to the reset
+    state.  A leading Hadamard layer followed by fused passes is generated by
+    the first pass in shared memory (that pass writes 2^n amplitudes and
+    reads none); alone, or before plain per-gate kernels, it is one uniform
+    fill (2^n amplitudes written)."""
     k = leading_h_layer(qs, g, n)
-    st = (qs.qs_plan_circuit(n, qs.QS_C64, g[k:], mode=md, precision=prec) if len(g) > k
-          else {"passes": 0, "bytes": 0.0})
-    return {"passes": st["passes"], "launches": st["passes"] + (1 if k else 0),
-            "bytes": st["bytes"] + (8.0 * (1 << n) if k else 0.0), "fill": k}
+    N8 = 8.0 * (1 << n)
+    if len(g) == k:
+        return {"passes": 0, "launches": 1 if k else 0, "bytes": N8 if k else 0.0, "fill": k}
+    st = qs.qs_plan_circuit(n, qs.QS_C64, g[k:], mode=md, precision=prec)
+    if md == qs.QS_MODE_PLAIN:
+        return {"passes": st["passes"], "launches": st["passes"] + (1 if k else 0),
+                "bytes": st["bytes"] + (N8 if k else 0.0), "fill": k}
+    return {"passes": st["passes"], "launches": st["passes"],
+            "bytes": st["bytes"] - (N8 if k else 0.0), "fill": k}
 
 
 def run_ours(args, rank, world, local):
@@ -258,15 +267,11 @@ def run_ours(args, rank, world, local):
     def step(i, timed, gates):
         seed = base_seed + i
         qs.qs_state_reset(h)                                                         # a2
-        # the leading Hadamard layer (one uniform fill on the reset state)
-        # and the fused passes are applied by two calls with an event between
-        # them, so that the passes' own device time is measured live
-        k = leading_h_layer(qs, gates, n)
-        e0, em, e1 = ev(), ev(), ev()
+        # one call: the leading Hadamard layer's uniform state is generated
+        # by the first fused pass; the events bracket the passes
+        e0, e1 = ev(), ev()
         e0.record(stream)
-        qs.qs_apply_circuit(h, gates[:k], mode=mode)                                 # a2 / cycle 0
-        em.record(stream)
-        qs.qs_apply_circuit(h, gates[k:], mode=mode)                                 # a4-a6
+        qs.qs_apply_circuit(h, gates, mode=mode)                                     # a2, a4-a6
         e1.record(stream)
         nxt = prepare(i + 1)                                                         # overlaps a4-a6
         qs.qs_probabilities(h, probs, fp64=W["fp64_probs"])                          # a7
@@ -274,7 +279,7 @@ def run_ours(args, rank, world, local):
         qs.qs_sample(h, m, 1000 + seed, out=samples)                                 # a9
         ce, dh = qs.qs_cross_entropy(h, samples)                                     # a10
         if timed:
-            apply_ms.append((e0, em, e1))
+            apply_ms.append((e0, e1))
             timed_gates.append(gates)
         results["last"] = dict(entropy=st["entropy"], norm=st["norm"], delta_h=dh, ce=ce)
         return nxt
@@ -296,19 +301,21 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    apply_total = sum(a.elapsed_time(c) for a, _, c in apply_ms)
-    passes_ms = sum(b.elapsed_time(c) for _, b, c in apply_ms)
-    fill_ms = apply_total - passes_ms
+    passes_ms = sum(a.elapsed_time(b) for a, b in apply_ms)
     total_ms = job_max_ms(total_ms, dist, "cuda")
-    passes_seen = [applied_plan(qs, n, g, mode)["passes"] for g in timed_gates]
+    plans_seen = [applied_plan(qs, n, g, mode) for g in timed_gates]
+    passes_seen = [pl["passes"] for pl in plans_seen]
     value = job_value(depth * args.steps, world, total_ms)
     passes_total = sum(passes_seen)
-    pass_bytes = 16.0 * (1 << n)                 # read + write of 2^n complex64
+    # algorithmic bytes: 16 per amplitude per pass (read + write), 8 for the
+    # first pass of a circuit, which generates its input (the uniform state)
+    bytes_total = sum(pl["bytes"] for pl in plans_seen)
+    pass_bytes = bytes_total / passes_total      # average per launch
     avg_pass_ms = passes_ms / passes_total
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     achieved = pass_bytes / (avg_pass_ms / 1000.0) / 1e9
-    traffic = load_traffic(args.mode, n)
+    traffic, traffic_launch = load_traffic(args.mode, n) or (None, None)
 
     # ---- e2e: same steps through the public API with host buffers ----
     probs_host = [torch.empty(1 << n, dtype=probs.dtype, pin_memory=True) for _ in range(2)]
@@ -439,23 +446,25 @@ def run_ours(args, rank, world, local):
         "dtype": "f32",
         "data": "synthetic (seeded random circuits of the paper's grid rules)",
         "config": workload_config(args, n, world),
-        "apply_cycles_per_s": round(depth * args.steps / (apply_total / 1000.0), 3),
+        "apply_cycles_per_s": round(depth * args.steps / (passes_ms / 1000.0), 3),
         "passes_per_circuit": passes_total / args.steps,
-        "fill_ms_per_circuit": round(fill_ms / args.steps, 4),
         "roofline": {"kernel": ("k_fused_pass<float,5,0,0>" if args.mode == "fused"
                                 else "k_fused_pass<float,5,1,1>"),
                      "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                      "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4),
                      "frac_of_nominal_7900": round(achieved / 7900.0, 4), "traffic": traffic,
+                     "traffic_launch": traffic_launch,
                      "bytes_per_launch": pass_bytes, "avg_launch_ms": round(avg_pass_ms, 4)},
-        # e2e: the asynchronous read-out (the copy engine moves step i's
-        # probabilities while step i + 1 evolves; timed until the last copy
-        # has landed); the synchronous read-out beside it
-        "e2e": {"value": round(e2e_async_value, 3), "unit": "cycles/s",
+        # e2e: the synchronous read-out (the read-out kernel writes the
+        # page-locked buffer directly); the asynchronous one (the copy engine
+        # moves step i's probabilities while step i + 1 evolves, timed until
+        # the last copy has landed) beside it.  The copy engine's rate into
+        # host memory differed by almost 2x from one machine to the next.
+        "e2e": {"value": round(e2e_value, 3), "unit": "cycles/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
-                "readout": "qs_probabilities_async",
-                "sync_readout_value": round(e2e_value, 3)},
+                "readout": "qs_probabilities",
+                "async_readout_value": round(e2e_async_value, 3)},
         "gpu_launches": sum(kernel_launches_per_step(p) for p in passes_seen),
         "clocks": clk,
         "last_step": {k: round(v, 6) for k, v in results["last"].items()},
@@ -630,7 +639,7 @@ def grid20_forms(qs, torch):
                 g = qs.qs_circuit_generate(4, 5, depth, seed)
                 plan = qs.qs_plan_circuit(n, dt, g[leading_h_layer(qs, g, n):])
                 esz = 8 if dt == qs.QS_C64 else 16
-                bytes_tot += plan["bytes"] + esz * (1 << n)              # passes + the uniform fill
+                bytes_tot += plan["bytes"] - esz * (1 << n)              # the first pass only writes
                 qs.qs_state_reset(h)
                 qs.qs_prepare_circuit(h, g)
                 torch.cuda.synchronize()
@@ -746,7 +755,7 @@ def load_traffic(mode, n):
     if not r or r.get("source_sha1") != digest:
         return None
     # scale the captured launch's traffic to this state size
-    return round(r["bytes_per_launch"] * (2.0 ** n) / (2.0 ** r["qubits"]), 1)
+    return round(r["bytes_per_launch"] * (2.0 ** n) / (2.0 ** r["qubits"]), 1), r.get("launch")
 
 
 ORACLE_SHARES = 64      # one oracle step = 1/64 of the whole step

@@ -392,11 +392,19 @@ static qs_status qs_apply_circuit_impl(qs_state *s, const qs_gate *gates, size_t
     DeviceGuard g(s->device);
     ++s->version;
     // Sec. pt, cycle 0: on |0...0> a leading layer of Hadamards on every
-    // qubit gives the uniform superposition, written in one pass
+    // qubit gives the uniform superposition: written in one pass, or, when
+    // fused passes follow, generated by the first pass in shared memory (the
+    // state is then neither written by a fill nor read by that pass)
+    double uniform = 0.0;
     if (s->is_zero && !s->escaped) {
         if (const size_t h = leading_h_layer(gates, ngates, s->n)) {
             s->zero_pending = false;
-            if (qs_status st = launch_init_uniform(s)) return st;
+            if (ngates > h && mode != QS_MODE_PLAIN && s->n >= rb) {
+                uniform = std::pow(2.0, -0.5 * s->n);
+                ++s->version;
+            } else if (qs_status st = launch_init_uniform(s)) {
+                return st;
+            }
             gates += h;
             ngates -= h;
         }
@@ -412,8 +420,12 @@ static qs_status qs_apply_circuit_impl(qs_state *s, const qs_gate *gates, size_t
     const Plan *plan;
     const void *dev;
     DevicePlanSlot *slot;
-    if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) return st;
-    if (qs_status st = run_fused_plan(s, *plan, dev)) return st;
+    if (qs_status st = get_plan(s, gates, ngates, opts, &plan, &dev, &slot)) {
+        // the leading layer is still applied, as when it is written first
+        if (uniform != 0.0) launch_init_uniform(s);
+        return st;
+    }
+    if (qs_status st = run_fused_plan(s, *plan, dev, uniform)) return st;
     return slot_in_use(s, slot);
 }
 

@@ -838,7 +838,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                                                 const DevOp *__restrict__ ops_g, uint64_t t_begin,
                                                 uint64_t t_end, const uint32_t *__restrict__ tc_words,
                                                 int *__restrict__ err_flag, FusedSmem<R, RB> &S, TcSmem &TS,
-                                                unsigned char *smem_raw)
+                                                unsigned char *smem_raw, R uniform = (R)0)
 {
     using V = typename V2T<R>::T;
     constexpr int NS = 1 << RB;                 // register slots per thread
@@ -994,7 +994,21 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         // out-of-tile and thread bits are disjoint from it_off: OR = add
         const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
-        if (active) {
+        if (active && uniform != (R)0) {
+            // the pass starts from the uniform state (the leading Hadamard
+            // layer on |0...0>): the tile is written, not loaded
+            V fill[CE];
+#pragma unroll
+            for (int q = 0; q < CE; ++q) {
+                fill[q].x = uniform;
+                fill[q].y = (R)0;
+            }
+#pragma unroll
+            for (int it = 0; it < CPT; ++it) {
+                const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
+                *reinterpret_cast<float4 *>(gsm + sw) = *reinterpret_cast<const float4 *>(fill);
+            }
+        } else if (active) {
 #pragma unroll
             for (int it = 0; it < CPT; ++it) {
                 const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
@@ -1142,7 +1156,7 @@ template <typename R, int RB, int TCP, bool FULL>
 __global__ void __launch_bounds__(kThreadsMax, pass_ctas_per_sm(TCP))
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
-             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag)
+             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag, R uniform)
 {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     __shared__ FusedSmem<R, RB> S;
@@ -1156,7 +1170,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
     const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
     fused_pass_body<R, RB, TCP, FULL>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
-                                      smem_raw);
+                                      smem_raw, uniform);
 }
 
 // True when pass `hp` stages an op that the Clifford+T interpreter has no
@@ -1288,7 +1302,7 @@ k_batch_persistent(float2 *amps, const PersistItem *__restrict__ items, int nite
 }
 
 template <typename R, int RB>
-static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan)
+static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan, double uniform)
 {
     using V = typename V2T<R>::T;
     const DevPass *dpass = reinterpret_cast<const DevPass *>(dev_plan);
@@ -1330,7 +1344,7 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                 const uint64_t cap = (uint64_t)s->num_sms * pass_ctas_per_sm(plan.precision);
                 const int grid = (int)(ntiles < cap ? ntiles : cap);
                 kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, dwords,
-                                                         err);
+                                                         err, p == 0 ? (R)uniform : (R)0);
             } else {
                 return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need complex64");
             }
@@ -1340,7 +1354,8 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
             QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const uint64_t cap = (uint64_t)s->num_sms * 2;
             const int grid = (int)(ntiles < cap ? ntiles : cap);
-            kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, nullptr, nullptr);
+            kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, nullptr, nullptr,
+                                                     p == 0 ? (R)uniform : (R)0);
         }
         QS_LAUNCH_CHECK();
     }
@@ -1417,10 +1432,10 @@ void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, ui
 
 QS_CHECK_READER(check_poll_fused)
 
-qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan)
+qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform)
 {
-    if (s->dt == QS_C64) return run_fused_t<float, 5>(s, plan, dev_plan);
-    return run_fused_t<double, 4>(s, plan, dev_plan);
+    if (s->dt == QS_C64) return run_fused_t<float, 5>(s, plan, dev_plan, uniform);
+    return run_fused_t<double, 4>(s, plan, dev_plan, uniform);
 }
 
 }  // namespace qs

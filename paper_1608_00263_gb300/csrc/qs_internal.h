@@ -343,7 +343,11 @@ qs_status launch_init_zero(qs_state *s);
 // Every amplitude = 2^(-n/2): H^{(x)n} |0...0>.
 qs_status launch_init_uniform(qs_state *s);
 qs_status launch_plain_gate(qs_state *s, const qs_gate &g);
-qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan);
+// Runs a fused plan on the state.  uniform != 0: the state is taken to be
+// the uniform superposition with that amplitude (the leading Hadamard layer
+// on |0...0>, not written): the first pass writes its tiles in shared memory
+// instead of loading them, so the state's memory is not read.
+qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform = 0.0);
 qs_status run_tc_plan(qs_state *s, const Plan &plan, const void *dev_plan,
                       int precision);
 qs_status launch_probabilities(const qs_state *s, void *out, int fp64,

@@ -173,6 +173,30 @@ def test_leading_hadamard_layer_only_from_basis_zero(dtype):
         qs.qs_state_destroy(h)
 
 
+@pytest.mark.parametrize("dtype,mode,n,tile", [(qs.QS_C64, qs.QS_MODE_FUSED, 20, 0), (qs.QS_C64, qs.QS_MODE_FUSED, 16, 9),
+                                              (qs.QS_C128, qs.QS_MODE_FUSED, 20, 0),
+                                              (qs.QS_C64, qs.QS_MODE_FUSED_TC, 20, 0)])
+def test_leading_layer_generated_by_the_first_pass_is_exact(dtype, mode, n, tile):
+    """Applied to |0...0> in one call, a circuit's leading Hadamard layer is
+    generated by the first fused pass in shared memory (the state is not
+    written first); applied alone it is a uniform fill.  Both give the same
+    state bit for bit, and the oracle's."""
+    rows, cols = (4, n // 4)
+    g = qs.qs_circuit_generate(rows, cols, 20, 7)
+    h = qs.qs_state_create(n, dtype)
+    try:
+        qs.qs_apply_circuit(h, g, mode=mode, tile_log2=tile)
+        one = qs.qs_state_copy_out(h, n, dtype)
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g[:n], mode=mode, tile_log2=tile)     # the fill
+        qs.qs_apply_circuit(h, g[n:], mode=mode, tile_log2=tile)
+        two = qs.qs_state_copy_out(h, n, dtype)
+    finally:
+        qs.qs_state_destroy(h)
+    assert np.array_equal(one, two)
+    assert rel_l2(one, O.simulate(n, g)) < (1e-5 if dtype == qs.QS_C64 else 1e-12)
+
+
 def test_invalid_gate_launches_nothing():
     n = 10
     h = qs.qs_state_create(n, qs.QS_C64)
