@@ -362,6 +362,9 @@ def run_ours(args, rank, world, local):
 
     e2e_value, h2d, d2h = e2e_run(False, base_seed + 10_000)
     e2e_async_value, _, _ = e2e_run(True, base_seed + 20_000)
+    # share of the probabilities the read-out kernel wrote into host memory
+    # itself in the asynchronous steps (the copy engine moved the rest)
+    async_share = qs.qs_readout_share(h)
 
     # ---- one-off comparison of the forms (apply only, untimed region) ----
     compare = {}
@@ -464,7 +467,8 @@ def run_ours(args, rank, world, local):
         "e2e": {"value": round(e2e_value, 3), "unit": "cycles/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                 "readout": "qs_probabilities",
-                "async_readout_value": round(e2e_async_value, 3)},
+                "async_readout_value": round(e2e_async_value, 3),
+                "async_direct_share": round(async_share, 3)},
         "gpu_launches": sum(kernel_launches_per_step(p) for p in passes_seen),
         "clocks": clk,
         "last_step": {k: round(v, 6) for k, v in results["last"].items()},

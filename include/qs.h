@@ -218,16 +218,32 @@ qs_status qs_probabilities(const qs_state *s, void *out, int out_is_fp64);
 /* As qs_probabilities, but stream-ordered for every kind of `out` except
  * pageable host memory (which is served synchronously, as by
  * qs_probabilities).  For page-locked host `out` (cudaHostAlloc /
- * cudaHostRegister) the probabilities are formed in a library-owned device
- * buffer (2^n floats or doubles, allocated on first use and kept with the
- * state) on the state's stream and copied to `out` by the copy engine on a
+ * cudaHostRegister) the read-out kernel runs on the state's stream and, for
+ * complex64 states with 16-byte aligned `out`, writes a share of the
+ * probabilities (whole groups of 256, from index 0) into `out` itself; the
+ * rest (all of them for complex128 states or unaligned `out`) goes to a
+ * library-owned device buffer (2^n floats or doubles, allocated on first use
+ * and kept with the state) and is copied to `out` by the copy engine on a
  * second stream, so the copy overlaps the work the caller enqueues next
- * (e.g. the next circuit).  `out` holds the probabilities of the state as
- * it was at the call once qs_state_sync(s) has returned; until then the
- * caller must neither read nor free it.  Successive asynchronous read-outs
- * of one state are copied in call order.  QS_ERR_OOM if the device buffer
+ * (e.g. the next circuit).  The share is 0 unless set by
+ * qs_readout_share: writing part of the output directly pays on hosts where
+ * the copy engine cannot move the whole read-out in the time of the work
+ * between read-outs (the kernel's own host writes hold up the state's
+ * stream, the copy engine's do not).  `out` holds the probabilities of the
+ * state as it was at the call once qs_state_sync(s) has returned; until
+ * then the caller must neither read nor free it.  Successive asynchronous read-outs
+ * of one state are copied in call order; the values are those of
+ * qs_probabilities whatever the share.  QS_ERR_OOM if the device buffer
  * cannot be allocated. */
 qs_status qs_probabilities_async(const qs_state *s, void *out, int out_is_fp64);
+
+/* Share of qs_probabilities_async's output that the read-out kernel writes
+ * into page-locked host memory itself (complex64 states; rounded to whole
+ * groups of 256 probabilities).  `share` in [0, 1] sets it for the
+ * following calls; a negative value restores the default, 0 (everything
+ * through the copy engine); NaN changes nothing.  `current` (may be NULL)
+ * receives the share in force.  QS_ERR_INVALID_ARG for a share above 1. */
+qs_status qs_readout_share(qs_state *s, double share, double *current);
 
 /* Waits for all work of the state: its stream and any asynchronous
  * read-out copies (qs_probabilities_async).  QS_ERR_CUDA on a device error. */

@@ -26,7 +26,7 @@ __all__ = [
     "qs_version", "qs_last_error", "qs_state_create", "qs_state_attach", "qs_state_destroy",
     "qs_state_amplitudes", "qs_state_reset", "qs_apply_circuit", "qs_prepare_circuit",
     "qs_plan_circuit",
-    "qs_probabilities", "qs_probabilities_async", "qs_state_sync", "qs_sample", "qs_sample_noalloc",
+    "qs_probabilities", "qs_probabilities_async", "qs_readout_share", "qs_state_sync", "qs_sample", "qs_sample_noalloc",
     "qs_cross_entropy", "qs_pt_moments",
     "qs_state_copy_out", "qs_state_copy_in", "qs_circuit_generate", "qs_adjoint_gradient",
     "qs_batch_create", "qs_batch_run", "qs_batch_state", "qs_batch_destroy", "qs_cycle_statistics",
@@ -142,9 +142,20 @@ def qs_probabilities(h, out, fp64=True):
 
 def qs_probabilities_async(h, out, fp64=True):
     """As qs_probabilities, stream-ordered; page-locked host `out` is filled
-    by the copy engine while later work runs: complete after qs_state_sync."""
+    partly by the read-out kernel and partly by the copy engine while later
+    work runs: complete after qs_state_sync."""
     N.check(N.lib().qs_probabilities_async(h, _ptr(out), 1 if fp64 else 0))
     return out
+
+
+def qs_readout_share(h, share=float("nan")):
+    """Share of an asynchronous read-out the kernel writes into host memory
+    itself: 0..1 sets it, negative restores the default 0 (all through the
+    copy engine), NaN (the default argument) only reads it.  Returns the
+    share in force."""
+    cur = ctypes.c_double()
+    N.check(N.lib().qs_readout_share(h, float(share), ctypes.byref(cur)))
+    return cur.value
 
 
 def qs_state_sync(h):

@@ -78,6 +78,7 @@ SIGNATURES = {
     "qs_probabilities": (ctypes.c_int, [P, P, ctypes.c_int]),
     "qs_probabilities_async": (ctypes.c_int, [P, P, ctypes.c_int]),
     "qs_state_sync": (ctypes.c_int, [P]),
+    "qs_readout_share": (ctypes.c_int, [P, ctypes.c_double, P]),
     "qs_sample": (ctypes.c_int, [P, U64, U64, P]),
     "qs_sample_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, P, P, U64, U64, P]),
     "qs_cross_entropy": (ctypes.c_int, [P, P, U64, PD, PD]),

@@ -500,7 +500,8 @@ extern "C" qs_status qs_probabilities_async(const qs_state *s, void *out, int ou
     DeviceGuard g(s->device);
     if (qs_status st = materialize(s)) return st;
     const uint64_t N = 1ULL << s->n;
-    const size_t bytes = N * (out_is_fp64 ? 8 : 4);
+    const size_t esz = out_is_fp64 ? 8 : 4;
+    const size_t bytes = N * esz;
     if (!s->ro_done) {
         cudaStream_t cs = nullptr;
         cudaEvent_t ready = nullptr, done = nullptr;
@@ -530,20 +531,46 @@ extern "C" qs_status qs_probabilities_async(const qs_state *s, void *out, int ou
         }
         s->ro_bytes = bytes;
     }
+    // complex64 states split the read-out at a chunk boundary: chunks
+    // [0, csplit) straight into the host memory, the rest through ro_buf
+    // (complex128 states and unaligned host memory take the copy engine only)
+    void *view = pinned_device_view(out);
+    const bool split = s->dt == QS_C64 && ((uintptr_t)view % 16) == 0;
+    const uint64_t nchunks = readout_chunks(s);
+    uint64_t csplit = 0;
+    if (split) csplit = std::min<uint64_t>(nchunks, (uint64_t)std::llround(s->ro_frac * (double)nchunks));
+    // a state of one partial chunk (n < 8) is written whole, never split
+    if (split && N < 256 && csplit > 0) csplit = nchunks;
+    const size_t direct = split ? std::min<size_t>(bytes, (size_t)csplit * 256 * esz) : 0;
     // the buffer is free once the previous copy has finished (an event never
     // recorded is complete)
     QS_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ro_done, 0));
-    if (qs_status st = launch_probabilities(s, s->ro_buf, out_is_fp64, 0, N)) return st;
+    if (split && csplit > 0) {
+        if (qs_status st = readout_c64(s, view, out_is_fp64 ? 2 : 1, s->ro_buf, csplit)) return st;
+    } else {
+        if (qs_status st = launch_probabilities(s, s->ro_buf, out_is_fp64, 0, N)) return st;
+    }
     QS_CUDA_TRY(cudaEventRecord(s->ro_ready, s->stream));
     QS_CUDA_TRY(cudaStreamWaitEvent(s->ro_stream, s->ro_ready, 0));
     // 64 MB pieces: the small device-to-host copies of later calls (scalar
     // results, samples) share the copy engine and would otherwise wait for
     // the whole read-out, and with them the host's next launches
     constexpr size_t kPiece = size_t(64) << 20;
-    for (size_t f = 0; f < bytes; f += kPiece)
-        QS_CUDA_TRY(cudaMemcpyAsync((char *)out + f, (const char *)s->ro_buf + f, std::min(kPiece, bytes - f),
-                                    cudaMemcpyDeviceToHost, s->ro_stream));
+    for (size_t f = direct; f < bytes; f += kPiece)
+        QS_CUDA_TRY(cudaMemcpyAsync((char *)out + f, (const char *)s->ro_buf + (f - direct),
+                                    std::min(kPiece, bytes - f), cudaMemcpyDeviceToHost, s->ro_stream));
     QS_CUDA_TRY(cudaEventRecord(s->ro_done, s->ro_stream));
+    return QS_OK;
+}
+
+extern "C" qs_status qs_readout_share(qs_state *s, double share, double *current)
+{
+    clear_error();
+    if (qs_status st = check_state(s)) return st;
+    if (share > 1.0) return set_error(QS_ERR_INVALID_ARG, "share %g above 1", share);
+    if (share >= 0.0) s->ro_frac = share;
+    else if (share < 0.0) s->ro_frac = 0.0;
+    if (current) *current = s->ro_frac;
     return QS_OK;
 }
 

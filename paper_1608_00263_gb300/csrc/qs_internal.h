@@ -310,13 +310,17 @@ struct qs_state {
     bool is_zero = false;
     mutable bool zero_pending = false;
     mutable bool escaped = false;
-    // asynchronous host read-out (qs_probabilities_async): the probabilities
-    // are formed in ro_buf on `stream`, then copied to page-locked host memory
-    // on ro_stream; ro_done marks the end of the last copy (the buffer is free)
+    // asynchronous host read-out (qs_probabilities_async): the read-out
+    // kernel writes the first share of the probabilities (ro_frac of the
+    // 256-probability chunks, set by qs_readout_share) into the page-locked
+    // host memory itself and the rest into ro_buf, which the copy engine
+    // moves on ro_stream while later work runs; ro_done marks the end of the
+    // last copy (the buffer is free)
     mutable void *ro_buf = nullptr;
     mutable size_t ro_bytes = 0;
     mutable cudaStream_t ro_stream = nullptr;
     mutable cudaEvent_t ro_ready = nullptr, ro_done = nullptr;
+    double ro_frac = 0.0;
     // page-locked host memory mapped into the device: kernels write small
     // results (hbox) and host-side sample arrays (stage) there directly, so
     // no copy-engine transfer is needed and nothing queues behind an
@@ -386,7 +390,12 @@ qs_status read_back(const qs_state *s, void *host, const void *dev, size_t bytes
 // the statistics partials and the sampler's chunk sums into the read-out
 // cache, which it marks valid for the current state.
 constexpr int kReadoutStats = 1, kReadoutChunks = 2, kReadoutScanned = 4;
-qs_status readout_c64(const qs_state *s, void *out, int out_kind);
+// Fused complex64 read-out (probabilities, statistics partials, sampler
+// chunk sums); with out_hi, chunks [csplit, nchunks) of the probabilities go
+// to out_hi (chunk csplit at its start) instead of out.  Chunks are
+// readout_chunks(s) groups of 256 probabilities.
+qs_status readout_c64(const qs_state *s, void *out, int out_kind, void *out_hi = nullptr, uint64_t csplit = 0);
+uint64_t readout_chunks(const qs_state *s);
 bool readout_cached(const qs_state *s, int flag);
 int readout_grid(const qs_state *s);
 double *readout_part(const qs_state *s);

@@ -532,7 +532,7 @@ __global__ void k_sample_search(const typename V2T<R>::T *__restrict__ a, uint64
 template <int OUT>   // 0: no p, 1: FP32 p, 2: FP64 p
 __global__ void __launch_bounds__(kStatThreads, 3)
 k_readout_c64(const float2 *__restrict__ a, uint64_t N, uint64_t nchunks, float scaleN, void *__restrict__ out,
-              double *__restrict__ csum, double *__restrict__ part)
+              void *__restrict__ out_hi, uint64_t csplit, double *__restrict__ csum, double *__restrict__ part)
 {
     __shared__ __align__(16) float stage_all[kStatThreads / 32][kChunk];
     float *stage = stage_all[threadIdx.x >> 5];
@@ -567,15 +567,18 @@ k_readout_c64(const float2 *__restrict__ a, uint64_t N, uint64_t nchunks, float 
                     for (int i = 0; i < 8; ++i) stage[lane * 8 + i] = p[i];
                     __syncwarp();
                     const float4 *st4 = reinterpret_cast<const float4 *>(stage);
+                    // chunks from csplit on go to the second output
+                    void *dst = c < csplit ? out : out_hi;
+                    const uint64_t cd = c < csplit ? c : c - csplit;
                     if constexpr (OUT == 2) {
-                        double2 *o = reinterpret_cast<double2 *>(static_cast<double *>(out) + c * kChunk);
+                        double2 *o = reinterpret_cast<double2 *>(static_cast<double *>(dst) + cd * kChunk);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const float2 q = reinterpret_cast<const float2 *>(stage)[k * 32 + lane];
                             o[k * 32 + lane] = make_double2(widen_f32(q.x), widen_f32(q.y));
                         }
                     } else {
-                        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + c * kChunk);
+                        float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(dst) + cd * kChunk);
 #pragma unroll
                         for (int k = 0; k < 2; ++k) o[k * 32 + lane] = st4[k * 32 + lane];
                     }
@@ -637,21 +640,30 @@ static qs_status readout_buffers(const qs_state *s)
 double *readout_part(const qs_state *s) { return s->rc_buf; }
 double *readout_csum(const qs_state *s) { return s->rc_buf + ((size_t)readout_grid(s) + 1) * kStatAcc; }
 
-qs_status readout_c64(const qs_state *s, void *out, int out_kind)
+uint64_t readout_chunks(const qs_state *s) { return ((1ULL << s->n) + kChunk - 1) / kChunk; }
+
+qs_status readout_c64(const qs_state *s, void *out, int out_kind, void *out_hi, uint64_t csplit)
 {
     if (qs_status st = readout_buffers(s)) return st;
     const uint64_t N = 1ULL << s->n;
     const uint64_t nchunks = (N + kChunk - 1) / kChunk;
+    // a state of one partial chunk (n < 8) is never split
+    if (!out_hi || csplit >= nchunks || N < kChunk) {
+        out_hi = nullptr;
+        csplit = nchunks;
+    }
     const int grid = readout_grid(s);
     const float scaleN = (float)std::ldexp(1.0, s->n);
     const float2 *a = (const float2 *)s->amps;
     if (out_kind == 2)
-        k_readout_c64<2><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, readout_csum(s), readout_part(s));
+        k_readout_c64<2><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, out_hi, csplit,
+                                                                readout_csum(s), readout_part(s));
     else if (out_kind == 1)
-        k_readout_c64<1><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, readout_csum(s), readout_part(s));
+        k_readout_c64<1><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, out, out_hi, csplit,
+                                                                readout_csum(s), readout_part(s));
     else
-        k_readout_c64<0><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, nullptr, readout_csum(s),
-                                                                readout_part(s));
+        k_readout_c64<0><<<grid, kStatThreads, 0, s->stream>>>(a, N, nchunks, scaleN, nullptr, nullptr, nchunks,
+                                                                readout_csum(s), readout_part(s));
     QS_LAUNCH_CHECK();
     s->rc_version = s->version;
     s->rc_flags = kReadoutStats | kReadoutChunks;

@@ -324,6 +324,39 @@ def test_probabilities_async_overlaps_next_circuit():
         qs.qs_state_destroy(h)
 
 
+@pytest.mark.parametrize("n", [5, 8, 20])
+def test_async_readout_equals_sync_at_every_share(n):
+    """The read-out kernel writes a share of the probabilities (whole groups
+    of 256 from index 0) into the page-locked host memory itself and the copy
+    engine moves the rest: with none, part or all written directly, over
+    consecutive calls, the host memory receives exactly what
+    qs_probabilities writes (FP64 and FP32 output).  A state of fewer than
+    256 amplitudes is never split."""
+    import torch
+    rng = np.random.default_rng(100 + n)
+    h = qs.qs_state_create(n, qs.QS_C64)
+    try:
+        assert qs.qs_readout_share(h) == 0.0
+        for share in (0.3, 1.0, 0.7, -1.0):
+            qs.qs_readout_share(h, share)
+            for c in range(2):
+                qs.qs_state_reset(h)
+                qs.qs_apply_circuit(h, random_gates(rng, n, 40))
+                for fp64 in (True, False):
+                    dt = torch.float64 if fp64 else torch.float32
+                    got = torch.full((1 << n,), -1.0, dtype=dt).pin_memory()
+                    qs.qs_probabilities_async(h, got, fp64=fp64)
+                    want = np.empty(1 << n, dtype=np.float64 if fp64 else np.float32)
+                    qs.qs_probabilities(h, want, fp64=fp64)
+                    qs.qs_state_sync(h)
+                    assert np.array_equal(got.numpy(), want), (share, c, fp64)
+            assert qs.qs_readout_share(h) == max(share, 0.0)
+        with pytest.raises(qs.QSError):
+            qs.qs_readout_share(h, 1.5)
+    finally:
+        qs.qs_state_destroy(h)
+
+
 def test_pt_moments(state20):
     dtype, h, ref, p = state20
     r = qs.qs_pt_moments(h, 10)
