@@ -52,6 +52,15 @@ def test_version_string():
     assert "sm_103a" in qs.qs_version()
 
 
+def test_state_calls_reject_a_null_state_on_the_host():
+    # argument checks run before any device call, so they hold without a GPU
+    for call in (lambda: qs.qs_readout_share(None, 0.5), lambda: qs.qs_readout_share(None),
+                 lambda: qs.qs_state_sync(None)):
+        with pytest.raises(qs.QSError) as e:
+            call()
+        assert e.value.status == _native.QS_ERR_INVALID_ARG
+
+
 GRIDS = [(4, 5, None), (5, 6, None), (2, 2, None), (1, 9, None), (3, 4, [(2, 3)]),
          (6, 6, [(0, 0), (5, 5)]), (4, 6, [(3, 4), (3, 5)])]
 
