@@ -175,6 +175,27 @@ def leading_h_layer(qs, g, n):
     return n if len(set(g["q0"][:n].tolist())) == n else 0
 
 
+def fold_diagonal_prefix(qs, g):
+    """Gates left to run after the library folds the diagonal prefix that
+    follows a leading Hadamard layer (register form): a T or CZ none of whose
+    qubits has met a non-diagonal gate becomes a phase of the first pass's
+    generated state.  Returns (number folded, remaining gates)."""
+    import numpy as np
+    touched, keep, nf = 0, [], 0
+    diag = (qs.QS_T, qs.QS_CZ, qs.QS_RZ, qs.QS_CPHASE)
+    for i in range(len(g)):
+        k, a, b = int(g["kind"][i]), int(g["q0"][i]), int(g["q1"][i])
+        two = k in (qs.QS_CZ, qs.QS_CPHASE)
+        m = (1 << a) | ((1 << b) if two else 0)
+        if (k == qs.QS_T or k == qs.QS_CZ) and not touched & m:
+            nf += 1
+            continue
+        if k not in diag:
+            touched |= m
+        keep.append(i)
+    return nf, g[np.array(keep, dtype=np.int64)]
+
+
 def device_state_copy(qs, torch, h, n):
     """A device copy of a complex64 state (as 2^(n+1) floats)."""
     ptr = qs.qs_state_amplitudes(h)
@@ -208,13 +229,19 @@ def applied_plan(qs, n, g, md, prec=0):
     """Launches and algorithmic bytes of applying g (complex64) to the reset
     state.  A leading Hadamard layer followed by fused passes is generated by
     the first pass in shared memory (that pass writes 2^n amplitudes and
-    reads none); alone, or before plain per-gate kernels, it is one uniform
-    fill (2^n amplitudes written)."""
+    reads none), in the register form with the diagonal prefix after it
+    folded in as phases (those gates are no pass's work); alone, or before
+    plain per-gate kernels, it is one uniform fill (2^n amplitudes written)."""
     k = leading_h_layer(qs, g, n)
     N8 = 8.0 * (1 << n)
     if len(g) == k:
         return {"passes": 0, "launches": 1 if k else 0, "bytes": N8 if k else 0.0, "fill": k}
-    st = qs.qs_plan_circuit(n, qs.QS_C64, g[k:], mode=md, precision=prec)
+    rest = g[k:]
+    if k and md == qs.QS_MODE_FUSED:
+        nf, folded_rest = fold_diagonal_prefix(qs, rest)
+        if nf and len(folded_rest):
+            rest = folded_rest
+    st = qs.qs_plan_circuit(n, qs.QS_C64, rest, mode=md, precision=prec)
     if md == qs.QS_MODE_PLAIN:
         return {"passes": st["passes"], "launches": st["passes"] + (1 if k else 0),
                 "bytes": st["bytes"] + (N8 if k else 0.0), "fill": k}

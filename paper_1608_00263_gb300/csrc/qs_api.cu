@@ -396,12 +396,25 @@ static qs_status qs_apply_circuit_impl(qs_state *s, const qs_gate *gates, size_t
     // fused passes follow, generated by the first pass in shared memory (the
     // state is then neither written by a fill nor read by that pass)
     double uniform = 0.0;
+    FoldArgs fold{};
+    std::vector<qs_gate> rest;
     if (s->is_zero && !s->escaped) {
-        if (const size_t h = leading_h_layer(gates, ngates, s->n)) {
+        if (size_t h = leading_h_layer(gates, ngates, s->n)) {
             s->zero_pending = false;
             if (ngates > h && mode != QS_MODE_PLAIN && s->n >= rb) {
                 uniform = std::pow(2.0, -0.5 * s->n);
                 ++s->version;
+                // the T and CZ gates that reach the uniform state before any
+                // non-diagonal gate on their qubits become its phases, formed
+                // by the same first pass (register form, gates left to run)
+                if (mode == QS_MODE_FUSED && fold_diagonal_prefix(gates + h, ngates - h, &rest, &fold) > 0 &&
+                    !rest.empty()) {
+                    gates = rest.data();
+                    ngates = rest.size();
+                    h = 0;
+                } else {
+                    fold.nfold = 0;
+                }
             } else if (qs_status st = launch_init_uniform(s)) {
                 return st;
             }
@@ -425,7 +438,7 @@ static qs_status qs_apply_circuit_impl(qs_state *s, const qs_gate *gates, size_t
         if (uniform != 0.0) launch_init_uniform(s);
         return st;
     }
-    if (qs_status st = run_fused_plan(s, *plan, dev, uniform)) return st;
+    if (qs_status st = run_fused_plan(s, *plan, dev, uniform, fold.nfold > 0 ? &fold : nullptr)) return st;
     return slot_in_use(s, slot);
 }
 
@@ -445,8 +458,18 @@ extern "C" qs_status qs_prepare_circuit(qs_state *s, const qs_gate *gates, size_
     DeviceGuard g(s->device);
     // a leading Hadamard layer is written as the uniform state when the
     // circuit starts from |0...0> (the usual reset + apply): plan the rest
+    std::vector<qs_gate> rest;
     if (!s->escaped) {
         const size_t h = leading_h_layer(gates, ngates, s->n);
+        if (h && ngates > h && s->n >= rb && mode == QS_MODE_FUSED) {
+            // as qs_apply_circuit: the folded diagonal prefix is no pass's work
+            FoldArgs fold;
+            if (fold_diagonal_prefix(gates + h, ngates - h, &rest, &fold) > 0 && !rest.empty()) {
+                const Plan *plan;
+                const void *dev;
+                return get_plan(s, rest.data(), rest.size(), opts, &plan, &dev);
+            }
+        }
         gates += h;
         ngates -= h;
         if (ngates == 0) return QS_OK;

@@ -459,6 +459,15 @@ struct FusedSmem {
     uint8_t code8[kMaxOpsPerPass + 4];      // Clifford+T interpreter (FULL = false)
     SThread th[kMaxPhasesPerPass][kThreadsMax];
     uint64_t it_off[(1 << RB)];
+    // diagonal prefix folded into the first pass's generated state
+    // (FoldArgs): CZ partners of each qubit as a qubit mask and as a mask of
+    // the tile bits holding them, T counts, the unit table and the eight
+    // values uniform * e^{i pi k / 4}
+    uint64_t fnb[kMaxQubits];
+    uint64_t fm[3];
+    uint16_t fg[kMaxQubits];
+    uint8_t fu[(1 << RB)];
+    typename V2T<R>::T fw[8];
 };
 
 // ---------------------------------------------------------------------------
@@ -838,7 +847,7 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
                                                 const DevOp *__restrict__ ops_g, uint64_t t_begin,
                                                 uint64_t t_end, const uint32_t *__restrict__ tc_words,
                                                 int *__restrict__ err_flag, FusedSmem<R, RB> &S, TcSmem &TS,
-                                                unsigned char *smem_raw, R uniform = (R)0)
+                                                unsigned char *smem_raw, R uniform = (R)0, bool folded = false)
 {
     using V = typename V2T<R>::T;
     constexpr int NS = 1 << RB;                 // register slots per thread
@@ -952,6 +961,41 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
     }
     for (int i = threadIdx.x; i < CPT; i += blockDim.x) S.it_off[i] = deposit((uint64_t)(CE * nthr) * i, S.P.L, t);
     const uint64_t tid_off = deposit((uint64_t)CE * tid, S.P.L, t);
+    // T count of qubit q (mod 8), for the folded diagonal prefix
+    auto fcount = [&](int q) -> uint32_t {
+        return (uint32_t)((S.fm[0] >> q) & 1) + 2u * (uint32_t)((S.fm[1] >> q) & 1) +
+               4u * (uint32_t)((S.fm[2] >> q) & 1);
+    };
+    if (folded) {
+        // each qubit's CZ partners as tile bits
+        for (int q = threadIdx.x; q < S.P.n; q += blockDim.x) {
+            uint32_t m = 0;
+            for (int b = 0; b < t; ++b) m |= (uint32_t)((S.fnb[q] >> S.P.L[b]) & 1) << b;
+            S.fg[q] = (uint16_t)m;
+        }
+        // unit u = (it, q) of every thread: tile element CE nthr it + q;
+        // 4 (CZ pairs among its tile bits) + (its T counts), mod 8
+        for (int u = threadIdx.x; u < CPT * CE; u += blockDim.x) {
+            const uint32_t eu = (uint32_t)(CE * nthr) * (uint32_t)(u / CE) + (uint32_t)(u % CE);
+            uint32_t pairs = 0, tcnt = 0;
+            for (uint32_t w = eu; w; w &= w - 1) {
+                const int qb = S.P.L[__ffs(w) - 1];
+                for (uint32_t v = w & (w - 1); v; v &= v - 1) pairs += (uint32_t)(S.fnb[qb] >> S.P.L[__ffs(v) - 1]) & 1u;
+                tcnt += fcount(qb);
+            }
+            S.fu[u] = (uint8_t)((4u * (pairs & 1u) + tcnt) & 7u);
+        }
+        // uniform * e^{i pi k / 4}: 2^(-n/2) and 2^(-n/2) / sqrt2 formed in
+        // FP64 from n (the latter a power of two for odd n)
+        if (threadIdx.x < 8) {
+            const int k = (int)threadIdx.x;
+            const double a = std::exp2(-0.5 * S.P.n), c = a * 0.70710678118654752440;
+            const double re[8] = {a, c, 0.0, -c, -a, -c, 0.0, c};
+            const double im[8] = {0.0, c, a, c, 0.0, -c, -a, -c};
+            S.fw[k].x = (R)re[k];
+            S.fw[k].y = (R)im[k];
+        }
+    }
     const R gsr = (R)S.P.gscale_re, gsi = (R)S.P.gscale_im;
     const bool gscale_one = (S.P.gscale_re == 1.0 && S.P.gscale_im == 0.0);
     __syncthreads();
@@ -994,7 +1038,45 @@ __device__ __forceinline__ void fused_pass_body(typename V2T<R>::T *__restrict__
         // out-of-tile and thread bits are disjoint from it_off: OR = add
         const V *tsrc = amps + (base | tid_off);
         // ---- load the tile (16-byte cp.async, coalesced runs) ----
-        if (active && uniform != (R)0) {
+        if (active && uniform != (R)0 && folded) {
+            // the pass starts from the uniform state times the folded
+            // diagonal prefix: element x gets e^{i pi k(x) / 4} 2^(-n/2) with
+            // k = 4 (CZ pairs within x) + (T counts of x), mod 8, summed over
+            // the out-of-tile bits (the tile base), the thread's tile bits
+            // (element CE tid) and the unit's (CE nthr it + q), plus the
+            // pairs across those parts
+            uint32_t pb = 0, nbm = 0;
+            for (uint64_t w = base; w; w &= w - 1) {
+                const int i = __ffsll((long long)w) - 1;
+                pb ^= (uint32_t)__popcll(base & S.fnb[i] & (~0ULL << i << 1));
+                nbm ^= S.fg[i];
+            }
+            const uint32_t lb = (uint32_t)(__popcll(base & S.fm[0]) + 2 * __popcll(base & S.fm[1]) +
+                                           4 * __popcll(base & S.fm[2]));
+            const uint32_t et = (uint32_t)(CE * tid);
+            uint32_t pt = 0, nt = 0, lt = 0;
+            for (uint32_t w = et; w; w &= w - 1) {
+                const int b = __ffs(w) - 1;
+                const int q = S.P.L[b];
+                pt ^= (uint32_t)__popc(et & (uint32_t)S.fg[q] & (~0u << b << 1));
+                nt ^= S.fg[q];
+                lt += fcount(q);
+            }
+            const uint32_t k0 = 4u * ((pb ^ pt ^ (uint32_t)__popc(et & nbm)) & 1u) + lb + lt;
+            const uint32_t nu = nbm ^ nt;
+#pragma unroll
+            for (int it = 0; it < CPT; ++it) {
+                V fill[CE];
+#pragma unroll
+                for (int q = 0; q < CE; ++q) {
+                    const uint32_t eu = (uint32_t)(CE * nthr) * (uint32_t)it + (uint32_t)q;
+                    const uint32_t k = (k0 + S.fu[it * CE + q] + 4u * ((uint32_t)__popc(eu & nu) & 1u)) & 7u;
+                    fill[q] = S.fw[k];
+                }
+                const uint32_t sw = sw_tid ^ (swz<CE>((uint32_t)(CE * it * nthr)) * (uint32_t)sizeof(V));
+                *reinterpret_cast<float4 *>(gsm + sw) = *reinterpret_cast<const float4 *>(fill);
+            }
+        } else if (active && uniform != (R)0) {
             // the pass starts from the uniform state (the leading Hadamard
             // layer on |0...0>): the tile is written, not loaded
             V fill[CE];
@@ -1152,15 +1234,28 @@ __host__ __device__ constexpr int pass_ctas_per_sm(int tcp)
                     : (128 + tc_prec(tcp).terms * (128 * tc_prec(tcp).elem_bytes / 4) <= 256 ? 2 : 1);
 }
 
-template <typename R, int RB, int TCP, bool FULL>
+// FOLD: the instance that may start from the folded diagonal prefix (the
+// first pass of a circuit); the others compile without that code.
+template <typename R, int RB, int TCP, bool FULL, bool FOLD = false>
 __global__ void __launch_bounds__(kThreadsMax, pass_ctas_per_sm(TCP))
 k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ pass_g,
              const DevPhase *__restrict__ phases_g, const DevOp *__restrict__ ops_g,
-             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag, R uniform)
+             uint64_t ntiles, const uint32_t *__restrict__ tc_words, int *__restrict__ err_flag, R uniform,
+             FoldArgs fold)
 {
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     __shared__ FusedSmem<R, RB> S;
     __shared__ TcSmem TS;
+    // the folded diagonal prefix (first pass of a circuit only); the pass
+    // body's first barrier publishes it
+    const bool folded = FOLD && fold.nfold > 0 && uniform != (R)0;
+    if (folded && threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < kMaxQubits; ++i) S.fnb[i] = fold.nb[i];
+        S.fm[0] = fold.m1;
+        S.fm[1] = fold.m2;
+        S.fm[2] = fold.m4;
+    }
     // the tensor-core form starts the tile (its MMA operand buffer) on a
     // 1024-byte boundary of the shared window; the launch adds the slack
     unsigned char *smem_raw = smem_dyn;
@@ -1170,7 +1265,7 @@ k_fused_pass(typename V2T<R>::T *__restrict__ amps, const DevPass *__restrict__ 
     const uint64_t t_begin = blockIdx.x * per + (blockIdx.x < extra ? blockIdx.x : extra);
     const uint64_t t_end = t_begin + per + (blockIdx.x < extra ? 1 : 0);
     fused_pass_body<R, RB, TCP, FULL>(amps, pass_g, phases_g, ops_g, t_begin, t_end, tc_words, err_flag, S, TS,
-                                      smem_raw, uniform);
+                                      smem_raw, uniform, folded);
 }
 
 // True when pass `hp` stages an op that the Clifford+T interpreter has no
@@ -1302,8 +1397,10 @@ k_batch_persistent(float2 *amps, const PersistItem *__restrict__ items, int nite
 }
 
 template <typename R, int RB>
-static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan, double uniform)
+static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan, double uniform,
+                             const FoldArgs *fold)
 {
+    const FoldArgs none{};
     using V = typename V2T<R>::T;
     const DevPass *dpass = reinterpret_cast<const DevPass *>(dev_plan);
     const DevPhase *dphase = reinterpret_cast<const DevPhase *>(dpass + plan.passes.size());
@@ -1344,18 +1441,22 @@ static qs_status run_fused_t(qs_state *s, const Plan &plan, const void *dev_plan
                 const uint64_t cap = (uint64_t)s->num_sms * pass_ctas_per_sm(plan.precision);
                 const int grid = (int)(ntiles < cap ? ntiles : cap);
                 kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, dwords,
-                                                         err, p == 0 ? (R)uniform : (R)0);
+                                                         err, p == 0 ? (R)uniform : (R)0, none);
             } else {
                 return set_error(QS_ERR_INVALID_ARG, "tensor-core phases need complex64");
             }
         } else {
-            auto kern = pass_needs_full(plan, hp) ? k_fused_pass<R, RB, 0, true> : k_fused_pass<R, RB, 0, false>;
+            // the circuit's first pass forms the folded prefix's phases
+            const bool fold_here = p == 0 && fold && fold->nfold > 0 && uniform != 0.0;
+            auto kern = pass_needs_full(plan, hp)
+                            ? (fold_here ? k_fused_pass<R, RB, 0, true, true> : k_fused_pass<R, RB, 0, true>)
+                            : (fold_here ? k_fused_pass<R, RB, 0, false, true> : k_fused_pass<R, RB, 0, false>);
             const size_t smem = (size_t(1) << hp.t) * sizeof(V);
             QS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const uint64_t cap = (uint64_t)s->num_sms * 2;
             const int grid = (int)(ntiles < cap ? ntiles : cap);
             kern<<<grid, threads, smem, s->stream>>>((V *)s->amps, dpass + p, dphase, dops, ntiles, nullptr, nullptr,
-                                                     p == 0 ? (R)uniform : (R)0);
+                                                     p == 0 ? (R)uniform : (R)0, fold_here ? *fold : none);
         }
         QS_LAUNCH_CHECK();
     }
@@ -1432,10 +1533,11 @@ void batch_item_fill(void *dst, uint64_t amp_off, uint32_t pass, uint32_t tb, ui
 
 QS_CHECK_READER(check_poll_fused)
 
-qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform)
+qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform,
+                         const FoldArgs *fold)
 {
-    if (s->dt == QS_C64) return run_fused_t<float, 5>(s, plan, dev_plan, uniform);
-    return run_fused_t<double, 4>(s, plan, dev_plan, uniform);
+    if (s->dt == QS_C64) return run_fused_t<float, 5>(s, plan, dev_plan, uniform, fold);
+    return run_fused_t<double, 4>(s, plan, dev_plan, uniform, fold);
 }
 
 }  // namespace qs

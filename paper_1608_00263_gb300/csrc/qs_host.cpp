@@ -77,6 +77,41 @@ size_t leading_h_layer(const qs_gate *g, size_t ng, int n)
     return (size_t)n;
 }
 
+size_t fold_diagonal_prefix(const qs_gate *g, size_t ng, std::vector<qs_gate> *rest, FoldArgs *f)
+{
+    std::memset(f, 0, sizeof(*f));
+    rest->clear();
+    rest->reserve(ng);
+    uint64_t touched = 0;       // qubits that have met a non-diagonal gate
+    uint8_t tcount[kMaxQubits] = {0};
+    size_t nf = 0;
+    for (size_t i = 0; i < ng; ++i) {
+        const qs_gate &x = g[i];
+        const uint64_t a = 1ULL << x.q0;
+        const uint64_t b = gate_is_two_qubit(x.kind) ? 1ULL << x.q1 : 0;
+        if (x.kind == QS_T && !(touched & a)) {
+            tcount[x.q0] = (uint8_t)((tcount[x.q0] + 1) & 7);
+            ++nf;
+        } else if (x.kind == QS_CZ && !(touched & (a | b))) {
+            f->nb[x.q0] ^= b;
+            f->nb[x.q1] ^= a;
+            ++nf;
+        } else {
+            // diagonal gates left in the list (T or CZ on a touched qubit,
+            // RZ, CPHASE) commute with the folded ones and touch nothing
+            if (x.kind != QS_T && x.kind != QS_CZ && x.kind != QS_RZ && x.kind != QS_CPHASE) touched |= a | b;
+            rest->push_back(x);
+        }
+    }
+    for (int q = 0; q < kMaxQubits; ++q) {
+        if (tcount[q] & 1) f->m1 |= 1ULL << q;
+        if (tcount[q] & 2) f->m2 |= 1ULL << q;
+        if (tcount[q] & 4) f->m4 |= 1ULL << q;
+    }
+    f->nfold = (int)nf;
+    return nf;
+}
+
 qs_status validate_gates(int n, const qs_gate *g, size_t ng)
 {
     if (ng && !g) return set_error(QS_ERR_INVALID_ARG, "gates is NULL but ngates = %zu", ng);

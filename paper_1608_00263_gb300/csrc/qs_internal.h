@@ -55,6 +55,23 @@ qs_status validate_gates(int n, const qs_gate *g, size_t ng);
 // (Sec. pt, cycle 0), written as one fill instead of a pass.
 size_t leading_h_layer(const qs_gate *g, size_t ng, int n);
 
+// Diagonal prefix folded into the initial state.  After a leading Hadamard
+// layer on |0...0>, a T or CZ gate none of whose qubits has yet met a
+// non-diagonal gate commutes with every gate before it, so it acts on the
+// uniform superposition: psi_0(x) = 2^(-n/2) exp(i pi k(x) / 4) with
+// k(x) = 4 sum_{CZ (i,j)} x_i x_j + sum_i c_i x_i (mod 8), c_i the number of
+// such T gates on qubit i (Sec. pt, cycle 0; Eq. sqgunitaryoperation).
+struct FoldArgs {
+    uint64_t nb[kMaxQubits];    // CZ partners of each qubit (a repeated pair cancels)
+    uint64_t m1, m2, m4;        // bits 0, 1, 2 of each qubit's T count
+    int nfold;                  // gates folded (0: the plain uniform state)
+    int pad;
+};
+// Splits the gates after a leading Hadamard layer into the foldable
+// diagonal prefix (into *f) and the rest, in order (into *rest).  Returns
+// the number of gates folded.
+size_t fold_diagonal_prefix(const qs_gate *g, size_t ng, std::vector<qs_gate> *rest, FoldArgs *f);
+
 // ---------------------------------------------------------------------------
 // Fused-pass plan (built on the host, executed by the fused kernels)
 // ---------------------------------------------------------------------------
@@ -350,8 +367,10 @@ qs_status launch_plain_gate(qs_state *s, const qs_gate &g);
 // Runs a fused plan on the state.  uniform != 0: the state is taken to be
 // the uniform superposition with that amplitude (the leading Hadamard layer
 // on |0...0>, not written): the first pass writes its tiles in shared memory
-// instead of loading them, so the state's memory is not read.
-qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform = 0.0);
+// instead of loading them, so the state's memory is not read.  With `fold`
+// (nfold > 0) those tiles also carry the folded diagonal prefix's phases.
+qs_status run_fused_plan(qs_state *s, const Plan &plan, const void *dev_plan, double uniform = 0.0,
+                         const FoldArgs *fold = nullptr);
 qs_status run_tc_plan(qs_state *s, const Plan &plan, const void *dev_plan,
                       int precision);
 qs_status launch_probabilities(const qs_state *s, void *out, int fp64,

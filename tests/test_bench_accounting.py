@@ -44,8 +44,11 @@ def test_applied_plan_counts_the_leading_layer():
     ap = bench.applied_plan(qs, n, g, qs.QS_MODE_PLAIN)
     assert ap["passes"] == rest["passes"] and ap["launches"] == rest["passes"] + 1
     assert ap["bytes"] == rest["bytes"] + 8.0 * N
-    # fused: no fill launch; 16 N per pass, 8 N for the first (it only writes)
-    rest = qs.qs_plan_circuit(n, qs.QS_C64, g[n:], mode=qs.QS_MODE_FUSED)
+    # fused: no fill launch; 16 N per pass, 8 N for the first (it only
+    # writes); the diagonal prefix after the layer is folded into that pass
+    nf, folded = bench.fold_diagonal_prefix(qs, g[n:])
+    assert nf > 0 and len(folded) == len(g) - n - nf
+    rest = qs.qs_plan_circuit(n, qs.QS_C64, folded, mode=qs.QS_MODE_FUSED)
     ap = bench.applied_plan(qs, n, g, qs.QS_MODE_FUSED)
     assert ap["passes"] == rest["passes"] and ap["launches"] == rest["passes"]
     assert ap["bytes"] == 16.0 * N * ap["passes"] - 8.0 * N

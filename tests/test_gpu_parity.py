@@ -180,9 +180,13 @@ def test_leading_layer_generated_by_the_first_pass_is_exact(dtype, mode, n, tile
     """Applied to |0...0> in one call, a circuit's leading Hadamard layer is
     generated by the first fused pass in shared memory (the state is not
     written first); applied alone it is a uniform fill.  Both give the same
-    state bit for bit, and the oracle's."""
+    state bit for bit, and the oracle's.  (A Y^1/2 on every qubit after the
+    layer leaves no diagonal prefix to fold.)"""
     rows, cols = (4, n // 4)
-    g = qs.qs_circuit_generate(rows, cols, 20, 7)
+    g0 = qs.qs_circuit_generate(rows, cols, 20, 7)
+    yh = np.zeros(n, dtype=qs.GATE_DTYPE)
+    yh["kind"], yh["q0"] = qs.QS_Y_HALF, np.arange(n)
+    g = np.concatenate([g0[:n], yh, g0[n:]])
     h = qs.qs_state_create(n, dtype)
     try:
         qs.qs_apply_circuit(h, g, mode=mode, tile_log2=tile)
@@ -195,6 +199,49 @@ def test_leading_layer_generated_by_the_first_pass_is_exact(dtype, mode, n, tile
         qs.qs_state_destroy(h)
     assert np.array_equal(one, two)
     assert rel_l2(one, O.simulate(n, g)) < (1e-5 if dtype == qs.QS_C64 else 1e-12)
+
+
+@pytest.mark.parametrize("dtype,n,tile,mixed", [(qs.QS_C64, 20, 0, False), (qs.QS_C64, 16, 9, False),
+                                                (qs.QS_C64, 12, 0, True), (qs.QS_C64, 13, 13, False),
+                                                (qs.QS_C128, 20, 0, False), (qs.QS_C128, 12, 0, True)])
+def test_diagonal_prefix_folded_into_the_first_pass(dtype, n, tile, mixed):
+    """After the leading Hadamard layer, the T and CZ gates that reach the
+    uniform state before any non-diagonal gate on their qubits are formed as
+    its phases by the first fused pass instead of running as ops: the state
+    matches the oracle's, and the unfolded evolution (the layer applied
+    alone, then the rest) to rounding.  `mixed`: a random gate mix after the
+    layer (repeated T on a qubit, cancelling CZ pairs, RZ and CPHASE left in
+    the list, the full interpreter)."""
+    rng = np.random.default_rng(300 + n)
+    if mixed:
+        layer = np.zeros(n, dtype=qs.GATE_DTYPE)
+        layer["kind"], layer["q0"] = qs.QS_H, rng.permutation(n)
+        pre = np.zeros(6, dtype=qs.GATE_DTYPE)
+        pre["kind"] = [qs.QS_T, qs.QS_T, qs.QS_T, qs.QS_CZ, qs.QS_CZ, qs.QS_T]
+        pre["q0"] = [0, 0, 1, 2, 2, 3]
+        pre["q1"] = [0, 0, 0, 3, 3, 0]
+        g = np.concatenate([layer, pre, random_gates(rng, n, 80)])
+    else:
+        g = qs.qs_circuit_generate(4, n // 4, 16, 11) if n % 4 == 0 else qs.qs_circuit_generate(1, n, 16, 11)
+    assert bench_fold(g[n:]) > 0
+    ref = O.simulate(n, g)
+    h = qs.qs_state_create(n, dtype)
+    try:
+        qs.qs_apply_circuit(h, g, mode=qs.QS_MODE_FUSED, tile_log2=tile)
+        one = qs.qs_state_copy_out(h, n, dtype)
+        qs.qs_state_reset(h)
+        qs.qs_apply_circuit(h, g[:n], mode=qs.QS_MODE_FUSED, tile_log2=tile)
+        qs.qs_apply_circuit(h, g[n:], mode=qs.QS_MODE_FUSED, tile_log2=tile)
+        two = qs.qs_state_copy_out(h, n, dtype)
+    finally:
+        qs.qs_state_destroy(h)
+    assert rel_l2(one, ref) < TOL[dtype]
+    assert rel_l2(one, two.astype(np.complex128)) < (5e-6 if dtype == qs.QS_C64 else 1e-13)
+
+
+def bench_fold(g):
+    import bench
+    return bench.fold_diagonal_prefix(qs, g)[0]
 
 
 def test_invalid_gate_launches_nothing():
