@@ -493,3 +493,21 @@ extern "C" int emulate_work(int count, const int *nq, const qs_gate *gates, cons
         if (done[i] != nitem[i]) return -6;
     return 0;
 }
+
+// The library's diagonal-prefix fold (the gates after a leading Hadamard
+// layer): the kept gates in order into `rest` (room for ng), their number
+// into *nrest, the fold masks into nb[kMaxQubits] and m[3] (T-count bits
+// 0, 1, 2); returns the number of gates folded.
+extern "C" int emul_fold(const qs_gate *g, size_t ng, qs_gate *rest, int *nrest, uint64_t *nb, uint64_t *m)
+{
+    std::vector<qs_gate> r;
+    FoldArgs f;
+    const size_t nf = fold_diagonal_prefix(g, ng, &r, &f);
+    for (size_t i = 0; i < r.size(); ++i) rest[i] = r[i];
+    *nrest = (int)r.size();
+    for (int q = 0; q < kMaxQubits; ++q) nb[q] = f.nb[q];
+    m[0] = f.m1;
+    m[1] = f.m2;
+    m[2] = f.m4;
+    return (int)nf;
+}

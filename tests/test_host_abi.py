@@ -169,6 +169,9 @@ def emulator():
     lib.emulate_work.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                  ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_int)]
+    lib.emul_fold.restype = ctypes.c_int
+    lib.emul_fold.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                              ctypes.c_void_p, ctypes.c_void_p]
     lib.emulate_plan.restype = ctypes.c_int
     lib.emulate_plan.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -478,3 +481,77 @@ def test_smallest_tiles_plan(dtype, t):
     g = O.generate_circuit(3, 4, 12, 4)
     st = qs.qs_plan_circuit(12, dtype, g, tile_log2=t)
     assert st["tile_log2"] == t and st["passes"] >= 2 and st["gates"] == g.size
+
+
+def _lib_fold(emulator, g):
+    g = np.ascontiguousarray(g)
+    rest = np.zeros(max(len(g), 1), dtype=qs.GATE_DTYPE)
+    nrest = ctypes.c_int()
+    nb = np.zeros(34, dtype=np.uint64)
+    m = np.zeros(3, dtype=np.uint64)
+    nf = emulator.emul_fold(g.ctypes.data if len(g) else None, len(g), rest.ctypes.data, ctypes.byref(nrest),
+                            nb.ctypes.data, m.ctypes.data)
+    return nf, rest[:nrest.value], nb, m
+
+
+def _random_list(rng, n, count):
+    kinds = [qs.QS_H, qs.QS_X_HALF, qs.QS_Y_HALF, qs.QS_T, qs.QS_T, qs.QS_T, qs.QS_CZ, qs.QS_CZ, qs.QS_CZ,
+             qs.QS_RX, qs.QS_RZ, qs.QS_CPHASE]
+    g = np.zeros(count, dtype=qs.GATE_DTYPE)
+    for i in range(count):
+        k = kinds[int(rng.integers(len(kinds)))]
+        g[i]["kind"] = k
+        a, b = rng.choice(n, size=2, replace=False)
+        g[i]["q0"] = a
+        g[i]["q1"] = b if k in (qs.QS_CZ, qs.QS_CPHASE) else 0
+        g[i]["theta"] = rng.uniform(-3, 3) if k in (qs.QS_RX, qs.QS_RZ, qs.QS_CPHASE) else 0.0
+    return g
+
+
+def test_library_fold_rule_matches_the_bench_accounting(emulator):
+    """The library's diagonal-prefix fold (qs_host.cpp) keeps exactly the
+    gates the bench's accounting mirror keeps, on random lists and on the
+    bench's circuits."""
+    import bench
+    rng = np.random.default_rng(41)
+    lists = [_random_list(rng, 6, c) for c in (0, 1, 5, 20, 60) for _ in range(8)]
+    lists += [qs.qs_circuit_generate(5, 6, 40, s)[30:] for s in range(3)]
+    for g in lists:
+        nf, rest, _, _ = _lib_fold(emulator, g)
+        nf_b, rest_b = bench.fold_diagonal_prefix(qs, g)
+        assert nf == nf_b and rest.tobytes() == rest_b.tobytes()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_library_fold_masks_give_the_oracle_state(emulator, seed):
+    """The fold masks the library hands to the first pass (CZ partners as
+    XOR-accumulated qubit masks, T counts mod 8 as three bit masks) give
+    2^(-n/2) e^{i pi k(x)/4}, k = 4 (CZ pairs set in x) + (T counts set in
+    x): the oracle's state after the Hadamard layer and the folded gates,
+    with repeated T and repeated (cancelling) CZ pairs in the list."""
+    rng = np.random.default_rng(500 + seed)
+    n = 7
+    g = _random_list(rng, n, 40)
+    nf, rest, nb, m = _lib_fold(emulator, g)
+    layer = np.zeros(n, dtype=qs.GATE_DTYPE)
+    layer["kind"], layer["q0"] = qs.QS_H, np.arange(n)
+    keep = np.zeros(len(g), dtype=bool)
+    j = 0
+    for i in range(len(g)):
+        if j < len(rest) and g[i].tobytes() == rest[j].tobytes():
+            keep[i] = True
+            j += 1
+    assert j == len(rest) and (~keep).sum() == nf
+    psi = O.simulate(n, np.concatenate([layer, g[~keep]]))
+    x = np.arange(1 << n, dtype=np.uint64)
+    bit = lambda v, q: (v >> np.uint64(q)) & np.uint64(1)
+    k = np.zeros(1 << n, dtype=np.int64)
+    for i in range(n):
+        for j2 in range(i + 1, n):
+            if (int(nb[i]) >> j2) & 1:
+                assert (int(nb[j2]) >> i) & 1                 # symmetric
+                k += 4 * (bit(x, i) * bit(x, j2)).astype(np.int64)
+        c = ((int(m[0]) >> i) & 1) + 2 * ((int(m[1]) >> i) & 1) + 4 * ((int(m[2]) >> i) & 1)
+        k += c * bit(x, i).astype(np.int64)
+    want = 2.0 ** (-n / 2) * np.exp(1j * np.pi * (k % 8) / 4)
+    assert np.max(np.abs(psi - want)) < 1e-13
