@@ -166,10 +166,13 @@ qs_status qs_state_amplitudes(const qs_state *s, void **device_amps);
 /* Sets the state to |0...0>.  For a state whose memory the caller cannot
  * reach (created by qs_state_create, pointer never taken) the write is
  * deferred to the next call that uses the state, and a following
- * qs_apply_circuit whose gates open with H on every qubit writes the
- * uniform superposition 2^(-n/2) in their place (Sec. "Convergence to
- * Porter-Thomas": cycle 0 is that layer), one pass instead of several.
- * Attached states, and states whose pointer was taken, are written at once. */
+ * qs_apply_circuit whose gates open with H on every qubit takes the uniform
+ * superposition 2^(-n/2) in their place (Sec. "Convergence to
+ * Porter-Thomas": cycle 0 is that layer): the first fused pass generates it
+ * in its tiles instead of reading the state (plain mode: one fill), and in
+ * QS_MODE_FUSED also forms the phases of the T and CZ gates that follow the
+ * layer before any non-diagonal gate on their qubits.  Attached states,
+ * and states whose pointer was taken, are written at once. */
 qs_status qs_state_reset(qs_state *s);
 
 /* Applies `ngates` gates (host array, read during the call) in order:

@@ -52,7 +52,8 @@ void gate_matrix(int kind, double theta, Cplx u[4]);
 qs_status validate_gates(int n, const qs_gate *g, size_t ng);
 // n when the gate list opens with H on every qubit (n gates, each qubit
 // once), else 0: on |0...0> that layer is the uniform superposition
-// (Sec. pt, cycle 0), written as one fill instead of a pass.
+// (Sec. pt, cycle 0), generated by the first fused pass (or written as one
+// fill before plain per-gate kernels) instead of run as gates.
 size_t leading_h_layer(const qs_gate *g, size_t ng, int n);
 
 // Diagonal prefix folded into the initial state.  After a leading Hadamard
